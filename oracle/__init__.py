@@ -1,0 +1,175 @@
+"""FP64 CPU oracle of the DIC hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never calls it.
+
+The arithmetic lives in ``dic_oracle.c`` (plain C, FP64 / exact int64 sums);
+this module compiles it with gcc and wraps it with ctypes.  Every function
+follows the paper's method as stated in the C file's header:
+
+* ``integer_search``  -- Eq. 1 (Section 2/2.1) with brute-force search.
+* ``subpixel``        -- IC-GN / Newton-Raphson (Section 2.2, Table 2) with
+                         a first-order warp and Keys bicubic interpolation.
+* ``znssd``           -- summed ZNSSD and its hand-derived FP64 gradient.
+* ``bicubic``         -- the bicubic interpolant itself (Section 2.2).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dic_oracle.c")
+_LIB = os.path.join(_HERE, "libdicoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ST_OK, ST_ZERO_VAR_REF, ST_OUT_OF_BOUNDS, ST_MAX_ITER, ST_NONFINITE, ST_SINGULAR, \
+    ST_ZERO_VAR_DEF = range(7)
+ICGN, FANR = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc -O2 -fopenmp, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-Wall", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            i32, i64, dbl = C.c_int, C.c_int64, C.c_double
+            lib.dico_grid.argtypes = [i32, i32, i32, i32, i32, P, P]
+            lib.dico_grid.restype = i32
+            lib.dico_integer_search.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64,
+                                                i32, P, P, P, P]
+            lib.dico_integer_search.restype = i32
+            lib.dico_subpixel.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, dbl, i32,
+                                          P, i64, P, P, P, i32, P, P, P, P, P]
+            lib.dico_subpixel.restype = i32
+            lib.dico_bicubic.argtypes = [P, i32, i32, i32, dbl, dbl, P, P]
+            lib.dico_bicubic.restype = dbl
+            lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P]
+            lib.dico_znssd.restype = i32
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def default_threads() -> int:
+    return os.cpu_count() or 1
+
+
+def grid(width: int, height: int, subset: int, step: int, radius: int) -> tuple[int, int]:
+    nx, ny = C.c_int(), C.c_int()
+    if _load().dico_grid(width, height, subset, step, radius, C.byref(nx), C.byref(ny)):
+        raise ValueError("bad grid arguments")
+    return nx.value, ny.value
+
+
+def _idx(poi_idx):
+    if poi_idx is None:
+        return None, -1
+    a = np.ascontiguousarray(poi_idx, dtype=np.int64)
+    return a, len(a)
+
+
+def integer_search(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
+                   poi_idx=None, threads: int | None = None) -> dict:
+    f = np.ascontiguousarray(f, np.uint8)
+    g = np.ascontiguousarray(g, np.uint8)
+    assert f.shape == g.shape and f.ndim == 2
+    H, W = f.shape
+    nx, ny = grid(W, H, subset, step, radius)
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        n = nx * ny
+    u0 = np.zeros(n, np.int32)
+    v0 = np.zeros(n, np.int32)
+    zn = np.zeros(n, np.float64)
+    st = np.zeros(n, np.uint8)
+    rc = _load().dico_integer_search(_ptr(f), _ptr(g), W, H, W, subset, step, radius,
+                                     _ptr(idx), n if idx is not None else -1,
+                                     threads or default_threads(),
+                                     _ptr(u0), _ptr(v0), _ptr(zn), _ptr(st))
+    if rc:
+        raise ValueError("oracle integer_search failed")
+    return dict(u0=u0, v0=v0, zncc=zn, status=st, nx=nx, ny=ny)
+
+
+def subpixel(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
+             u0, v0, status0, method: int = ICGN, tol: float = 1e-3, max_iter: int = 50,
+             poi_idx=None, threads: int | None = None, trajectory: bool = False) -> dict:
+    f = np.ascontiguousarray(f, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    H, W = f.shape
+    nx, ny = grid(W, H, subset, step, radius)
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        n = nx * ny
+    u0 = np.ascontiguousarray(u0, np.int32)
+    v0 = np.ascontiguousarray(v0, np.int32)
+    status0 = np.ascontiguousarray(status0, np.uint8)
+    assert len(u0) == n and len(v0) == n and len(status0) == n
+    p = np.zeros((n, 6), np.float64)
+    zn = np.zeros(n, np.float64)
+    it = np.zeros(n, np.int32)
+    st = np.zeros(n, np.uint8)
+    traj = np.zeros((n, max_iter + 1, 6), np.float64) if trajectory else None
+    rc = _load().dico_subpixel(_ptr(f), _ptr(g), W, H, W, subset, step, radius, method,
+                               tol, max_iter, _ptr(idx), n if idx is not None else -1,
+                               _ptr(u0), _ptr(v0), _ptr(status0),
+                               threads or default_threads(), _ptr(p), _ptr(zn), _ptr(it),
+                               _ptr(st), _ptr(traj))
+    if rc:
+        raise ValueError("oracle subpixel failed")
+    out = dict(p=p, u=p[:, 0], ux=p[:, 1], uy=p[:, 2], v=p[:, 3], vx=p[:, 4], vy=p[:, 5],
+               zncc=zn, iters=it, status=st, nx=nx, ny=ny)
+    if trajectory:
+        out["traj"] = traj
+    return out
+
+
+def bicubic(img: np.ndarray, x: float, y: float) -> tuple[float, float, float]:
+    img = np.ascontiguousarray(img, np.float64)
+    H, W = img.shape
+    gx, gy = C.c_double(), C.c_double()
+    v = _load().dico_bicubic(_ptr(img), W, H, W, float(x), float(y), C.byref(gx), C.byref(gy))
+    return v, gx.value, gy.value
+
+
+def znssd(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, p: np.ndarray,
+          poi_idx=None, grad: bool = True):
+    """Summed ZNSSD at shape parameters ``p`` (n x 6) and, optionally, its
+    gradient with respect to every pixel of ``g`` and every row of ``p``."""
+    f = np.ascontiguousarray(f, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    H, W = f.shape
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        nx, ny = grid(W, H, subset, step, radius)
+        n = nx * ny
+    p = np.ascontiguousarray(p, np.float64).reshape(n, 6)
+    loss = C.c_double()
+    dg = np.zeros((H, W), np.float64) if grad else None
+    dp = np.zeros((n, 6), np.float64) if grad else None
+    rc = _load().dico_znssd(_ptr(f), _ptr(g), W, H, W, subset, step, radius, _ptr(idx),
+                            n if idx is not None else -1, _ptr(p), C.byref(loss),
+                            _ptr(dg), _ptr(dp))
+    if rc:
+        raise ValueError("oracle znssd failed")
+    return (loss.value, dg, dp) if grad else loss.value

@@ -1,0 +1,557 @@
+/*
+ * dic_oracle.c -- plain, slow FP64 CPU oracle of the DIC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg call this file.  The CUDA library never links,
+ * includes or calls it, and it shares no code with the CUDA path.
+ *
+ * What it computes (Thoma & Ravi, "Significance of parallel computing on the
+ * performance of Digital Image Correlation algorithms in MATLAB"):
+ *
+ *  - ZNCC of a (2M+1)^2 reference subset and a target subset, Eq. 1
+ *    (Section 2 / 2.1), evaluated from exact 64-bit integer sums of 8-bit
+ *    grey levels.  With N = (2M+1)^2:
+ *        num = N*Sfg - Sf*Sg,  Df = N*Sff - Sf^2,  Dg = N*Sgg - Sg^2,
+ *        C   = num / sqrt(Df*Dg)
+ *    which is Eq. 1 with the means multiplied out.
+ *  - Brute-force search (Section 2.1): every integer offset of the search
+ *    window is evaluated and the largest C wins.  Candidates are compared
+ *    exactly (sign of num, then num_a^2*Dg_b against num_b^2*Dg_a in 128-bit
+ *    integers); ties keep the lowest linear index (dv+R)(2R+1)+(du+R).
+ *  - Sub-pixel refinement (Section 2.2) by the inverse-compositional
+ *    Gauss-Newton algorithm with a first-order ("affine") warp, and by the
+ *    forward-additive Newton-Raphson algorithm in its Gauss-Newton form
+ *    (Table 2).  Grey levels between pixels come from bicubic interpolation
+ *    (Section 2.2) with the Keys cubic-convolution kernel, a = -0.5, on the
+ *    4x4 neighbourhood, evaluated straight from the pixels (no look-up table).
+ *  - The summed ZNSSD of every subset at given shape parameters and its
+ *    gradient with respect to the deformed-image pixels and the parameters
+ *    (hand-derived adjoint, FP64).
+ *
+ * The paper leaves the shape function, the update rules, the bicubic kernel,
+ * the gradient operator, the convergence norm and the POI grid unstated; the
+ * readings used here are the standard first-order IC-GN / FA-NR forms:
+ *
+ *   warp      W(xi; p) = (x0 + dx + u + ux*dx + uy*dy, y0 + dy + v + vx*dx + vy*dy),
+ *             p = (u, ux, uy, v, vx, vy)
+ *   IC-GN     SD_i = [fx, fx dx, fx dy, fy, fy dx, fy dy], H = sum SD_i^T SD_i,
+ *             r_i = (f_i - fbar) - (df/dg)(g_i - gbar),
+ *             dp = -H^-1 sum SD_i^T r_i,  W(p) <- W(p) W(dp)^-1
+ *   FA-NR     J_i = grad g(W(xi_i;p)) dW/dp,
+ *             dp = (sum J^T J)^-1 sum J_i^T [(dg/df)(f_i - fbar) - (g_i - gbar)],
+ *             p <- p + dp
+ *   stop      |dp|_c = sqrt(du^2 + dv^2 + M^2 (dux^2+duy^2+dvx^2+dvy^2)) < tol,
+ *             or max_iter solves
+ *   gradients of f: central differences at integer pixels (equal to the
+ *             derivative of the Keys a=-0.5 interpolant at the nodes)
+ *   POI grid  x0 = B + k*step, B = M + R + 2, while x0 <= W-1-B (same in y)
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC (no fast-math).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum {
+  ST_OK = 0,
+  ST_ZERO_VAR_REF = 1,
+  ST_OUT_OF_BOUNDS = 2,
+  ST_MAX_ITER = 3,
+  ST_NONFINITE = 4,
+  ST_SINGULAR = 5,
+  ST_ZERO_VAR_DEF = 6
+};
+
+/* ------------------------------------------------------------------ grid */
+int dico_grid(int W, int H, int subset, int step, int R, int *nx, int *ny) {
+  if (subset < 3 || (subset & 1) == 0 || step < 1 || R < 0 || W < 1 || H < 1)
+    return -1;
+  int M = subset / 2, B = M + R + 2;
+  int ax = W - 1 - 2 * B, ay = H - 1 - 2 * B;
+  *nx = ax >= 0 ? ax / step + 1 : 0;
+  *ny = ay >= 0 ? ay / step + 1 : 0;
+  return 0;
+}
+
+static void poi_centre(int64_t poi, int nx, int M, int R, int step, int *x0, int *y0) {
+  int B = M + R + 2;
+  *x0 = B + (int)(poi % nx) * step;
+  *y0 = B + (int)(poi / nx) * step;
+}
+
+/* ------------------------------------------------------- integer search */
+/* 1 if C_a > C_b strictly, where C = n / sqrt(Df * d) with the same Df > 0. */
+static int zncc_greater(int64_t na, int64_t da, int64_t nb, int64_t db) {
+  if (na >= 0 && nb < 0) return 1;
+  if (na < 0 && nb >= 0) return 0;
+  __int128 lhs = (__int128)na * (__int128)na * (__int128)db;
+  __int128 rhs = (__int128)nb * (__int128)nb * (__int128)da;
+  if (na >= 0) return lhs > rhs;
+  return lhs < rhs; /* both negative: smaller |C| is the larger C */
+}
+
+static void search_one(const uint8_t *f, const uint8_t *g, int pitch, int x0, int y0,
+                       int M, int R, int32_t *u0, int32_t *v0, double *zncc,
+                       uint8_t *status) {
+  const int64_t N = (int64_t)(2 * M + 1) * (2 * M + 1);
+  int64_t Sf = 0, Sff = 0;
+  for (int dy = -M; dy <= M; ++dy)
+    for (int dx = -M; dx <= M; ++dx) {
+      int64_t a = f[(int64_t)(y0 + dy) * pitch + (x0 + dx)];
+      Sf += a;
+      Sff += a * a;
+    }
+  const int64_t Df = N * Sff - Sf * Sf;
+  if (Df == 0) {
+    *u0 = 0; *v0 = 0; *zncc = 0.0; *status = ST_ZERO_VAR_REF;
+    return;
+  }
+  int have = 0;
+  int64_t bn = 0, bd = 1;
+  int bu = -R, bv = -R;
+  for (int dv = -R; dv <= R; ++dv)
+    for (int du = -R; du <= R; ++du) {
+      int64_t Sg = 0, Sgg = 0, Sfg = 0;
+      for (int dy = -M; dy <= M; ++dy)
+        for (int dx = -M; dx <= M; ++dx) {
+          int64_t a = f[(int64_t)(y0 + dy) * pitch + (x0 + dx)];
+          int64_t b = g[(int64_t)(y0 + dy + dv) * pitch + (x0 + dx + du)];
+          Sg += b;
+          Sgg += b * b;
+          Sfg += a * b;
+        }
+      int64_t Dg = N * Sgg - Sg * Sg;
+      if (Dg == 0) continue; /* undefined correlation: never preferred */
+      int64_t num = N * Sfg - Sf * Sg;
+      if (!have || zncc_greater(num, Dg, bn, bd)) {
+        have = 1; bn = num; bd = Dg; bu = du; bv = dv;
+      }
+    }
+  if (!have) {
+    *u0 = -R; *v0 = -R; *zncc = 0.0; *status = ST_ZERO_VAR_DEF;
+    return;
+  }
+  *u0 = bu; *v0 = bv;
+  *zncc = (double)bn / sqrt((double)Df * (double)bd);
+  *status = ST_OK;
+}
+
+int dico_integer_search(const uint8_t *f, const uint8_t *g, int W, int H, int pitch,
+                        int subset, int step, int R, const int64_t *poi_idx,
+                        int64_t n_idx, int nthreads, int32_t *u0, int32_t *v0,
+                        double *zncc, uint8_t *status) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  const int M = subset / 2;
+  const int64_t total = (int64_t)nx * ny;
+  const int64_t n = poi_idx ? n_idx : total;
+  if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t poi = poi_idx ? poi_idx[k] : k;
+    int x0, y0;
+    poi_centre(poi, nx, M, R, step, &x0, &y0);
+    search_one(f, g, pitch, x0, y0, M, R, &u0[k], &v0[k], &zncc[k], &status[k]);
+  }
+  return 0;
+}
+
+/* -------------------------------------------------- bicubic (Keys a=-0.5) */
+/* Keys cubic-convolution kernel with a = -1/2 and its derivative. */
+static double keys(double s) {
+  double t = fabs(s);
+  if (t <= 1.0) return 1.5 * t * t * t - 2.5 * t * t + 1.0;
+  if (t < 2.0) return -0.5 * t * t * t + 2.5 * t * t - 4.0 * t + 2.0;
+  return 0.0;
+}
+static double keys_d(double s) {
+  double t = fabs(s), sg = s < 0 ? -1.0 : 1.0;
+  if (t <= 1.0) return sg * (4.5 * t * t - 5.0 * t);
+  if (t < 2.0) return sg * (-1.5 * t * t + 5.0 * t - 4.0);
+  return 0.0;
+}
+
+/* Value (and optionally the x/y derivatives) of the bicubic interpolant at
+ * (x, y); the caller guarantees 1 <= x < W-2 and 1 <= y < H-2. */
+static double interp(const double *img, int pitch, double x, double y, double *gx,
+                     double *gy) {
+  double fx0 = floor(x), fy0 = floor(y);
+  int ix = (int)fx0, iy = (int)fy0;
+  double tx = x - fx0, ty = y - fy0;
+  double wx[4], wy[4], dwx[4], dwy[4];
+  for (int k = 0; k < 4; ++k) {
+    wx[k] = keys(tx - (k - 1));
+    wy[k] = keys(ty - (k - 1));
+    dwx[k] = keys_d(tx - (k - 1));
+    dwy[k] = keys_d(ty - (k - 1));
+  }
+  double v = 0, vx = 0, vy = 0;
+  for (int l = 0; l < 4; ++l)
+    for (int k = 0; k < 4; ++k) {
+      double p = img[(int64_t)(iy + l - 1) * pitch + (ix + k - 1)];
+      v += wy[l] * wx[k] * p;
+      vx += wy[l] * dwx[k] * p;
+      vy += dwy[l] * wx[k] * p;
+    }
+  if (gx) *gx = vx;
+  if (gy) *gy = vy;
+  return v;
+}
+
+double dico_bicubic(const double *img, int W, int H, int pitch, double x, double y,
+                    double *gx, double *gy) {
+  if (!(x >= 1.0 && x < W - 2.0 && y >= 1.0 && y < H - 2.0)) return NAN;
+  return interp(img, pitch, x, y, gx, gy);
+}
+
+/* ------------------------------------------------------------ 6x6 solve */
+/* Cholesky factorisation of a symmetric 6x6 matrix in place (lower). */
+static int chol6(double A[6][6]) {
+  for (int j = 0; j < 6; ++j) {
+    double d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    if (!(d > 0.0) || !isfinite(d)) return -1;
+    d = sqrt(d);
+    A[j][j] = d;
+    for (int i = j + 1; i < 6; ++i) {
+      double s = A[i][j];
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s / d;
+    }
+  }
+  return 0;
+}
+static void chol6_solve(double L[6][6], const double b[6], double x[6]) {
+  double y[6];
+  for (int i = 0; i < 6; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+    y[i] = s / L[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
+    x[i] = s / L[i][i];
+  }
+}
+
+/* ----------------------------------------------------------- warp helpers */
+/* p = (u, ux, uy, v, vx, vy) */
+static void warp_pt(const double p[6], int x0, int y0, int dx, int dy, double *x,
+                    double *y) {
+  *x = x0 + dx + p[0] + p[1] * dx + p[2] * dy;
+  *y = y0 + dy + p[3] + p[4] * dx + p[5] * dy;
+}
+
+static int in_bounds(const double p[6], int x0, int y0, int M, int W, int H) {
+  for (int cy = -1; cy <= 1; cy += 2)
+    for (int cx = -1; cx <= 1; cx += 2) {
+      double x, y;
+      warp_pt(p, x0, y0, cx * M, cy * M, &x, &y);
+      if (!(x >= 1.0 && x < W - 2.0 && y >= 1.0 && y < H - 2.0)) return 0;
+    }
+  return 1;
+}
+
+/* W(p) <- W(p) * W(dp)^-1 with W(q) = [[1+ux, uy, u], [vx, 1+vy, v], [0, 0, 1]]. */
+static void compose_inverse(const double p[6], const double dp[6], double out[6]) {
+  double a = 1 + dp[1], b = dp[2], c = dp[4], d = 1 + dp[5];
+  double det = a * d - b * c;
+  double ia = d / det, ib = -b / det, ic = -c / det, id = a / det;
+  double itx = -(ia * dp[0] + ib * dp[3]);
+  double ity = -(ic * dp[0] + id * dp[3]);
+  double P00 = 1 + p[1], P01 = p[2], P02 = p[0];
+  double P10 = p[4], P11 = 1 + p[5], P12 = p[3];
+  double n00 = P00 * ia + P01 * ic, n01 = P00 * ib + P01 * id;
+  double n02 = P00 * itx + P01 * ity + P02;
+  double n10 = P10 * ia + P11 * ic, n11 = P10 * ib + P11 * id;
+  double n12 = P10 * itx + P11 * ity + P12;
+  out[0] = n02; out[1] = n00 - 1; out[2] = n01;
+  out[3] = n12; out[4] = n10; out[5] = n11 - 1;
+}
+
+static double dp_norm(const double dp[6], int M) {
+  double m2 = (double)M * M;
+  return sqrt(dp[0] * dp[0] + dp[3] * dp[3] +
+              m2 * (dp[1] * dp[1] + dp[2] * dp[2] + dp[4] * dp[4] + dp[5] * dp[5]));
+}
+
+/* g at every warped subset point; returns mean and sqrt(sum (g-gbar)^2).
+ * Optional derivative outputs. */
+static void sample_subset(const double *g, int pitch, const double p[6], int x0, int y0,
+                          int M, double *gv, double *gxv, double *gyv, double *gbar,
+                          double *dg) {
+  int S = 2 * M + 1, N = S * S;
+  double s = 0;
+  for (int i = 0; i < N; ++i) {
+    int dx = i % S - M, dy = i / S - M;
+    double x, y;
+    warp_pt(p, x0, y0, dx, dy, &x, &y);
+    gv[i] = interp(g, pitch, x, y, gxv ? &gxv[i] : NULL, gyv ? &gyv[i] : NULL);
+    s += gv[i];
+  }
+  double m = s / N, q = 0;
+  for (int i = 0; i < N; ++i) q += (gv[i] - m) * (gv[i] - m);
+  *gbar = m;
+  *dg = sqrt(q);
+}
+
+/* ------------------------------------------------------------- sub-pixel */
+static void subpixel_one(const double *f, const double *g, int W, int H, int pitch,
+                         int x0, int y0, int M, int method, double tol, int max_iter,
+                         int32_t iu0, int32_t iv0, uint8_t st0, double *pout,
+                         double *zncc, int32_t *iters, uint8_t *status, double *traj) {
+  const int S = 2 * M + 1, N = S * S;
+  double p[6] = {(double)iu0, 0, 0, (double)iv0, 0, 0};
+  for (int k = 0; k < 6; ++k) pout[k] = p[k];
+  *iters = 0;
+  if (traj)
+    for (int k = 0; k < (max_iter + 1) * 6; ++k) traj[k] = NAN;
+  if (traj)
+    for (int k = 0; k < 6; ++k) traj[k] = p[k];
+  if (st0 != ST_OK) {
+    *zncc = 0.0;
+    *status = st0;
+    return;
+  }
+  double *fc = malloc(sizeof(double) * N * 6);
+  double *fx = fc + N, *fy = fx + N, *gv = fy + N, *gxv = gv + N, *gyv = gxv + N;
+  double fs = 0;
+  for (int i = 0; i < N; ++i) {
+    int dx = i % S - M, dy = i / S - M;
+    int64_t o = (int64_t)(y0 + dy) * pitch + (x0 + dx);
+    fc[i] = f[o];
+    fx[i] = 0.5 * (f[o + 1] - f[o - 1]);
+    fy[i] = 0.5 * (f[o + pitch] - f[o - pitch]);
+    fs += fc[i];
+  }
+  double fbar = fs / N, q = 0;
+  for (int i = 0; i < N; ++i) {
+    fc[i] -= fbar;
+    q += fc[i] * fc[i];
+  }
+  const double df = sqrt(q);
+  uint8_t st = ST_MAX_ITER;
+  int it_done = 0;
+  if (df == 0.0) {
+    st = ST_ZERO_VAR_REF;
+    goto final;
+  }
+
+  if (method == 0) {
+    /* ---------------- IC-GN: Hessian from the reference subset, once ---- */
+    double Hm[6][6] = {{0}};
+    for (int i = 0; i < N; ++i) {
+      int dx = i % S - M, dy = i / S - M;
+      double sd[6] = {fx[i], fx[i] * dx, fx[i] * dy, fy[i], fy[i] * dx, fy[i] * dy};
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) Hm[a][b] += sd[a] * sd[b];
+    }
+    if (chol6(Hm)) {
+      st = ST_SINGULAR;
+      goto final;
+    }
+    for (int it = 1; it <= max_iter; ++it) {
+      double gbar, dg;
+      sample_subset(g, pitch, p, x0, y0, M, gv, NULL, NULL, &gbar, &dg);
+      if (!(dg > 0.0) || !isfinite(dg)) {
+        st = ST_NONFINITE;
+        break;
+      }
+      double b[6] = {0};
+      for (int i = 0; i < N; ++i) {
+        int dx = i % S - M, dy = i / S - M;
+        double r = fc[i] - (df / dg) * (gv[i] - gbar);
+        double sd[6] = {fx[i], fx[i] * dx, fx[i] * dy, fy[i], fy[i] * dx, fy[i] * dy};
+        for (int a = 0; a < 6; ++a) b[a] += sd[a] * r;
+      }
+      double dp[6];
+      chol6_solve(Hm, b, dp);
+      for (int a = 0; a < 6; ++a) dp[a] = -dp[a];
+      it_done = it;
+      int fin = 1;
+      for (int a = 0; a < 6; ++a) fin &= isfinite(dp[a]);
+      if (!fin) {
+        st = ST_NONFINITE;
+        break;
+      }
+      double pn[6];
+      compose_inverse(p, dp, pn);
+      if (!in_bounds(pn, x0, y0, M, W, H)) {
+        st = ST_OUT_OF_BOUNDS;
+        break;
+      }
+      memcpy(p, pn, sizeof p);
+      if (traj)
+        for (int k = 0; k < 6; ++k) traj[it * 6 + k] = p[k];
+      if (dp_norm(dp, M) < tol) {
+        st = ST_OK;
+        break;
+      }
+    }
+  } else {
+    /* ---------------- FA-NR (Gauss-Newton Hessian, rebuilt each step) --- */
+    for (int it = 1; it <= max_iter; ++it) {
+      double gbar, dg;
+      sample_subset(g, pitch, p, x0, y0, M, gv, gxv, gyv, &gbar, &dg);
+      if (!(dg > 0.0) || !isfinite(dg)) {
+        st = ST_NONFINITE;
+        break;
+      }
+      double Hm[6][6] = {{0}}, b[6] = {0};
+      for (int i = 0; i < N; ++i) {
+        int dx = i % S - M, dy = i / S - M;
+        double J[6] = {gxv[i], gxv[i] * dx, gxv[i] * dy, gyv[i], gyv[i] * dx,
+                       gyv[i] * dy};
+        double r = (dg / df) * fc[i] - (gv[i] - gbar);
+        for (int a = 0; a < 6; ++a) {
+          b[a] += J[a] * r;
+          for (int c = 0; c < 6; ++c) Hm[a][c] += J[a] * J[c];
+        }
+      }
+      it_done = it;
+      if (chol6(Hm)) {
+        st = ST_SINGULAR;
+        break;
+      }
+      double dp[6];
+      chol6_solve(Hm, b, dp);
+      int fin = 1;
+      for (int a = 0; a < 6; ++a) fin &= isfinite(dp[a]);
+      if (!fin) {
+        st = ST_NONFINITE;
+        break;
+      }
+      double pn[6];
+      for (int a = 0; a < 6; ++a) pn[a] = p[a] + dp[a];
+      if (!in_bounds(pn, x0, y0, M, W, H)) {
+        st = ST_OUT_OF_BOUNDS;
+        break;
+      }
+      memcpy(p, pn, sizeof p);
+      if (traj)
+        for (int k = 0; k < 6; ++k) traj[it * 6 + k] = p[k];
+      if (dp_norm(dp, M) < tol) {
+        st = ST_OK;
+        break;
+      }
+    }
+  }
+
+final:
+  for (int k = 0; k < 6; ++k) pout[k] = p[k];
+  *iters = it_done;
+  *status = st;
+  if (st == ST_ZERO_VAR_REF) {
+    *zncc = 0.0;
+  } else {
+    /* Eq. 1 at the returned shape, interpolated target grey levels */
+    double gbar, dg;
+    sample_subset(g, pitch, p, x0, y0, M, gv, NULL, NULL, &gbar, &dg);
+    double s = 0;
+    for (int i = 0; i < N; ++i) s += fc[i] * (gv[i] - gbar);
+    *zncc = (dg > 0.0) ? s / (df * dg) : 0.0;
+  }
+  free(fc);
+}
+
+int dico_subpixel(const double *f, const double *g, int W, int H, int pitch, int subset,
+                  int step, int R, int method, double tol, int max_iter,
+                  const int64_t *poi_idx, int64_t n_idx, const int32_t *u0,
+                  const int32_t *v0, const uint8_t *st0, int nthreads, double *p_out,
+                  double *zncc, int32_t *iters, uint8_t *status, double *traj) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  if (method != 0 && method != 1) return -1;
+  if (max_iter < 1) return -1;
+  const int M = subset / 2;
+  const int64_t n = poi_idx ? n_idx : (int64_t)nx * ny;
+  if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t poi = poi_idx ? poi_idx[k] : k;
+    int x0, y0;
+    poi_centre(poi, nx, M, R, step, &x0, &y0);
+    subpixel_one(f, g, W, H, pitch, x0, y0, M, method, tol, max_iter, u0[k], v0[k],
+                 st0[k], &p_out[k * 6], &zncc[k], &iters[k], &status[k],
+                 traj ? &traj[k * (int64_t)(max_iter + 1) * 6] : NULL);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------- ZNSSD + adjoint */
+/* L = sum over POIs k and subset points i of
+ *       [ (f_i - fbar)/df - (g(W(xi_i; p_k)) - gbar)/dg ]^2
+ * and, if requested, dL/dg (H x pitch, accumulated) and dL/dp (n x 6).
+ * With ft_i = (f_i-fbar)/df, gt_i = (g_i-gbar)/dg and C = sum ft_i gt_i:
+ *   dL/dg_i = (2/dg) (C gt_i - ft_i),  dL/dp = sum_i dL/dg_i * grad g_i dW/dp,
+ * and dL/dg_i is spread onto the 4x4 pixels with the bicubic weights. */
+int dico_znssd(const double *f, const double *g, int W, int H, int pitch, int subset,
+               int step, int R, const int64_t *poi_idx, int64_t n_idx,
+               const double *p, double *loss, double *dL_dg, double *dL_dp) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  const int M = subset / 2, S = subset, N = S * S;
+  const int64_t n = poi_idx ? n_idx : (int64_t)nx * ny;
+  double *buf = malloc(sizeof(double) * N * 4);
+  double *fc = buf, *gv = buf + N, *gxv = gv + N, *gyv = gxv + N;
+  double total = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t poi = poi_idx ? poi_idx[k] : k;
+    int x0, y0;
+    poi_centre(poi, nx, M, R, step, &x0, &y0);
+    const double *pk = &p[k * 6];
+    if (dL_dp)
+      for (int a = 0; a < 6; ++a) dL_dp[k * 6 + a] = 0.0;
+    if (!in_bounds(pk, x0, y0, M, W, H)) continue;
+    double fs = 0;
+    for (int i = 0; i < N; ++i) {
+      int dx = i % S - M, dy = i / S - M;
+      fc[i] = f[(int64_t)(y0 + dy) * pitch + (x0 + dx)];
+      fs += fc[i];
+    }
+    double fbar = fs / N, q = 0;
+    for (int i = 0; i < N; ++i) {
+      fc[i] -= fbar;
+      q += fc[i] * fc[i];
+    }
+    double df = sqrt(q), gbar, dg;
+    sample_subset(g, pitch, pk, x0, y0, M, gv, gxv, gyv, &gbar, &dg);
+    if (!(df > 0) || !(dg > 0)) continue;
+    double C = 0, Lk = 0;
+    for (int i = 0; i < N; ++i) {
+      double e = fc[i] / df - (gv[i] - gbar) / dg;
+      Lk += e * e;
+      C += (fc[i] / df) * ((gv[i] - gbar) / dg);
+    }
+    total += Lk;
+    if (!dL_dg && !dL_dp) continue;
+    for (int i = 0; i < N; ++i) {
+      int dx = i % S - M, dy = i / S - M;
+      double gi = (2.0 / dg) * (C * (gv[i] - gbar) / dg - fc[i] / df);
+      if (dL_dp) {
+        double J[6] = {gxv[i], gxv[i] * dx, gxv[i] * dy, gyv[i], gyv[i] * dx,
+                       gyv[i] * dy};
+        for (int a = 0; a < 6; ++a) dL_dp[k * 6 + a] += gi * J[a];
+      }
+      if (dL_dg) {
+        double x, y;
+        warp_pt(pk, x0, y0, dx, dy, &x, &y);
+        double fx0 = floor(x), fy0 = floor(y);
+        int ix = (int)fx0, iy = (int)fy0;
+        double tx = x - fx0, ty = y - fy0;
+        for (int l = 0; l < 4; ++l)
+          for (int c = 0; c < 4; ++c)
+            dL_dg[(int64_t)(iy + l - 1) * pitch + (ix + c - 1)] +=
+                gi * keys(ty - (l - 1)) * keys(tx - (c - 1));
+      }
+    }
+  }
+  free(buf);
+  *loss = total;
+  return 0;
+}

@@ -1,0 +1,328 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks it against a
+closed form, an invariance of Eq. 1, brute force written independently here,
+a special case with a known exact answer, or the accuracy the paper states
+(0.1 px guaranteed, usually below 0.05 px; Section 3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import configs
+from workloads.speckle import Rigid
+
+
+# ----------------------------------------------------------------- POI grid
+@pytest.mark.parametrize("w,h,subset,step,r,count", [
+    (256, 256, 21, 10, 10, 484),       # rigid256: 22 x 22
+    (1024, 1024, 31, 5, 20, 36100),    # affine1024: 190 x 190
+    (2048, 2048, 41, 8, 24, 60025),    # sine2048x64: 245 x 245 per pair
+    (1024, 1024, 31, 8, 20, 14161),    # affine1024x8: 119 x 119 per pair
+])
+def test_grid_counts(w, h, subset, step, r, count):
+    nx, ny = oracle.grid(w, h, subset, step, r)
+    assert nx * ny == count
+    m = subset // 2
+    b = m + r + 2
+    # last centre keeps the search window plus the 4x4 stencil inside
+    assert b + (nx - 1) * step + m + r + 2 <= w - 1
+
+
+def test_grid_empty_when_image_too_small():
+    assert oracle.grid(20, 20, 21, 5, 10) == (0, 0)
+
+
+# ----------------------------------------------------- ZNCC / integer search
+def _eq1_map(f, g, x0, y0, m, r):
+    """Eq. 1 written out literally (means subtracted, float64), all offsets."""
+    a = f[y0 - m:y0 + m + 1, x0 - m:x0 + m + 1].astype(np.float64)
+    a = a - a.mean()
+    out = np.full((2 * r + 1, 2 * r + 1), -np.inf)
+    for dv in range(-r, r + 1):
+        for du in range(-r, r + 1):
+            b = g[y0 + dv - m:y0 + dv + m + 1, x0 + du - m:x0 + du + m + 1].astype(np.float64)
+            b = b - b.mean()
+            den = math.sqrt((a * a).sum()) * math.sqrt((b * b).sum())
+            if den > 0:
+                out[dv + r, du + r] = (a * b).sum() / den
+    return out
+
+
+@pytest.mark.parametrize("seed,anti", [(1, False), (2, False), (3, True)])
+def test_search_matches_brute_force_eq1(seed, anti):
+    """Brute force (Section 2.1) over Eq. 1 on tiny inputs, including an
+    anti-correlated pair where most candidates have C < 0."""
+    f, g = configs.tiny(seed, 28, 26, 35, Rigid(1.3, -0.6), noise=3.0)
+    if anti:
+        g = (255 - g).astype(np.uint8)
+    subset, step, r = 5, 2, 3
+    res = oracle.integer_search(f, g, subset, step, r)
+    m = subset // 2
+    b = m + r + 2
+    n_checked = 0
+    for k in range(res["nx"] * res["ny"]):
+        x0 = b + (k % res["nx"]) * step
+        y0 = b + (k // res["nx"]) * step
+        cmap = _eq1_map(f, g, x0, y0, m, r)
+        if not np.isfinite(cmap).any():     # flat reference or flat targets
+            assert res["status"][k] in (oracle.ST_ZERO_VAR_REF, oracle.ST_ZERO_VAR_DEF)
+            continue
+        assert res["status"][k] == oracle.ST_OK
+        best = np.argmax(cmap)          # first maximum in (dv, du) row-major order
+        flat = np.sort(cmap.ravel())[::-1]
+        assert res["zncc"][k] == pytest.approx(flat[0], abs=1e-12)
+        # the chosen offset attains the maximum of the literal Eq. 1 map
+        assert cmap[res["v0"][k] + r, res["u0"][k] + r] == pytest.approx(flat[0], abs=1e-12)
+        if flat[0] - flat[1] > 1e-9:     # no near-tie: offset is unique
+            assert (res["v0"][k], res["u0"][k]) == (best // (2 * r + 1) - r, best % (2 * r + 1) - r)
+            n_checked += 1
+    assert n_checked > 0.6 * res["nx"] * res["ny"]
+
+
+def test_identical_subsets_give_one():
+    """C = 1 exactly for g = f (Section 2.1: maximum when grey levels equal)."""
+    f, _ = configs.tiny(7, 40, 40, 80)
+    res = oracle.integer_search(f, f, 7, 3, 4)
+    assert (res["u0"] == 0).all() and (res["v0"] == 0).all()
+    assert np.abs(res["zncc"] - 1.0).max() < 1e-14
+
+
+@pytest.mark.parametrize("du,dv", [(3, -2), (-4, 1), (0, 4)])
+def test_planted_integer_shift(du, dv):
+    """g(x + du, y + dv) = f(x, y) is found exactly, with C = 1."""
+    big, _ = configs.tiny(11, 64, 64, 250)
+    f = big[8:56, 8:56]
+    g = big[8 - dv:56 - dv, 8 - du:56 - du]
+    res = oracle.integer_search(np.ascontiguousarray(f), np.ascontiguousarray(g), 9, 4, 5)
+    assert (res["u0"] == du).all() and (res["v0"] == dv).all()
+    assert np.abs(res["zncc"] - 1.0).max() < 1e-14
+
+
+def test_affine_intensity_invariance_exact():
+    """C is invariant under g -> a g + b, a > 0 (Eq. 1); sign flips for a < 0."""
+    f, g = configs.tiny(5, 32, 32, 60, Rigid(0.4, 1.7), noise=2.0)
+    f = (f // 3).astype(np.uint8)
+    g = (g // 3).astype(np.uint8)            # range 0..85
+    g2 = (2 * g.astype(np.int32) + 30).astype(np.uint8)   # a=2, b=30, still 8-bit
+    r1 = oracle.integer_search(f, g, 7, 2, 3)
+    r2 = oracle.integer_search(f, g2, 7, 2, 3)
+    assert (r1["u0"] == r2["u0"]).all() and (r1["v0"] == r2["v0"]).all()
+    assert np.abs(r1["zncc"] - r2["zncc"]).max() < 1e-13
+    # a = -1: each C becomes -C; the single-candidate search (R = 0) shows it
+    g3 = (255 - g.astype(np.int32)).astype(np.uint8)
+    s1 = oracle.integer_search(f, g, 7, 2, 0)
+    s3 = oracle.integer_search(f, g3, 7, 2, 0)
+    assert np.abs(s1["zncc"] + s3["zncc"]).max() < 1e-13
+
+
+def test_tie_keeps_lowest_linear_index():
+    """Equal C at several offsets: the lowest (dv+R)(2R+1)+(du+R) wins."""
+    rng = np.random.default_rng(3)
+    period = rng.integers(0, 256, (40, 3)).astype(np.uint8)
+    g = np.tile(period, (1, 14))             # 40 x 42, period 3 in x
+    f = np.roll(g, -1, axis=1)               # f(x) = g(x+1): C = 1 at du = 1 + 3k
+    res = oracle.integer_search(f, g, 5, 5, 3)
+    assert res["nx"] * res["ny"] > 0
+    # candidates with C = 1 at dv = 0: du in {-2, 1}; the lowest index is du = -2
+    assert (res["u0"] == -2).all() and (res["v0"] == 0).all()
+    assert np.abs(res["zncc"] - 1.0).max() < 1e-14
+
+
+def test_zero_variance_statuses():
+    f = np.full((30, 30), 77, np.uint8)
+    g, _ = configs.tiny(4, 30, 30, 40)
+    res = oracle.integer_search(f, g, 5, 3, 2)
+    assert (res["status"] == oracle.ST_ZERO_VAR_REF).all()
+    assert (res["zncc"] == 0).all()
+    res2 = oracle.integer_search(g, f, 5, 3, 2)
+    assert (res2["status"] == oracle.ST_ZERO_VAR_DEF).all()
+    assert (res2["u0"] == -2).all() and (res2["v0"] == -2).all()
+
+
+# ------------------------------------------------------------------ bicubic
+def test_bicubic_nodes_and_central_difference():
+    rng = np.random.default_rng(0)
+    img = rng.uniform(0, 255, (12, 14))
+    for y in range(1, 10):
+        for x in range(1, 12):
+            v, gx, gy = oracle.bicubic(img, x, y)
+            assert v == pytest.approx(img[y, x], abs=1e-12)
+            assert gx == pytest.approx(0.5 * (img[y, x + 1] - img[y, x - 1]), abs=1e-12)
+            assert gy == pytest.approx(0.5 * (img[y + 1, x] - img[y - 1, x]), abs=1e-12)
+
+
+def test_bicubic_reproduces_quadratics():
+    """The Keys kernel with a = -1/2 reproduces every quadratic exactly (its
+    third-order accuracy); any other a, or a wrong basis row, fails here."""
+    yy, xx = np.mgrid[0:16, 0:16].astype(np.float64)
+    c = [3.0, 0.7, -1.1, 0.05, -0.03, 0.08]
+    q = lambda x, y: c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y
+    img = q(xx, yy)
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        x, y = rng.uniform(1, 12.999, 2)
+        v, gx, gy = oracle.bicubic(img, x, y)
+        assert v == pytest.approx(q(x, y), abs=1e-10)
+        assert gx == pytest.approx(c[1] + 2 * c[3] * x + c[4] * y, abs=1e-10)
+        assert gy == pytest.approx(c[2] + c[4] * x + 2 * c[5] * y, abs=1e-10)
+
+
+def test_bicubic_does_not_reproduce_cubics():
+    """Guard on the previous pin: the kernel is cubic convolution, not a
+    cubic spline through cubics, so a cubic image is not exact."""
+    yy, xx = np.mgrid[0:16, 0:16].astype(np.float64)
+    img = 0.01 * xx ** 3
+    v, _, _ = oracle.bicubic(img, 5.25, 5.0)
+    assert abs(v - 0.01 * 5.25 ** 3) > 1e-4
+
+
+# --------------------------------------------------------------- sub-pixel
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+@pytest.mark.parametrize("du,dv", [(2, -1), (-3, 2)])
+def test_subpixel_exact_integer_shift_fixed_point(method, du, dv):
+    """g(x + du, y + dv) = f(x, y) exactly.  The bicubic interpolant equals
+    the pixels at integer nodes, so p = (du, 0, 0, dv, 0, 0) makes every
+    residual zero: it is an exact fixed point.  Started one pixel away in
+    each direction, the iteration must come back to it (through sub-pixel
+    positions) to round-off, with C = 1."""
+    big, _ = configs.tiny(17, 96, 96, 420)
+    f = np.ascontiguousarray(big[10:86, 10:86]).astype(np.float64)
+    g = np.ascontiguousarray(big[10 - dv:86 - dv, 10 - du:86 - du]).astype(np.float64)
+    subset, step, r = 15, 6, 4
+    n = int(np.prod(oracle.grid(76, 76, subset, step, r)))
+    z = np.zeros(n, np.int32)
+    s = oracle.subpixel(f, g, subset, step, r, z + du + 1, z + dv - 1, np.zeros(n, np.uint8),
+                        method=method, tol=1e-11, max_iter=100)
+    ok = s["status"] == oracle.ST_OK
+    assert ok.mean() > 0.9
+    want = np.array([du, 0, 0, dv, 0, 0], np.float64)
+    assert np.abs(s["p"][ok] - want).max() < 1e-9
+    assert np.abs(s["zncc"][ok] - 1.0).max() < 1e-12
+    assert (s["iters"][ok] >= 3).all()
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_subpixel_rigid_speckle_accuracy(rigid256, method):
+    """Imposed rigid field (3.4, -2.7) px on analytically re-rendered
+    speckles: within the paper's usual accuracy (0.05 px), small bias."""
+    p = rigid256
+    r = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
+    assert (r["u0"] >= 3).all() and (r["u0"] <= 4).all() and (r["v0"] == -3).all()
+    s = oracle.subpixel(p.ref, p.defm, p.subset, p.step, p.radius, r["u0"], r["v0"], r["status"],
+                        method=method)
+    assert (s["status"] == oracle.ST_OK).all()
+    eu, ev = s["u"] - 3.4, s["v"] + 2.7
+    assert abs(eu.mean()) < 0.02 and abs(ev.mean()) < 0.02
+    assert np.abs(eu).max() < 0.05 and np.abs(ev).max() < 0.05
+    grads = s["p"][:, [1, 2, 4, 5]]
+    assert np.abs(grads).mean() < 2e-3 and np.abs(grads).max() < 1e-2
+    assert s["zncc"].min() > 0.99
+
+
+def test_subpixel_affine_speckle_accuracy(affine1024):
+    p = affine1024
+    nx, ny = oracle.grid(1024, 1024, p.subset, p.step, p.radius)
+    idx = np.sort(np.random.default_rng(0).choice(nx * ny, 200, replace=False))
+    r = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx)
+    s = oracle.subpixel(p.ref, p.defm, p.subset, p.step, p.radius, r["u0"], r["v0"],
+                        r["status"], poi_idx=idx)
+    b = p.subset // 2 + p.radius + 2
+    x0 = (b + (idx % nx) * p.step).astype(float)
+    y0 = (b + (idx // nx) * p.step).astype(float)
+    gt = np.stack(p.deformation.displacement(x0, y0), 1)
+    e = np.abs(s["p"] - gt)
+    assert (s["status"] == oracle.ST_OK).all()
+    assert e[:, [0, 3]].max() < 0.05 and e[:, [0, 3]].mean() < 0.01
+    assert e[:, [1, 2, 4, 5]].mean() < 1e-3 and e[:, [1, 2, 4, 5]].max() < 5e-3
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_subpixel_affine_intensity_invariance(method):
+    """ZNSSD normalisation: g -> a g + b leaves p and C unchanged."""
+    f, g = configs.tiny(21, 48, 48, 120, Rigid(0.6, -0.35), noise=1.0)
+    f = f.astype(np.float64)
+    g = g.astype(np.float64)
+    kw = dict(subset=11, step=6, radius=2)
+    n = np.prod(oracle.grid(48, 48, 11, 6, 2))
+    z = np.zeros(n, np.int32)
+    s1 = oracle.subpixel(f, g, u0=z + 1, v0=z, status0=np.zeros(n, np.uint8), method=method, **kw)
+    s2 = oracle.subpixel(f, 1.7 * g + 13.0, u0=z + 1, v0=z, status0=np.zeros(n, np.uint8),
+                         method=method, **kw)
+    assert np.abs(s1["p"] - s2["p"]).max() < 1e-9
+    assert np.abs(s1["zncc"] - s2["zncc"]).max() < 1e-12
+    assert (s1["iters"] == s2["iters"]).all()
+
+
+def test_subpixel_status_paths():
+    f, g = configs.tiny(9, 48, 48, 120, Rigid(0.6, -0.35), noise=1.0)
+    kw = dict(subset=11, step=6, radius=2)
+    n = np.prod(oracle.grid(48, 48, 11, 6, 2))
+    z = np.zeros(n, np.int32)
+    ok = np.zeros(n, np.uint8)
+    # iteration cap: one solve cannot meet a 1e-12 tolerance
+    s = oracle.subpixel(f, g, u0=z + 1, v0=z, status0=ok, tol=1e-12, max_iter=1, **kw)
+    assert (s["status"] == oracle.ST_MAX_ITER).all() and (s["iters"] == 1).all()
+    # statuses from the integer search pass straight through
+    bad = np.full(n, oracle.ST_ZERO_VAR_REF, np.uint8)
+    s = oracle.subpixel(f, g, u0=z, v0=z, status0=bad, **kw)
+    assert (s["status"] == oracle.ST_ZERO_VAR_REF).all() and (s["iters"] == 0).all()
+    # a start that pushes the subset against the image edge stops in bounds
+    s = oracle.subpixel(f, g, u0=z - 9, v0=z, status0=ok, **kw)
+    assert (s["status"] != oracle.ST_OK).any()
+    # flat reference subset -> zero variance even if the search was skipped
+    flat = np.full((48, 48), 50.0)
+    s = oracle.subpixel(flat, g, u0=z, v0=z, status0=ok, **kw)
+    assert (s["status"] == oracle.ST_ZERO_VAR_REF).all()
+
+
+# -------------------------------------------------------- ZNSSD and adjoint
+def _adjoint_case():
+    f, g = configs.tiny(31, 40, 40, 100, Rigid(0.8, 0.3), noise=1.0)
+    f = f.astype(np.float64)
+    g = g.astype(np.float64)
+    n = int(np.prod(oracle.grid(40, 40, 9, 7, 2)))
+    rng = np.random.default_rng(5)
+    p = np.zeros((n, 6))
+    p[:, 0] = 0.8 + rng.uniform(-0.3, 0.3, n)
+    p[:, 3] = 0.3 + rng.uniform(-0.3, 0.3, n)
+    p[:, [1, 2, 4, 5]] = rng.uniform(-3e-3, 3e-3, (n, 4))
+    return f, g, p, dict(subset=9, step=7, radius=2)
+
+
+def test_znssd_zero_at_exact_match_and_equals_2_minus_2c():
+    f, g = configs.tiny(2, 40, 40, 100)
+    n = int(np.prod(oracle.grid(40, 40, 9, 7, 2)))
+    loss = oracle.znssd(f, f, 9, 7, 2, np.zeros((n, 6)), grad=False)
+    assert abs(loss) < 1e-20
+    # ZNSSD = 2 - 2 C per subset (both normalised vectors have unit norm)
+    f2, g2 = configs.tiny(3, 40, 40, 100, Rigid(0.4, 0.2), noise=2.0)
+    z = np.zeros(n, np.int32)
+    s = oracle.subpixel(f2, g2, 9, 7, 2, z, z, np.zeros(n, np.uint8))
+    loss = oracle.znssd(f2, g2, 9, 7, 2, s["p"], grad=False)
+    assert loss == pytest.approx(np.sum(2 - 2 * s["zncc"]), rel=1e-10)
+
+
+def test_adjoint_matches_central_differences():
+    f, g, p, kw = _adjoint_case()
+    loss, dg, dp = oracle.znssd(f, g, p=p, **kw)
+    h = 1e-5
+    for k in range(p.shape[0]):
+        for a in range(6):
+            pp, pm = p.copy(), p.copy()
+            pp[k, a] += h
+            pm[k, a] -= h
+            fd = (oracle.znssd(f, g, p=pp, grad=False, **kw)
+                  - oracle.znssd(f, g, p=pm, grad=False, **kw)) / (2 * h)
+            assert dp[k, a] == pytest.approx(fd, rel=1e-5, abs=1e-7 * max(1.0, abs(fd)))
+    rng = np.random.default_rng(8)
+    touched = np.argwhere(dg != 0)
+    for (y, x) in touched[rng.choice(len(touched), 40, replace=False)]:
+        gp, gm = g.copy(), g.copy()
+        gp[y, x] += 1e-3
+        gm[y, x] -= 1e-3
+        fd = (oracle.znssd(f, gp, p=p, grad=False, **kw)
+              - oracle.znssd(f, gm, p=p, grad=False, **kw)) / 2e-3
+        assert dg[y, x] == pytest.approx(fd, rel=1e-5, abs=1e-9)

@@ -1,0 +1,218 @@
+"""Seeded synthetic speckle image pairs (input generation only).
+
+This module produces the inputs that both the CUDA path and the CPU oracle
+consume.  It holds none of the correlation method's arithmetic: no ZNCC, no
+interpolation kernel, no warp update.  It renders an analytic intensity field
+(a sum of Gaussian speckles on a constant background) at pixel centres, once
+in the reference frame and once in the deformed frame through the inverse of
+a known deformation map, then adds Gaussian noise, clips to [0, 255] and
+rounds half-to-even to 8-bit grey levels.
+
+The paper's two test sets (a tensile specimen series and a public DIC image
+series, Section 3) are not available; these renders stand in for them with
+the image sizes, speckle densities and deformations of the benchmark
+workloads listed in ``workloads.configs``.
+
+Intensity model (one speckle k with centre c_k, radius r_k, peak A_k)::
+
+    I(x) = 20 + sum_k A_k * exp(-|x - c_k|^2 / r_k^2) * [|x - c_k| < 4 r_k]
+
+The deformed image is g(x') = I(phi^-1(x')) for a deformation phi mapping
+reference coordinates to deformed coordinates (x' = x + u(x)).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BACKGROUND = 20.0
+CUTOFF = 4.0  # speckle support radius in units of r_k
+
+
+# ---------------------------------------------------------------------------
+# Deformation maps.  Each provides forward(x, y) -> (x', y') and
+# inverse(x', y') -> (x, y) on float64 arrays, plus the exact displacement
+# and displacement gradient at reference points (ground truth for tests).
+# ---------------------------------------------------------------------------
+@dataclass
+class Rigid:
+    tx: float
+    ty: float
+
+    def forward(self, x, y):
+        return x + self.tx, y + self.ty
+
+    def inverse(self, xp, yp):
+        return xp - self.tx, yp - self.ty
+
+    def displacement(self, x, y):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        z = np.zeros(np.broadcast(x, y).shape)
+        return (z + self.tx, z + self.ty, z, z, z, z)
+
+
+@dataclass
+class Affine:
+    """x' = c + Rot(theta) diag(1+exx, 1+eyy) (x - c) + t, c = image centre."""
+    exx: float
+    eyy: float
+    theta_deg: float
+    tx: float
+    ty: float
+    cx: float
+    cy: float
+
+    def _mat(self):
+        th = math.radians(self.theta_deg)
+        c, s = math.cos(th), math.sin(th)
+        a = np.array([[c * (1 + self.exx), -s * (1 + self.eyy)],
+                      [s * (1 + self.exx), c * (1 + self.eyy)]], np.float64)
+        return a
+
+    def forward(self, x, y):
+        a = self._mat()
+        dx, dy = x - self.cx, y - self.cy
+        return (self.cx + a[0, 0] * dx + a[0, 1] * dy + self.tx,
+                self.cy + a[1, 0] * dx + a[1, 1] * dy + self.ty)
+
+    def inverse(self, xp, yp):
+        ai = np.linalg.inv(self._mat())
+        dx, dy = xp - self.cx - self.tx, yp - self.cy - self.ty
+        return (self.cx + ai[0, 0] * dx + ai[0, 1] * dy,
+                self.cy + ai[1, 0] * dx + ai[1, 1] * dy)
+
+    def displacement(self, x, y):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        xp, yp = self.forward(x, y)
+        a = self._mat()
+        z = np.zeros(np.broadcast(x, y).shape)
+        return (xp - x, z + a[0, 0] - 1, z + a[0, 1],
+                yp - y, z + a[1, 0], z + a[1, 1] - 1)
+
+
+@dataclass
+class Sinusoidal:
+    """u = au sin(2 pi y / ly) + tx,  v = av cos(2 pi x / lx) + ty (reference frame)."""
+    au: float = 2.0
+    ly: float = 128.0
+    av: float = 1.5
+    lx: float = 96.0
+    tx: float = 0.0
+    ty: float = 0.0
+
+    def forward(self, x, y):
+        return (x + self.au * np.sin(2 * np.pi * y / self.ly) + self.tx,
+                y + self.av * np.cos(2 * np.pi * x / self.lx) + self.ty)
+
+    def inverse(self, xp, yp, iters: int = 40):
+        # Fixed point x = x' - u(x); the map u has Lipschitz constant
+        # max(2 pi au / ly, 2 pi av / lx) ~ 0.098, so 40 sweeps reach 1e-15 px.
+        x = xp - self.tx
+        y = yp - self.ty
+        for _ in range(iters):
+            x = xp - self.tx - self.au * np.sin(2 * np.pi * y / self.ly)
+            y = yp - self.ty - self.av * np.cos(2 * np.pi * x / self.lx)
+        return x, y
+
+    def displacement(self, x, y):
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        z = np.zeros(np.broadcast(x, y).shape)
+        u = self.au * np.sin(2 * np.pi * y / self.ly) + self.tx + z
+        v = self.av * np.cos(2 * np.pi * x / self.lx) + self.ty + z
+        uy = self.au * 2 * np.pi / self.ly * np.cos(2 * np.pi * y / self.ly) + z
+        vx = -self.av * 2 * np.pi / self.lx * np.sin(2 * np.pi * x / self.lx) + z
+        return (u, z, uy, v, vx, z)
+
+
+@dataclass
+class SpeckleSet:
+    cx: np.ndarray
+    cy: np.ndarray
+    r: np.ndarray
+    amp: np.ndarray
+
+
+def draw_speckles(rng: np.random.Generator, n: int, width: int, height: int,
+                  pad: float, r_range=(2.5, 4.0), amp_range=(60.0, 200.0)) -> SpeckleSet:
+    """Uniform centres over the image padded by ``pad`` px on every side."""
+    cx = rng.uniform(-pad, width - 1 + pad, n)
+    cy = rng.uniform(-pad, height - 1 + pad, n)
+    r = rng.uniform(*r_range, n)
+    amp = rng.uniform(*amp_range, n)
+    return SpeckleSet(cx, cy, r, amp)
+
+
+def _render(sp: SpeckleSet, width: int, height: int, inverse, forward,
+            chunk: int = 2048) -> np.ndarray:
+    """Evaluate the analytic field at every pixel centre of the target frame.
+
+    ``inverse`` maps target-frame pixel coordinates to reference coordinates;
+    ``forward`` maps speckle centres into the target frame to find their
+    footprints.  Returns float64 (height, width).
+    """
+    img = np.full(height * width, BACKGROUND, np.float64)
+    if len(sp.cx) == 0:
+        return img.reshape(height, width)
+    # footprint half size: support radius 4 r_max plus a margin for the local
+    # stretch of the map (strains and rotations here are below 5 %)
+    h = int(math.ceil(CUTOFF * float(sp.r.max()) * 1.1)) + 2
+    off = np.arange(-h, h + 1)
+    oy, ox = np.meshgrid(off, off, indexing="ij")
+    oy = oy.ravel()
+    ox = ox.ravel()
+    pcx, pcy = forward(sp.cx, sp.cy)
+    for s in range(0, len(sp.cx), chunk):
+        e = min(s + chunk, len(sp.cx))
+        px = np.rint(pcx[s:e])[:, None] + ox[None, :]
+        py = np.rint(pcy[s:e])[:, None] + oy[None, :]
+        ok = (px >= 0) & (px < width) & (py >= 0) & (py < height)
+        kk = np.nonzero(ok)
+        pxv = px[kk]
+        pyv = py[kk]
+        rx, ry = inverse(pxv, pyv)
+        dx = rx - sp.cx[s:e][kk[0]]
+        dy = ry - sp.cy[s:e][kk[0]]
+        d2 = dx * dx + dy * dy
+        rr = sp.r[s:e][kk[0]]
+        val = sp.amp[s:e][kk[0]] * np.exp(-d2 / (rr * rr))
+        val = np.where(d2 < (CUTOFF * rr) ** 2, val, 0.0)
+        idx = (pyv * width + pxv).astype(np.int64)
+        img += np.bincount(idx, weights=val, minlength=height * width)
+    return img.reshape(height, width)
+
+
+def quantise(img: np.ndarray) -> np.ndarray:
+    """Clip to [0, 255] and round half-to-even to uint8."""
+    return np.rint(np.clip(img, 0.0, 255.0)).astype(np.uint8)
+
+
+@dataclass
+class Pair:
+    ref: np.ndarray          # uint8 (H, W)
+    defm: np.ndarray         # uint8 (H, W)
+    deformation: object      # map with forward/inverse/displacement
+    subset: int
+    step: int
+    radius: int
+    meta: dict = field(default_factory=dict)
+
+
+def render_pair(seed: int, width: int, height: int, n_speckles: int, deformation,
+                noise_sigma: float = 0.0, pad: float | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """Render (reference, deformed) uint8 images with a PCG64 stream of ``seed``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if pad is None:
+        pad = 4 * 4.0 + 8.0
+    sp = draw_speckles(rng, n_speckles, width, height, pad)
+    ident = (lambda x, y: (x, y))
+    f = _render(sp, width, height, ident, ident)
+    g = _render(sp, width, height, deformation.inverse, deformation.forward)
+    if noise_sigma > 0:
+        f = f + rng.normal(0.0, noise_sigma, f.shape)
+        g = g + rng.normal(0.0, noise_sigma, g.shape)
+    return quantise(f), quantise(g)
