@@ -1,0 +1,361 @@
+"""Benchmark of the DIC hot path on GB300: converged POI/s.
+
+One step = one pass of the whole hot path over one image pair: bind the pair
+(precompute kernel: gradients + bicubic table), brute-force ZNCC integer
+search, IC-GN sub-pixel refinement.  Workload ``affine1024``: one 1024x1024
+speckle pair (40000 speckles, affine exx=0.5 %, eyy=-0.2 %, 1 deg,
+t=(7.3, 4.1) px, noise sigma 2), subset 31x31, grid step 5 (36100 POIs),
+search +-20 px, tol 1e-3, at most 50 iterations.  Synthetic, seeded inputs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one replica per GPU (launched by torchrun; each rank processes
+its own pair, no collective on the data path) and reports the aggregate.
+``--impl reference`` times the FP64 CPU oracle on a bounded POI sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "affine1024"
+SUBSET, STEP, RADIUS, TOL, MAX_ITER = 31, 5, 20, 1e-3, 50
+METRIC = "converged POI/s"
+UNIT = "POI/s"
+L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--solve-bits", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=8192,
+                    help="POIs in the oracle's CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard(n_units: int, rank: int, world: int) -> list[int]:
+    """Units (image pairs) of one rank: round-robin, no data exchange."""
+    return list(range(rank, n_units, world))
+
+
+def config_dict(world: int) -> dict:
+    return {"workload": WORKLOAD, "image": "1024x1024 u8", "pairs_per_gpu": 1,
+            "subset": SUBSET, "grid_step": STEP, "search_radius": RADIUS, "pois_per_pair": 36100,
+            "method": "IC-GN", "conv_tol": TOL, "max_iter": MAX_ITER,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{world}"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region (read-only)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    from workloads import configs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dic.build()
+    pairs = shard(world, rank, world)          # one pair per rank (weak scaling)
+    pair = configs.affine1024(pair=pairs[0])
+    ref_d = torch.from_numpy(pair.ref).to(dev)
+    def_d = torch.from_numpy(pair.defm).to(dev)
+    stream = torch.cuda.Stream(dev)
+    props = torch.cuda.get_device_properties(dev)
+
+    def make(solve_bits):
+        d = dic.DIC(SUBSET, STEP, RADIUS, TOL, MAX_ITER, solve_bits=solve_bits, stream=stream)
+        return d
+
+    d = make(args.solve_bits)
+    n, nx, ny = d.set_pair(ref_d, def_d)
+    with torch.cuda.stream(stream):
+        s_out = d.integer_search()
+        p_out = d.subpixel(s_out)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(dd, search_events=None):
+        dic.dic_set_pair(dd.h, ref_d, def_d)
+        if search_events:
+            search_events[0].record(stream)
+        dic.dic_integer_search(dd.h, s_out["u0"], s_out["v0"], s_out["zncc0"], s_out["status0"])
+        if search_events:
+            search_events[1].record(stream)
+        dic.dic_subpixel(dd.h, dic.DIC_ICGN, s_out["u0"], s_out["v0"], s_out["status0"],
+                         p_out["u"], p_out["v"], p_out["ux"], p_out["uy"], p_out["vx"],
+                         p_out["vy"], p_out["zncc"], p_out["iters"], p_out["status"])
+
+    def timed_loop(dd, steps, warmup, sampler=None):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                flush.zero_()
+                step(dd)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        starts = [ev() for _ in range(steps)]
+        ends = [ev() for _ in range(steps)]
+        sev = [(ev(), ev()) for _ in range(steps)]
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(steps):
+                flush.zero_()
+                starts[i].record(stream)
+                step(dd, sev[i])
+                ends[i].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        search_ms = [a.elapsed_time(b) for a, b in sev]
+        conv = int((p_out["status"] == 0).sum().item())
+        return step_ms, search_ms, conv, wall, clocks
+
+    sampler = ClockSampler(local)
+    step_ms, search_ms, conv, wall, clocks = timed_loop(d, args.steps, args.warmup, sampler)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum[1:], op=torch.distributed.ReduceOp.SUM)
+        total_ms = float(tmax[0])
+        conv_all = float(tsum[1])
+    else:
+        conv_all = float(conv)
+    ms_per_step = total_ms / args.steps
+    value = conv_all * args.steps / (total_ms / 1e3)
+
+    # plain FP32 form (FP32 6x6 solve) on the same input, same timing rules
+    d32 = make(32)
+    d32.set_pair(ref_d, def_d)
+    st32, _, conv32, _, _ = timed_loop(d32, max(10, args.steps // 4), 3)
+    plain_value = conv32 * len(st32) / (sum(st32) / 1e3)
+    d32.close()
+
+    # e2e through the public call with host buffers: H2D of both images,
+    # the three kernels, D2H of every per-POI output, all inside the events
+    h_ref = torch.from_numpy(pair.ref).pin_memory()
+    h_def = torch.from_numpy(pair.defm).pin_memory()
+    h_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in p_out.items()}
+    h_s = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in s_out.items()}
+    ek = max(10, args.steps // 4)
+    e_starts = [ev() for _ in range(ek)]
+    e_ends = [ev() for _ in range(ek)]
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for i in range(ek):
+            flush.zero_()
+            e_starts[i].record(stream)
+            ref_d.copy_(h_ref, non_blocking=True)
+            def_d.copy_(h_def, non_blocking=True)
+            step(d)
+            for k in h_out:
+                h_out[k].copy_(p_out[k], non_blocking=True)
+            for k in h_s:
+                h_s[k].copy_(s_out[k], non_blocking=True)
+            e_ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)) / ek
+    e_conv = int((h_out["status"] == 0).sum().item())
+    e2e = {"value": e_conv / (e_ms / 1e3) * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(h_ref.numel() + h_def.numel()),
+           "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_out.values())
+                                     + sum(v.numel() * v.element_size() for v in h_s.values()))}
+
+    # roofline of the dominant kernel (integer search): FP32 FMA pipe
+    search_avg_s = statistics.mean(search_ms) / 1e3
+    flops = 2.0 * SUBSET * SUBSET * (2 * RADIUS + 1) ** 2 * n
+    peak_mhz = 2070.0
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    achieved = flops / search_avg_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "search_affine1024_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "search_kernel (FP32 FMA correlation)",
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                              f"{peak_mhz:.0f} MHz (nominal max clock)",
+                "search_ms": search_avg_s * 1e3}
+
+    cpu = None
+    if rank == 0:
+        cpu = cpu_baseline(pair, args.cpu_sample)
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded speckle renders)",
+                "config": config_dict(world), "e2e": e2e, "gpu_launches": 3 * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "forms": {"chosen": {"search": "fp32-exact", "solve": f"fp{args.solve_bits}",
+                                     "value": value},
+                          "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
+                                         "value": plain_value}},
+                "converged_fraction": conv / n, "wall_s_timed": wall}
+        print(json.dumps(line))
+    d.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------- CPU oracle arm
+def cpu_sample_idx(n: int, k: int):
+    import numpy as np
+    k = min(k, n)
+    return np.unique(np.linspace(0, n - 1, k).round().astype(np.int64))
+
+
+def cpu_baseline(pair, sample: int) -> dict:
+    """The FP64 oracle, as it stands, on an evenly spaced POI sample of the
+    same pair, on every host core."""
+    import numpy as np
+
+    import oracle
+    nx, ny = oracle.grid(pair.ref.shape[1], pair.ref.shape[0], SUBSET, STEP, RADIUS)
+    idx = cpu_sample_idx(nx * ny, sample)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.integer_search(pair.ref, pair.defm, SUBSET, STEP, RADIUS, poi_idx=idx,
+                              threads=threads)
+    s = oracle.subpixel(pair.ref, pair.defm, SUBSET, STEP, RADIUS, r["u0"], r["v0"],
+                        r["status"], tol=TOL, max_iter=MAX_ITER, poi_idx=idx, threads=threads)
+    dt = time.perf_counter() - t0
+    conv = int((s["status"] == 0).sum())
+    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(idx)} evenly spaced POIs of {WORKLOAD} (search + IC-GN), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from workloads import configs
+    pair = configs.affine1024(pair=0)
+    sample = max(64, args.cpu_sample // 8)
+    for _ in range(args.warmup):
+        cpu_baseline(pair, 64)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        cb = cpu_baseline(pair, sample)
+        secs.append(time.perf_counter() - t0)
+        vals.append(cb["value"])
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded speckle renders)", "config": config_dict(world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1,
+                             "kind": "oracle",
+                             "sample": f"{sample} evenly spaced POIs of {WORKLOAD} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * dic.h -- C ABI of the GB300 digital-image-correlation hot path.
+ *
+ * Method: Thoma & Ravi, "Significance of parallel computing on the
+ * performance of Digital Image Correlation algorithms in MATLAB".  For every
+ * point of interest (POI) on a regular grid of the reference image f, the
+ * library finds the integer displacement that maximises the zero-normalised
+ * cross-correlation (ZNCC, Eq. 1) of a (2M+1)x(2M+1) subset by brute-force
+ * search (Section 2.1), then refines it to sub-pixel accuracy with a
+ * first-order (6-parameter, affine) subset shape function over bicubically
+ * interpolated deformed-image grey levels, by the inverse-compositional
+ * Gauss-Newton algorithm or by forward-additive Newton-Raphson
+ * (Section 2.2, Table 2).
+ *
+ * Conventions shared by every call:
+ *  - Images are 8-bit grey, row-major, pixel (x, y) at byte y*pitch + x;
+ *    x is the column, y the row.
+ *  - All image and array pointers are DEVICE pointers.  The caller allocates
+ *    and owns them; the library never frees caller memory and keeps image
+ *    pointers only as borrowed references between dic_set_pair and the next
+ *    dic_set_pair / dic_destroy (the images must stay alive and unchanged).
+ *  - The library owns its scratch (bicubic coefficient table, gradient
+ *    field), allocates it in dic_set_pair and frees it in dic_destroy.
+ *  - Work is enqueued asynchronously on the stream given to dic_set_stream
+ *    (default: the legacy default stream).  Argument errors are returned
+ *    synchronously; a CUDA launch error is returned as DIC_ERR_CUDA with the
+ *    message in dic_last_error.  Per-POI numerical outcomes are reported in
+ *    the per-POI status arrays, never as a call failure.
+ *  - POI k lies at x0 = B + (k % nx)*step, y0 = B + (k / nx)*step with
+ *    B = M + R + 2, so the whole search window and the 4x4 interpolation
+ *    stencil of every integer start stay inside the image.  The paper does
+ *    not state a grid; this margin is the reading used here.
+ *  - Shape vector order p = (u, ux, uy, v, vx, vy); the warp of subset point
+ *    (dx, dy) is (x0 + dx + u + ux*dx + uy*dy, y0 + dy + v + vx*dx + vy*dy).
+ *  - Calls on one handle are not thread-safe; distinct handles are.
+ */
+#ifndef DIC_GB300_H
+#define DIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dic_s *dic_t;
+
+typedef enum {
+  DIC_OK = 0,
+  DIC_ERR_ARG = -1,         /* invalid argument (null, size, alignment)        */
+  DIC_ERR_CUDA = -2,        /* CUDA runtime error; see dic_last_error           */
+  DIC_ERR_OOM = -3,         /* device allocation of library scratch failed      */
+  DIC_ERR_STATE = -4,       /* call out of order (e.g. no pair set)             */
+  DIC_ERR_TIMEOUT = -5,     /* a bounded device wait gave up                    */
+  DIC_ERR_UNSUPPORTED = -6  /* valid request this build does not implement      */
+} dic_status;
+
+typedef enum { DIC_ICGN = 0, DIC_FANR = 1 } dic_method;
+
+/* Integer-search arithmetic.  Both forms return the same argmax. */
+typedef enum {
+  DIC_FORM_PLAIN_FP32 = 0, /* FP32 FMA correlation, exact integer sums          */
+  DIC_FORM_BF16TC = 1      /* reserved: tensor-core correlation                 */
+} dic_form;
+
+/* Per-POI status codes written by dic_integer_search / dic_subpixel. */
+enum {
+  DIC_POI_OK = 0,
+  DIC_POI_ZERO_VAR_REF = 1,  /* flat reference subset: Eq. 1 undefined           */
+  DIC_POI_OUT_OF_BOUNDS = 2, /* an update would move the subset off the image     */
+  DIC_POI_MAX_ITER = 3,      /* iteration cap reached; last shape still returned  */
+  DIC_POI_NONFINITE = 4,     /* flat target subset or non-finite update           */
+  DIC_POI_SINGULAR = 5,      /* 6x6 Gauss-Newton matrix not positive definite     */
+  DIC_POI_ZERO_VAR_DEF = 6   /* every candidate target subset is flat             */
+};
+
+/* Library version as an integer major*10000 + minor*100 + patch. */
+int dic_version(void);
+
+/* Create a handle.
+ *   subset_size    odd, >= 3 and <= 63 (the paper's (2M+1), Section 2.1)
+ *   grid_step      POI spacing in pixels, >= 1
+ *   search_radius  R >= 0: offsets [-R, R]^2 are searched (Section 2.1 uses a
+ *                  fixed window around the reference position)
+ *   shape_order    1 = first-order 6-parameter warp (the only order built;
+ *                  anything else returns DIC_ERR_UNSUPPORTED)
+ *   conv_tol       stop when |dp| < conv_tol, with
+ *                  |dp| = sqrt(du^2 + dv^2 + M^2 (dux^2+duy^2+dvx^2+dvy^2))
+ *   max_iter       maximum Gauss-Newton solves per POI, >= 1
+ * Host-only: touches no GPU.  *out is NULL on failure. */
+dic_status dic_create(dic_t *out, int subset_size, int grid_step, int search_radius,
+                      int shape_order, float conv_tol, int max_iter);
+
+/* Release the handle and its device scratch.  NULL is accepted. */
+void dic_destroy(dic_t h);
+
+/* Message of the last failed call on this handle ("" if none). */
+const char *dic_last_error(dic_t h);
+
+/* Stream for all later work (a cudaStream_t passed as void*; NULL = default). */
+dic_status dic_set_stream(dic_t h, void *cuda_stream);
+
+/* Integer-search arithmetic form (see dic_form). */
+dic_status dic_set_form(dic_t h, dic_form form);
+
+/* Precision of the per-POI 6x6 Gauss-Newton solve: 32 (FP32) or 64 (FP64
+ * Cholesky).  The per-point work is FP32 either way.  Default 32. */
+dic_status dic_set_solve_precision(dic_t h, int bits);
+
+/* Bind a reference/deformed image pair (device pointers, borrowed) and
+ * enqueue the precompute kernel: central-difference gradients of f and the
+ * 16 bicubic coefficients of every 1x1 cell of g (Section 2.2's bicubic
+ * interpolation with the look-up table of its ref. [18]).
+ *   width, height  >= 4 pixels each
+ *   pitch_bytes    >= width; both pointers 16-byte aligned and pitch a
+ *                  multiple of 16 enable TMA staging, otherwise plain loads
+ * Allocates scratch of 72 bytes per pixel on first use or growth
+ * (DIC_ERR_OOM on failure). */
+dic_status dic_set_pair(dic_t h, const uint8_t *ref_dev, const uint8_t *def_dev,
+                        int width, int height, int pitch_bytes);
+
+/* Grid size of the bound pair: n_pois = nx * ny (0 if the image is too
+ * small for one POI).  Any output pointer may be NULL. */
+dic_status dic_num_pois(dic_t h, int *n_pois, int *nx, int *ny);
+
+/* Brute-force integer search (Eq. 1, Section 2.1) for every POI.
+ * Outputs (device, n_pois each): u0, v0 = best integer offset in [-R, R];
+ * zncc0 = its ZNCC; status = DIC_POI_OK / ZERO_VAR_REF / ZERO_VAR_DEF.
+ * Every candidate's sums are exact integers; ties keep the lowest linear
+ * index (v0+R)(2R+1)+(u0+R).  Requires dic_set_pair (else DIC_ERR_STATE). */
+dic_status dic_integer_search(dic_t h, int32_t *u0, int32_t *v0, float *zncc0,
+                              uint8_t *status);
+
+/* Sub-pixel refinement (Section 2.2) of every POI from the integer start
+ * (u0, v0, status0), e.g. the outputs of dic_integer_search.  POIs whose
+ * status0 is not DIC_POI_OK are passed through with zero gradients.
+ * Outputs (device, n_pois each): the six shape parameters, zncc (Eq. 1 at the
+ * returned shape), iters (solves performed) and status. */
+dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int32_t *v0,
+                        const uint8_t *status0, float *u, float *v, float *ux, float *uy,
+                        float *vx, float *vy, float *zncc, int32_t *iters,
+                        uint8_t *status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIC_GB300_H */

@@ -1,0 +1,223 @@
+"""GB300 digital-image-correlation hot path: thin Python binding of the C ABI.
+
+The functions below carry the names of ``include/dic.h`` and only marshal
+arguments (device pointers of torch tensors, sizes) into the CUDA library
+``libdicgb.so``; every step of the computation runs in its kernels.  There is
+no CPU fallback: if the library cannot be loaded, or no CUDA device is
+present when work is requested, a ``RuntimeError`` is raised.
+
+Method (Thoma & Ravi): brute-force ZNCC integer search (Eq. 1, Section 2.1)
+then first-order IC-GN or Newton-Raphson sub-pixel refinement over bicubic
+interpolation (Section 2.2, Table 2), for every POI of a regular grid.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdicgb.so")
+
+DIC_OK, DIC_ERR_ARG, DIC_ERR_CUDA, DIC_ERR_OOM, DIC_ERR_STATE, DIC_ERR_TIMEOUT, \
+    DIC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+DIC_ICGN, DIC_FANR = 0, 1
+DIC_FORM_PLAIN_FP32, DIC_FORM_BF16TC = 0, 1
+POI_OK, POI_ZERO_VAR_REF, POI_OUT_OF_BOUNDS, POI_MAX_ITER, POI_NONFINITE, POI_SINGULAR, \
+    POI_ZERO_VAR_DEF = range(7)
+
+_STATUS_NAMES = {0: "DIC_OK", -1: "DIC_ERR_ARG", -2: "DIC_ERR_CUDA", -3: "DIC_ERR_OOM",
+                 -4: "DIC_ERR_STATE", -5: "DIC_ERR_TIMEOUT", -6: "DIC_ERR_UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+P = C.c_void_p
+i32 = C.c_int
+f32 = C.c_float
+
+# name -> (restype, argtypes); mirrors include/dic.h
+SIGNATURES = {
+    "dic_version": (i32, []),
+    "dic_create": (i32, [C.POINTER(P), i32, i32, i32, i32, f32, i32]),
+    "dic_destroy": (None, [P]),
+    "dic_last_error": (C.c_char_p, [P]),
+    "dic_set_stream": (i32, [P, P]),
+    "dic_set_form": (i32, [P, i32]),
+    "dic_set_solve_precision": (i32, [P, i32]),
+    "dic_set_pair": (i32, [P, P, P, i32, i32, i32]),
+    "dic_num_pois": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    "dic_integer_search": (i32, [P, P, P, P, P]),
+    "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
+}
+
+
+class DICError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def build() -> str:
+    from . import _build
+    return _build.build()
+
+
+def lib():
+    """Load libdicgb.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run build())")
+            l = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(l, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = l
+    return _lib
+
+
+def _check(code: int, h=None):
+    if code != DIC_OK:
+        msg = lib().dic_last_error(h).decode() if h else ""
+        raise DICError(code, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    if not t.is_cuda:
+        raise RuntimeError("expected a CUDA tensor (the library takes device pointers)")
+    if not t.is_contiguous():
+        raise RuntimeError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C names
+def dic_version() -> int:
+    return lib().dic_version()
+
+
+def dic_create(subset_size: int, grid_step: int, search_radius: int, shape_order: int = 1,
+               conv_tol: float = 1e-3, max_iter: int = 50):
+    h = P()
+    _check(lib().dic_create(C.byref(h), subset_size, grid_step, search_radius, shape_order,
+                            conv_tol, max_iter))
+    return h
+
+
+def dic_destroy(h) -> None:
+    lib().dic_destroy(h)
+
+
+def dic_last_error(h) -> str:
+    return lib().dic_last_error(h).decode()
+
+
+def dic_set_stream(h, stream) -> None:
+    ptr = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else 0)
+    _check(lib().dic_set_stream(h, C.c_void_p(ptr)), h)
+
+
+def dic_set_form(h, form: int) -> None:
+    _check(lib().dic_set_form(h, form), h)
+
+
+def dic_set_solve_precision(h, bits: int) -> None:
+    _check(lib().dic_set_solve_precision(h, bits), h)
+
+
+def dic_set_pair(h, ref, defm, width: int | None = None, height: int | None = None,
+                 pitch: int | None = None) -> None:
+    if ref.dtype.itemsize != 1 or defm.dtype.itemsize != 1:
+        raise RuntimeError("images must be 8-bit")
+    hgt, wid = ref.shape[-2:]
+    _check(lib().dic_set_pair(h, _ptr(ref), _ptr(defm), width or wid, height or hgt,
+                              pitch or ref.stride(-2)), h)
+
+
+def dic_num_pois(h) -> tuple[int, int, int]:
+    n, nx, ny = i32(), i32(), i32()
+    _check(lib().dic_num_pois(h, C.byref(n), C.byref(nx), C.byref(ny)), h)
+    return n.value, nx.value, ny.value
+
+
+def dic_integer_search(h, u0, v0, zncc0, status) -> None:
+    _check(lib().dic_integer_search(h, _ptr(u0), _ptr(v0), _ptr(zncc0), _ptr(status)), h)
+
+
+def dic_subpixel(h, method, u0, v0, status0, u, v, ux, uy, vx, vy, zncc, iters, status) -> None:
+    _check(lib().dic_subpixel(h, method, _ptr(u0), _ptr(v0), _ptr(status0), _ptr(u), _ptr(v),
+                              _ptr(ux), _ptr(uy), _ptr(vx), _ptr(vy), _ptr(zncc), _ptr(iters),
+                              _ptr(status)), h)
+
+
+# ------------------------------------------------------------ convenience
+class DIC:
+    """Handle owner with torch-allocated outputs (device memory and streams
+    come from PyTorch; the computation is the library's)."""
+
+    def __init__(self, subset: int, step: int, radius: int, tol: float = 1e-3,
+                 max_iter: int = 50, solve_bits: int = 32, stream=None):
+        self.h = dic_create(subset, step, radius, 1, tol, max_iter)
+        self.subset, self.step, self.radius = subset, step, radius
+        if solve_bits != 32:
+            dic_set_solve_precision(self.h, solve_bits)
+        if stream is not None:
+            dic_set_stream(self.h, stream)
+        self._pair = None
+
+    def close(self):
+        if self.h is not None:
+            dic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_pair(self, ref, defm):
+        dic_set_pair(self.h, ref, defm)
+        self._pair = (ref, defm)  # keep the borrowed images alive
+        return dic_num_pois(self.h)
+
+    def integer_search(self, out=None):
+        import torch
+        n, _, _ = dic_num_pois(self.h)
+        dev = self._pair[0].device
+        if out is None:
+            out = dict(u0=torch.empty(n, dtype=torch.int32, device=dev),
+                       v0=torch.empty(n, dtype=torch.int32, device=dev),
+                       zncc0=torch.empty(n, dtype=torch.float32, device=dev),
+                       status0=torch.empty(n, dtype=torch.uint8, device=dev))
+        if n:
+            dic_integer_search(self.h, out["u0"], out["v0"], out["zncc0"], out["status0"])
+        return out
+
+    def subpixel(self, start, method=DIC_ICGN, out=None):
+        import torch
+        n, _, _ = dic_num_pois(self.h)
+        dev = self._pair[0].device
+        if out is None:
+            out = {k: torch.empty(n, dtype=torch.float32, device=dev)
+                   for k in ("u", "v", "ux", "uy", "vx", "vy", "zncc")}
+            out["iters"] = torch.empty(n, dtype=torch.int32, device=dev)
+            out["status"] = torch.empty(n, dtype=torch.uint8, device=dev)
+        if n:
+            dic_subpixel(self.h, method, start["u0"], start["v0"], start["status0"], out["u"],
+                         out["v"], out["ux"], out["uy"], out["vx"], out["vy"], out["zncc"],
+                         out["iters"], out["status"])
+        return out
+
+    def run(self, ref, defm, method=DIC_ICGN):
+        self.set_pair(ref, defm)
+        s = self.integer_search()
+        r = self.subpixel(s, method)
+        r.update(s)
+        return r

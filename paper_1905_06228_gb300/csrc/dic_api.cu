@@ -1,0 +1,273 @@
+// dic_api.cu -- the C ABI declared in include/dic.h: argument checking, the
+// handle's device scratch, TMA descriptors and kernel launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dic_internal.cuh"
+
+namespace dic {
+size_t search_smem_bytes(int S, int R);
+}
+
+namespace {
+
+constexpr int kVersion = 10000;  // 1.0.0
+
+dic_status fail(dic_t h, dic_status st, const char* fmt, ...) {
+  if (h) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->last_error = buf;
+  }
+  return st;
+}
+
+dic_status cuda_fail(dic_t h, cudaError_t e, const char* what) {
+  return fail(h, DIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D uint8 tensor map over an image with a box of (box_w bytes, box_h rows).
+bool encode_u8(CUtensorMap* tm, const uint8_t* base, int W, int H, int pitch, int box_w,
+               int box_h) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+void grid_of(int W, int H, int S, int step, int R, int* nx, int* ny) {
+  const int B = S / 2 + R + 2;
+  const int ax = W - 1 - 2 * B, ay = H - 1 - 2 * B;
+  *nx = ax >= 0 ? ax / step + 1 : 0;
+  *ny = ay >= 0 ? ay / step + 1 : 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dic_version(void) { return kVersion; }
+
+dic_status dic_create(dic_t* out, int subset_size, int grid_step, int search_radius,
+                      int shape_order, float conv_tol, int max_iter) {
+  if (!out) return DIC_ERR_ARG;
+  *out = nullptr;
+  if (subset_size < 3 || subset_size > dic::kMaxSubset || (subset_size & 1) == 0 ||
+      grid_step < 1 || search_radius < 0 || search_radius > 1000 || !(conv_tol > 0.f) ||
+      max_iter < 1)
+    return DIC_ERR_ARG;
+  if (shape_order != 1) return DIC_ERR_UNSUPPORTED;
+  dic_t h = new (std::nothrow) dic_s;
+  if (!h) return DIC_ERR_OOM;
+  h->subset = subset_size;
+  h->M = subset_size / 2;
+  h->step = grid_step;
+  h->R = search_radius;
+  h->shape_order = shape_order;
+  h->tol = conv_tol;
+  h->max_iter = max_iter;
+  *out = h;
+  return DIC_OK;
+}
+
+void dic_destroy(dic_t h) {
+  if (!h) return;
+  if (h->lut) cudaFree(h->lut);
+  if (h->grad) cudaFree(h->grad);
+  if (h->err_flag) cudaFree(h->err_flag);
+  delete h;
+}
+
+const char* dic_last_error(dic_t h) { return h ? h->last_error.c_str() : "null handle"; }
+
+dic_status dic_set_stream(dic_t h, void* s) {
+  if (!h) return DIC_ERR_ARG;
+  h->stream = static_cast<cudaStream_t>(s);
+  return DIC_OK;
+}
+
+dic_status dic_set_form(dic_t h, dic_form form) {
+  if (!h) return DIC_ERR_ARG;
+  if (form == DIC_FORM_PLAIN_FP32) {
+    h->form = form;
+    return DIC_OK;
+  }
+  if (form == DIC_FORM_BF16TC) return fail(h, DIC_ERR_UNSUPPORTED, "tensor-core form not built");
+  return fail(h, DIC_ERR_ARG, "unknown form %d", (int)form);
+}
+
+dic_status dic_set_solve_precision(dic_t h, int bits) {
+  if (!h) return DIC_ERR_ARG;
+  if (bits != 32 && bits != 64) return fail(h, DIC_ERR_ARG, "solve precision must be 32 or 64");
+  h->solve_bits = bits;
+  return DIC_OK;
+}
+
+dic_status dic_set_pair(dic_t h, const uint8_t* ref, const uint8_t* def, int width, int height,
+                        int pitch) {
+  if (!h) return DIC_ERR_ARG;
+  h->have_pair = false;
+  if (!ref || !def) return fail(h, DIC_ERR_ARG, "null image pointer");
+  if (width < 4 || height < 4 || pitch < width)
+    return fail(h, DIC_ERR_ARG, "bad image size %dx%d pitch %d", width, height, pitch);
+  int nx, ny;
+  grid_of(width, height, h->subset, h->step, h->R, &nx, &ny);
+  const size_t px = (size_t)width * height;
+  if (px > h->scratch_px) {
+    if (h->lut) cudaFree(h->lut);
+    if (h->grad) cudaFree(h->grad);
+    h->lut = nullptr;
+    h->grad = nullptr;
+    h->scratch_px = 0;
+    if (cudaMalloc(&h->lut, px * 4 * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&h->grad, px * sizeof(float2)) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->lut) cudaFree(h->lut);
+      h->lut = nullptr;
+      return fail(h, DIC_ERR_OOM, "cannot allocate %zu bytes of scratch", px * 72);
+    }
+    h->scratch_px = px;
+  }
+  if (!h->err_flag) {
+    if (cudaMalloc(&h->err_flag, sizeof(unsigned int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, DIC_ERR_OOM, "cannot allocate error flag");
+    }
+    cudaMemsetAsync(h->err_flag, 0, sizeof(unsigned int), h->stream);
+  }
+  h->ref = ref;
+  h->def = def;
+  h->g.W = width;
+  h->g.H = height;
+  h->g.pitch = pitch;
+  h->g.nx = nx;
+  h->g.ny = ny;
+  h->g.n_pois = (int64_t)nx * ny;
+  // TMA staging needs 16-byte aligned bases and pitch, and boxes <= 256.
+  const int span = h->subset + 2 * h->R;
+  const int bwg = dic::tma_box_width(span), bwf = dic::tma_box_width(h->subset);
+  h->tma_ok = ((uintptr_t)ref % 16 == 0) && ((uintptr_t)def % 16 == 0) && (pitch % 16 == 0) &&
+              bwg <= 256 && span <= 256 &&
+              encode_u8(&h->tm_def, def, width, height, pitch, bwg, span) &&
+              encode_u8(&h->tm_ref, ref, width, height, pitch, bwf, h->subset);
+  cudaError_t e = dic::launch_precompute(ref, def, width, height, pitch, h->grad, h->lut,
+                                         h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "precompute launch");
+  h->have_pair = true;
+  return DIC_OK;
+}
+
+dic_status dic_num_pois(dic_t h, int* n_pois, int* nx, int* ny) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (n_pois) *n_pois = (int)h->g.n_pois;
+  if (nx) *nx = h->g.nx;
+  if (ny) *ny = h->g.ny;
+  return DIC_OK;
+}
+
+dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
+                              uint8_t* status) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->g.n_pois == 0) return DIC_OK;
+  if (!u0 || !v0 || !zncc0 || !status) return fail(h, DIC_ERR_ARG, "null output pointer");
+  if (dic::search_smem_bytes(h->subset, h->R) > 227 * 1024)
+    return fail(h, DIC_ERR_UNSUPPORTED, "search window too large for shared memory");
+  dic::SearchParams p;
+  p.ref = h->ref;
+  p.def = h->def;
+  p.W = h->g.W;
+  p.H = h->g.H;
+  p.pitch = h->g.pitch;
+  p.S = h->subset;
+  p.M = h->M;
+  p.R = h->R;
+  p.step = h->step;
+  p.nx = h->g.nx;
+  p.n_pois = h->g.n_pois;
+  p.use_tma = h->tma_ok ? 1 : 0;
+  p.u0 = u0;
+  p.v0 = v0;
+  p.zncc0 = zncc0;
+  p.status = status;
+  p.err_flag = h->err_flag;
+  cudaError_t e = dic::launch_search(p, &h->tm_ref, &h->tm_def, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "integer search launch");
+  return DIC_OK;
+}
+
+dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int32_t* v0,
+                        const uint8_t* status0, float* u, float* v, float* ux, float* uy,
+                        float* vx, float* vy, float* zncc, int32_t* iters, uint8_t* status) {
+  if (!h) return DIC_ERR_ARG;
+  if (method != DIC_ICGN && method != DIC_FANR) return fail(h, DIC_ERR_ARG, "unknown method");
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->g.n_pois == 0) return DIC_OK;
+  if (!u0 || !v0 || !status0 || !u || !v || !ux || !uy || !vx || !vy || !zncc || !iters ||
+      !status)
+    return fail(h, DIC_ERR_ARG, "null pointer");
+  dic::SubpixelParams p;
+  p.ref = h->ref;
+  p.grad = h->grad;
+  p.lut = h->lut;
+  p.W = h->g.W;
+  p.H = h->g.H;
+  p.pitch = h->g.pitch;
+  p.S = h->subset;
+  p.M = h->M;
+  p.R = h->R;
+  p.step = h->step;
+  p.nx = h->g.nx;
+  p.n_pois = h->g.n_pois;
+  p.max_iter = h->max_iter;
+  p.tol = h->tol;
+  p.u0 = u0;
+  p.v0 = v0;
+  p.st0 = status0;
+  p.u = u;
+  p.v = v;
+  p.ux = ux;
+  p.uy = uy;
+  p.vx = vx;
+  p.vy = vy;
+  p.zncc = zncc;
+  p.iters = iters;
+  p.status = status;
+  cudaError_t e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "subpixel launch");
+  return DIC_OK;
+}
+
+}  // extern "C"

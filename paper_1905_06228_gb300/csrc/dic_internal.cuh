@@ -1,0 +1,108 @@
+// dic_internal.cuh -- handle layout and kernel launch interfaces shared by the
+// translation units of the CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dic.h"
+
+namespace dic {
+
+// POI status codes (mirrors DIC_POI_* of dic.h).
+enum : uint8_t {
+  kOk = 0,
+  kZeroVarRef = 1,
+  kOutOfBounds = 2,
+  kMaxIter = 3,
+  kNonFinite = 4,
+  kSingular = 5,
+  kZeroVarDef = 6
+};
+
+constexpr int kMaxSubset = 63;
+
+// Geometry of one bound image pair.
+struct PairGeom {
+  int W = 0, H = 0, pitch = 0;
+  int nx = 0, ny = 0;
+  int64_t n_pois = 0;
+};
+
+// Parameters of the integer search kernel.
+struct SearchParams {
+  const uint8_t* ref;
+  const uint8_t* def;
+  int W, H, pitch;
+  int S, M, R, step, nx;
+  int64_t n_pois;
+  int use_tma;
+  int32_t* u0;
+  int32_t* v0;
+  float* zncc0;
+  uint8_t* status;
+  unsigned int* err_flag;  // set when a bounded wait gives up
+};
+
+// Parameters of the sub-pixel kernels.
+struct SubpixelParams {
+  const uint8_t* ref;
+  const float2* grad;  // central-difference gradients of f, W*H
+  const float4* lut;   // bicubic coefficient planes of g, 4*W*H
+  int W, H, pitch;
+  int S, M, R, step, nx;
+  int64_t n_pois;
+  int max_iter;
+  float tol;
+  const int32_t* u0;
+  const int32_t* v0;
+  const uint8_t* st0;
+  float* u;
+  float* v;
+  float* ux;
+  float* uy;
+  float* vx;
+  float* vy;
+  float* zncc;
+  int32_t* iters;
+  uint8_t* status;
+};
+
+// Launchers (each returns the cudaError_t of its launch).
+cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int H,
+                              int pitch, float2* grad, float4* lut, cudaStream_t st);
+cudaError_t launch_search(const SearchParams& p, const CUtensorMap* tm_ref,
+                          const CUtensorMap* tm_def, cudaStream_t st);
+cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
+                            cudaStream_t st);
+
+// Size of the byte box that TMA stages for a subset / search window.
+__host__ __device__ inline int tma_box_width(int span) { return ((span + 15 + 15) / 16) * 16; }
+
+}  // namespace dic
+
+struct dic_s {
+  int subset = 0, M = 0, step = 0, R = 0, shape_order = 1, max_iter = 0;
+  float tol = 0.f;
+  int form = DIC_FORM_PLAIN_FP32;
+  int solve_bits = 32;
+  cudaStream_t stream = nullptr;
+
+  bool have_pair = false;
+  const uint8_t* ref = nullptr;
+  const uint8_t* def = nullptr;
+  dic::PairGeom g;
+
+  float4* lut = nullptr;
+  float2* grad = nullptr;
+  size_t scratch_px = 0;  // capacity in pixels
+  unsigned int* err_flag = nullptr;
+
+  bool tma_ok = false;
+  CUtensorMap tm_ref{}, tm_def{};
+
+  std::string last_error;
+};

@@ -1,0 +1,464 @@
+// k_subpixel.cu -- sub-pixel refinement: IC-GN and FA-NR (Section 2.2, Table 2).
+//
+// One warp per POI; lane l owns subset points i = l, l+32, ...  Per-point
+// reference data (gradients of f, f - fbar, the point's (dx, dy)) lives in
+// shared memory for the whole solve; the deformed image is read through the
+// bicubic coefficient table (4 float4 per cell, from the precompute kernel).
+//
+// Warp:   W(xi; p) = (x0 + dx + u + ux dx + uy dy, y0 + dy + v + vx dx + vy dy).
+// IC-GN:  SD_i = grad f_i dW/dp, H = sum SD^T SD (once per POI),
+//         r_i = (f_i - fbar) - (df/dg)(g_i - gbar),
+//         dp = -H^-1 sum SD_i r_i,   W(p) <- W(p) W(dp)^-1.
+// FA-NR:  J_i = grad g(W(xi_i; p)) dW/dp (derivative of the bicubic patch),
+//         dp = (sum J^T J)^-1 sum J_i [(dg/df)(f_i - fbar) - (g_i - gbar)],
+//         p <- p + dp  (Gauss-Newton form of Newton-Raphson).
+// Stop:   |dp|_c = sqrt(du^2 + dv^2 + M^2 (dux^2+duy^2+dvx^2+dvy^2)) < tol,
+//         else after max_iter solves; an update that moves a subset corner
+//         outside [1, W-2) x [1, H-2) is rejected (status OUT_OF_BOUNDS).
+//
+// Each iteration is ONE pass over the points: with the shift c = fbar the
+// lane accumulates S0 = sum (g-c), S1 = sum (g-c)^2 and sum SD_k (g-c) (or
+// the FA-NR sums); then gbar = c + S0/N, dg^2 = S1 - S0^2/N and the
+// right-hand side follow exactly as in the formulas above.  The 6x6 solve is
+// FP32 or FP64 (Cholesky), chosen per launch.  The final ZNCC is Eq. 1 at
+// the returned shape (one extra pass).
+#include "dic_internal.cuh"
+
+namespace dic {
+namespace {
+
+constexpr int kWarpsPerCta = 4;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Cholesky factorisation of a symmetric 6x6 (lower part used), in place.
+template <typename T>
+__device__ __forceinline__ bool chol6(T A[6][6]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    T d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    if (!(d > T(0))) return false;
+    d = sqrt(d);
+    A[j][j] = d;
+    const T inv = T(1) / d;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      T s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s * inv;
+    }
+  }
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void chol6_solve(const T L[6][6], const T b[6], T x[6]) {
+  T y[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+    y[i] = s / L[i][i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    T s = y[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
+    x[i] = s / L[i][i];
+  }
+}
+
+// Bicubic value (and optionally derivatives) from one table cell.
+template <bool DERIV>
+__device__ __forceinline__ float bicubic(const float4* __restrict__ lut, size_t plane,
+                                         size_t cell, float tx, float ty, float& gx, float& gy) {
+  const float4 a0 = __ldg(lut + cell), a1 = __ldg(lut + plane + cell),
+               a2 = __ldg(lut + 2 * plane + cell), a3 = __ldg(lut + 3 * plane + cell);
+  const float r0 = fmaf(fmaf(fmaf(a0.w, tx, a0.z), tx, a0.y), tx, a0.x);
+  const float r1 = fmaf(fmaf(fmaf(a1.w, tx, a1.z), tx, a1.y), tx, a1.x);
+  const float r2 = fmaf(fmaf(fmaf(a2.w, tx, a2.z), tx, a2.y), tx, a2.x);
+  const float r3 = fmaf(fmaf(fmaf(a3.w, tx, a3.z), tx, a3.y), tx, a3.x);
+  if (DERIV) {
+    const float d0 = fmaf(fmaf(3.f * a0.w, tx, 2.f * a0.z), tx, a0.y);
+    const float d1 = fmaf(fmaf(3.f * a1.w, tx, 2.f * a1.z), tx, a1.y);
+    const float d2 = fmaf(fmaf(3.f * a2.w, tx, 2.f * a2.z), tx, a2.y);
+    const float d3 = fmaf(fmaf(3.f * a3.w, tx, 2.f * a3.z), tx, a3.y);
+    gx = fmaf(fmaf(fmaf(d3, ty, d2), ty, d1), ty, d0);
+    gy = fmaf(fmaf(3.f * r3, ty, 2.f * r2), ty, r1);
+  }
+  return fmaf(fmaf(fmaf(r3, ty, r2), ty, r1), ty, r0);
+}
+
+// Subset point walk of one lane: points i = lane, lane+32, ... in row-major
+// (dy outer) order, with (dx, dy) advanced incrementally.
+struct PtWalk {
+  int dx, dy, ddx, ddy, S, M;
+  __device__ __forceinline__ PtWalk(int lane, int S_, int M_) : S(S_), M(M_) {
+    dy = lane / S - M;
+    dx = lane % S - M;
+    ddy = 32 / S;
+    ddx = 32 % S;
+  }
+  __device__ __forceinline__ void next() {
+    dx += ddx;
+    dy += ddy;
+    if (dx > M) {
+      dx -= S;
+      dy += 1;
+    }
+  }
+};
+
+// Location of a warped point: table cell and fractional offsets.
+__device__ __forceinline__ size_t locate(const float p[6], int dx, int dy, int x0, int y0, int W,
+                                         int H, float& tx, float& ty) {
+  const float lx = fmaf(p[2], (float)dy, fmaf(1.f + p[1], (float)dx, p[0]));
+  const float ly = fmaf(1.f + p[5], (float)dy, fmaf(p[4], (float)dx, p[3]));
+  const float fx = floorf(lx), fy = floorf(ly);
+  tx = lx - fx;
+  ty = ly - fy;
+  int ix = x0 + (int)fx, iy = y0 + (int)fy;
+  ix = min(max(ix, 1), W - 3);  // memory safety only; bounds are checked on p
+  iy = min(max(iy, 1), H - 3);
+  return (size_t)iy * W + ix;
+}
+
+__device__ __forceinline__ bool corners_in(const float p[6], int x0, int y0, int M, int W, int H) {
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float cx = (c & 1) ? (float)M : -(float)M, cy = (c & 2) ? (float)M : -(float)M;
+    const float lx = fmaf(p[2], cy, fmaf(1.f + p[1], cx, p[0]));
+    const float ly = fmaf(1.f + p[5], cy, fmaf(p[4], cx, p[3]));
+    const float x = (float)x0 + lx, y = (float)y0 + ly;
+    ok = ok && (x >= 1.f) && (x < (float)(W - 2)) && (y >= 1.f) && (y < (float)(H - 2));
+  }
+  return ok;
+}
+
+// W(p) <- W(p) W(dp)^-1 for the first-order warp.
+__device__ __forceinline__ void compose_inverse(float p[6], const float dp[6]) {
+  const float a = 1.f + dp[1], b = dp[2], c = dp[4], d = 1.f + dp[5];
+  const float det = a * d - b * c;
+  const float ia = d / det, ib = -b / det, ic = -c / det, id = a / det;
+  const float itx = -(ia * dp[0] + ib * dp[3]);
+  const float ity = -(ic * dp[0] + id * dp[3]);
+  const float P00 = 1.f + p[1], P01 = p[2], P02 = p[0];
+  const float P10 = p[4], P11 = 1.f + p[5], P12 = p[3];
+  const float n00 = P00 * ia + P01 * ic, n01 = P00 * ib + P01 * id;
+  const float n02 = P00 * itx + P01 * ity + P02;
+  const float n10 = P10 * ia + P11 * ic, n11 = P10 * ib + P11 * id;
+  const float n12 = P10 * itx + P11 * ity + P12;
+  p[0] = n02;
+  p[1] = n00 - 1.f;
+  p[2] = n01;
+  p[3] = n12;
+  p[4] = n10;
+  p[5] = n11 - 1.f;
+}
+
+template <typename T>
+__device__ __forceinline__ bool solve6(const float Hf[21], const float bf[6], float out[6],
+                                       bool negate) {
+  T A[6][6];
+  int k = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      A[i][j] = (T)Hf[k];
+      A[j][i] = (T)Hf[k];
+      ++k;
+    }
+  if (!chol6<T>(A)) return false;
+  T b[6], x[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) b[i] = (T)bf[i];
+  chol6_solve<T>(A, b, x);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) out[i] = negate ? (float)(-x[i]) : (float)x[i];
+  return true;
+}
+
+template <bool FANR, typename TS>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+subpixel_kernel(const SubpixelParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t poi = (int64_t)blockIdx.x * kWarpsPerCta + wid;
+  if (poi >= p.n_pois) return;
+  const int S = p.S, M = p.M, N = S * S;
+  float2* sgrad = reinterpret_cast<float2*>(smem) + (size_t)wid * N;
+  float* sfc = reinterpret_cast<float*>(smem + (size_t)kWarpsPerCta * N * sizeof(float2)) +
+               (size_t)wid * N;
+  const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
+  const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
+  const int W = p.W, H = p.H;
+  const size_t plane = (size_t)W * H;
+
+  const uint8_t st0 = p.st0[poi];
+  float prm[6] = {(float)p.u0[poi], 0.f, 0.f, (float)p.v0[poi], 0.f, 0.f};
+  auto write_out = [&](float zn, int it, uint8_t st) {
+    if (lane == 0) {
+      p.u[poi] = prm[0];
+      p.ux[poi] = prm[1];
+      p.uy[poi] = prm[2];
+      p.v[poi] = prm[3];
+      p.vx[poi] = prm[4];
+      p.vy[poi] = prm[5];
+      p.zncc[poi] = zn;
+      p.iters[poi] = it;
+      p.status[poi] = st;
+    }
+  };
+  if (st0 != kOk) {
+    write_out(0.f, 0, st0);
+    return;
+  }
+
+  // ---- reference subset: f, its gradients, fbar, df
+  float fsum = 0.f;
+  {
+    PtWalk w(lane, S, M);
+    for (int i = lane; i < N; i += 32, w.next()) {
+      const int x = x0 + w.dx, y = y0 + w.dy;
+      const float f = (float)p.ref[(size_t)y * p.pitch + x];
+      sgrad[i] = p.grad[(size_t)y * W + x];
+      sfc[i] = f;
+      fsum += f;
+    }
+  }
+  fsum = warp_sum(fsum);  // exact: integer sum below 2^24
+  const float fbar = fsum / (float)N;
+  float q = 0.f;
+  float Hs[21], sdsum[6], bfv[6];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) Hs[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sdsum[k] = bfv[k] = 0.f;
+  {
+   PtWalk w(lane, S, M);
+   for (int i = lane; i < N; i += 32, w.next()) {
+    const float fc = sfc[i] - fbar;
+    sfc[i] = fc;
+    q = fmaf(fc, fc, q);
+    if (!FANR) {
+      const float2 gr = sgrad[i];
+      const float dx = (float)w.dx, dy = (float)w.dy;
+      const float sd[6] = {gr.x, gr.x * dx, gr.x * dy, gr.y, gr.y * dx, gr.y * dy};
+      int k = 0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        sdsum[a] += sd[a];
+        bfv[a] = fmaf(sd[a], fc, bfv[a]);
+#pragma unroll
+        for (int b = 0; b <= a; ++b, ++k) Hs[k] = fmaf(sd[a], sd[b], Hs[k]);
+      }
+    }
+   }
+  }
+  q = warp_sum(q);
+  const float df = sqrtf(q);
+  if (!(df > 0.f)) {
+    write_out(0.f, 0, kZeroVarRef);
+    return;
+  }
+  if (!FANR) {
+#pragma unroll
+    for (int k = 0; k < 21; ++k) Hs[k] = warp_sum(Hs[k]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      sdsum[k] = warp_sum(sdsum[k]);
+      bfv[k] = warp_sum(bfv[k]);
+    }
+  }
+  // IC-GN: factor H once (in the solve precision)
+  TS L[6][6];
+  if (!FANR) {
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        L[i][j] = (TS)Hs[k];
+        L[j][i] = (TS)Hs[k];
+        ++k;
+      }
+    if (!chol6<TS>(L)) {
+      write_out(0.f, 0, kSingular);
+      return;
+    }
+  }
+  if (!corners_in(prm, x0, y0, M, W, H)) {
+    write_out(0.f, 0, kOutOfBounds);
+    return;
+  }
+
+  const float c = fbar;
+  const float invN = 1.f / (float)N;
+  const float m2 = (float)M * (float)M;
+  uint8_t st = kMaxIter;
+  int it_done = 0;
+  for (int it = 1; it <= p.max_iter; ++it) {
+    float s0 = 0.f, s1 = 0.f;
+    float acc[FANR ? 39 : 6];
+#pragma unroll
+    for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = 0.f;
+    PtWalk w(lane, S, M);
+    for (int i = lane; i < N; i += 32, w.next()) {
+      const int dx = w.dx, dy = w.dy;
+      float tx, ty, gx = 0.f, gy = 0.f;
+      const size_t cell = locate(prm, dx, dy, x0, y0, W, H, tx, ty);
+      const float g = bicubic<FANR>(p.lut, plane, cell, tx, ty, gx, gy);
+      const float d = g - c;
+      s0 += d;
+      s1 = fmaf(d, d, s1);
+      const float fdx = (float)dx, fdy = (float)dy;
+      if (!FANR) {
+        const float2 gr = sgrad[i];
+        const float a = gr.x * d, b = gr.y * d;
+        acc[0] += a;
+        acc[1] = fmaf(a, fdx, acc[1]);
+        acc[2] = fmaf(a, fdy, acc[2]);
+        acc[3] += b;
+        acc[4] = fmaf(b, fdx, acc[4]);
+        acc[5] = fmaf(b, fdy, acc[5]);
+      } else {
+        const float J[6] = {gx, gx * fdx, gx * fdy, gy, gy * fdx, gy * fdy};
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+          for (int b = 0; b <= a; ++b, ++k) acc[k] = fmaf(J[a], J[b], acc[k]);  // 21 sums
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          acc[21 + a] = fmaf(J[a], d, acc[21 + a]);     // sum J (g - c)
+          acc[27 + a] = fmaf(J[a], sfc[i], acc[27 + a]);  // sum J (f - fbar)
+          acc[33 + a] += J[a];                          // sum J
+        }
+      }
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+#pragma unroll
+    for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = warp_sum(acc[k]);
+    const float gm = s0 * invN;  // gbar - c
+    const float var = s1 - s0 * gm;
+    const float dg = sqrtf(fmaxf(var, 0.f));
+    if (!(dg > 0.f) || !isfinite(dg)) {
+      st = kNonFinite;
+      break;
+    }
+    float dp[6], rhs[6];
+    bool ok;
+    if (!FANR) {
+      const float ratio = df / dg;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) rhs[a] = bfv[a] - ratio * (acc[a] - gm * sdsum[a]);
+      TS bb[6], xx[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) bb[a] = (TS)rhs[a];
+      chol6_solve<TS>(L, bb, xx);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) dp[a] = (float)(-xx[a]);
+      ok = true;
+    } else {
+      const float ratio = dg / df;
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+        rhs[a] = ratio * acc[27 + a] - (acc[21 + a] - gm * acc[33 + a]);
+      ok = solve6<TS>(acc, rhs, dp, false);
+      if (!ok) {
+        it_done = it;
+        st = kSingular;
+        break;
+      }
+    }
+    it_done = it;
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) fin = fin && isfinite(dp[a]);
+    if (!fin) {
+      st = kNonFinite;
+      break;
+    }
+    float pn[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) pn[a] = prm[a];
+    if (!FANR) {
+      compose_inverse(pn, dp);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 6; ++a) pn[a] += dp[a];
+    }
+    if (!corners_in(pn, x0, y0, M, W, H)) {
+      st = kOutOfBounds;
+      break;
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) prm[a] = pn[a];
+    const float nrm = sqrtf(dp[0] * dp[0] + dp[3] * dp[3] +
+                            m2 * (dp[1] * dp[1] + dp[2] * dp[2] + dp[4] * dp[4] + dp[5] * dp[5]));
+    if (nrm < p.tol) {
+      st = kOk;
+      break;
+    }
+  }
+
+  // ---- Eq. 1 at the returned shape
+  float s0 = 0.f, s1 = 0.f, sfg = 0.f;
+  {
+    PtWalk w(lane, S, M);
+    for (int i = lane; i < N; i += 32, w.next()) {
+      float tx, ty, gx, gy;
+      const size_t cell = locate(prm, w.dx, w.dy, x0, y0, W, H, tx, ty);
+      const float d = bicubic<false>(p.lut, plane, cell, tx, ty, gx, gy) - c;
+      s0 += d;
+      s1 = fmaf(d, d, s1);
+      sfg = fmaf(sfc[i], d, sfg);
+    }
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  sfg = warp_sum(sfg);
+  const float var = s1 - s0 * s0 * invN;
+  const float dgf = sqrtf(fmaxf(var, 0.f));
+  // sum fc (g - gbar) = sum fc (g - c) because sum fc = 0
+  const float zn = dgf > 0.f ? sfg / (df * dgf) : 0.f;
+  write_out(zn, it_done, st);
+}
+
+template <bool FANR, typename TS>
+cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
+  const size_t smem = (size_t)kWarpsPerCta * p.S * p.S * (sizeof(float2) + sizeof(float));
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const unsigned grid = (unsigned)((p.n_pois + kWarpsPerCta - 1) / kWarpsPerCta);
+  subpixel_kernel<FANR, TS><<<grid, 32 * kWarpsPerCta, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
+                            cudaStream_t st) {
+  if (p.n_pois == 0) return cudaSuccess;
+  if (method == DIC_ICGN)
+    return solve_fp64 ? launch_one<false, double>(p, st) : launch_one<false, float>(p, st);
+  return solve_fp64 ? launch_one<true, double>(p, st) : launch_one<true, float>(p, st);
+}
+
+}  // namespace dic

@@ -1,0 +1,96 @@
+"""The C ABI: every symbol declared in include/dic.h is exported by the
+library, the Python binding covers it, and host-side argument checking works
+without a GPU (no compute call is made here)."""
+import os
+import re
+
+import pytest
+
+import paper_1905_06228_gb300 as dic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(dic_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    dic.build()
+    return dic.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_declarations():
+    assert _declared() <= set(dic.SIGNATURES)
+
+
+def test_version(lib):
+    assert dic.dic_version() >= 10000
+
+
+@pytest.mark.parametrize("args", [
+    (4, 5, 10), (1, 5, 10), (65, 5, 10), (21, 0, 10), (21, 5, -1),
+])
+def test_create_rejects_bad_arguments(args):
+    with pytest.raises(dic.DICError) as e:
+        dic.dic_create(*args)
+    assert e.value.code == dic.DIC_ERR_ARG
+
+
+def test_create_rejects_bad_tolerance_and_iterations():
+    for tol, it in ((0.0, 50), (-1.0, 50), (1e-3, 0)):
+        with pytest.raises(dic.DICError):
+            dic.dic_create(21, 5, 10, 1, tol, it)
+
+
+def test_unsupported_shape_order():
+    with pytest.raises(dic.DICError) as e:
+        dic.dic_create(21, 5, 10, 2)
+    assert e.value.code == dic.DIC_ERR_UNSUPPORTED
+
+
+def test_state_errors_before_set_pair():
+    h = dic.dic_create(21, 5, 10)
+    try:
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_num_pois(h)
+        assert e.value.code == dic.DIC_ERR_STATE
+        assert "no image pair" in dic.dic_last_error(h)
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_integer_search(h, 0, 0, 0, 0)
+        assert e.value.code == dic.DIC_ERR_STATE
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_set_solve_precision(h, 16)
+        assert e.value.code == dic.DIC_ERR_ARG
+        dic.dic_set_solve_precision(h, 64)
+    finally:
+        dic.dic_destroy(h)
+
+
+def test_set_pair_rejects_null_and_bad_sizes():
+    lib = dic.lib()
+    h = dic.dic_create(21, 5, 10)
+    try:
+        assert lib.dic_set_pair(h, None, None, 64, 64, 64) == dic.DIC_ERR_ARG
+        assert lib.dic_set_pair(h, 16, 16, 2, 64, 64) == dic.DIC_ERR_ARG
+        assert lib.dic_set_pair(h, 16, 16, 64, 64, 32) == dic.DIC_ERR_ARG
+    finally:
+        dic.dic_destroy(h)
+
+
+def test_destroy_null_is_harmless():
+    dic.lib().dic_destroy(None)
