@@ -33,7 +33,8 @@ def test_rigid256_full(rigid256, method, solve_bits):
     ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
     assert gpu["n"] == 484
     compare_search(gpu, ref)
-    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method)
+    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method,
+                          min_compared=0.99)
     print(st)
 
 
@@ -51,7 +52,8 @@ def test_affine1024_sampled(affine1024, method):
     idx = np.unique(np.r_[idx, edge])
     ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx)
     compare_search(gpu, ref, idx)
-    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method, idx=idx)
+    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method, idx=idx,
+                          min_compared=0.99)
     print(st)
     # properties at every POI: integer start within the window, results finite
     assert (np.abs(gpu["u0"]) <= p.radius).all() and (np.abs(gpu["v0"]) <= p.radius).all()
@@ -60,9 +62,20 @@ def test_affine1024_sampled(affine1024, method):
 
 
 # --------------------------------------------------------------- edge cases
+def test_smallest_subset_search():
+    """Subset 3 (N = 9 < 32 lanes): integer search bit-exact.  The
+    6-parameter fit over 9 points is degenerate (on this input only 2 of 36
+    POIs converge, after ~20 iterations, at |grad u| ~ 0.8), so its sub-pixel
+    result is not a parity case."""
+    f, g = configs.tiny(1003, 24, 24, 17, Rigid(1.4, -0.7), noise=1.5)
+    gpu = run_gpu(f, g, 3, 3, 1, subpixel=False)
+    ref = oracle.integer_search(f, g, 3, 3, 1)
+    assert gpu["n"] == len(ref["u0"]) == 36
+    compare_search(gpu, ref)
+
+
 @pytest.mark.parametrize("subset,step,radius,size", [
-    (3, 3, 1, 24),      # smallest subset, N = 9 < 32 lanes
-    (5, 2, 3, 28),      # ragged: N = 25
+    (5, 2, 3, 28),      # ragged: N = 25 < 32 lanes
     (9, 4, 0, 40),      # R = 0: a single candidate
     (33, 9, 4, 96),     # N = 1089 > 1024: FP32 blocks flushed to int32
     (41, 12, 6, 120),
@@ -72,11 +85,12 @@ def test_affine1024_sampled(affine1024, method):
 def test_sizes(subset, step, radius, size):
     f, g = configs.tiny(1000 + subset, size, size, int(0.03 * size * size),
                         Rigid(1.4, -0.7), noise=1.5)
-    gpu = run_gpu(f, g, subset, step, radius, method=0)
+    gpu = run_gpu(f, g, subset, step, radius, method=0, solve_bits=64)
     ref = oracle.integer_search(f, g, subset, step, radius)
     assert gpu["n"] == len(ref["u0"]) > 0
     compare_search(gpu, ref)
-    compare_subpixel(gpu, f, g, subset, step, radius, ref, 0, min_iter_agreement=0.8)
+    st = compare_subpixel(gpu, f, g, subset, step, radius, ref, 0, min_iter_agreement=0.8)
+    print(subset, st)
 
 
 def test_unaligned_pitch_uses_plain_loads():
