@@ -259,9 +259,14 @@ def run_gpu(args):
     traffic = None
     prof = os.path.join(ROOT, "profiles", "search_affine1024_traffic.json")
     if os.path.exists(prof):
+        # counters apply only while the kernel source is the one they were taken on
         try:
-            traffic = json.load(open(prof)).get("bytes_per_launch")
-        except (OSError, ValueError):
+            import hashlib
+            meta = json.load(open(prof))
+            src = open(os.path.join(ROOT, meta["source"]), "rb").read()
+            if hashlib.sha256(src).hexdigest() == meta.get("source_sha256"):
+                traffic = meta.get("bytes_per_launch")
+        except (OSError, ValueError, KeyError):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
