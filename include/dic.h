@@ -142,6 +142,37 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int
                         float *vx, float *vy, float *zncc, int32_t *iters,
                         uint8_t *status);
 
+/* Sub-pixel refinement that allocates no device memory.  The paper has no
+ * counterpart; this call exists for callers that must not call cudaMalloc /
+ * cudaFree -- e.g. real-time acquisition loops that cannot absorb the device
+ * synchronisation those calls imply, or plug-ins whose host application owns
+ * the whole device-memory budget through its own allocator.
+ *
+ * Same arithmetic as dic_set_pair (precompute) followed by dic_subpixel, but
+ * without a handle: the bicubic table and gradient field go to one fixed
+ * array inside the library (a static device symbol of 4.5 MiB, held by every
+ * GPU that loads the library until the process exits).
+ *   - width * height must be <= 65536 pixels (e.g. 256 x 256); larger
+ *     images, and every other invalid argument, return DIC_ERR_ARG before any
+ *     GPU work is enqueued.  Other arguments as in dic_create / dic_set_pair /
+ *     dic_subpixel; solve_bits is 32 or 64; cuda_stream may be NULL.
+ *   - Allocates nothing: no cudaMalloc, no cudaFree, no library allocator.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  Later calls only enqueue two kernels.
+ *   - All calls share the one array.  Each call overwrites every entry it
+ *     reads, so no clearing is needed, but calls whose work overlaps on the
+ *     GPU (different streams, or host threads) race on the array: serialise
+ *     them, e.g. on one stream.
+ *   - Returns DIC_ERR_CUDA if a launch fails. */
+dic_status dic_subpixel_noalloc(const uint8_t *ref_dev, const uint8_t *def_dev, int width,
+                                int height, int pitch_bytes, int subset_size, int grid_step,
+                                int search_radius, dic_method method, float conv_tol,
+                                int max_iter, int solve_bits, const int32_t *u0,
+                                const int32_t *v0, const uint8_t *status0, float *u, float *v,
+                                float *ux, float *uy, float *vx, float *vy, float *zncc,
+                                int32_t *iters, uint8_t *status, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,8 @@ SIGNATURES = {
     "dic_num_pois": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "dic_subpixel_noalloc": (i32, [P, P, i32, i32, i32, i32, i32, i32, i32, f32, i32, i32,
+                                   P, P, P, P, P, P, P, P, P, P, P, P, P]),
 }
 
 
@@ -154,6 +156,22 @@ def dic_subpixel(h, method, u0, v0, status0, u, v, ux, uy, vx, vy, zncc, iters, 
     _check(lib().dic_subpixel(h, method, _ptr(u0), _ptr(v0), _ptr(status0), _ptr(u), _ptr(v),
                               _ptr(ux), _ptr(uy), _ptr(vx), _ptr(vy), _ptr(zncc), _ptr(iters),
                               _ptr(status)), h)
+
+
+def dic_subpixel_noalloc(ref, defm, subset_size, grid_step, search_radius, method, u0, v0,
+                         status0, u, v, ux, uy, vx, vy, zncc, iters, status, conv_tol=1e-3,
+                         max_iter=50, solve_bits=32, stream=None, width=None, height=None,
+                         pitch=None) -> None:
+    """Sub-pixel refinement with no device allocation (images up to 65536
+    pixels); see include/dic.h."""
+    hgt, wid = ref.shape[-2:]
+    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().dic_subpixel_noalloc(_ptr(ref), _ptr(defm), width or wid, height or hgt,
+                                      pitch or ref.stride(-2), subset_size, grid_step,
+                                      search_radius, method, conv_tol, max_iter, solve_bits,
+                                      _ptr(u0), _ptr(v0), _ptr(status0), _ptr(u), _ptr(v),
+                                      _ptr(ux), _ptr(uy), _ptr(vx), _ptr(vy), _ptr(zncc),
+                                      _ptr(iters), _ptr(status), C.c_void_p(sp)))
 
 
 # ------------------------------------------------------------ convenience
