@@ -120,6 +120,14 @@ dic_status dic_set_solve_precision(dic_t h, int bits);
 dic_status dic_set_pair(dic_t h, const uint8_t *ref_dev, const uint8_t *def_dev,
                         int width, int height, int pitch_bytes);
 
+/* Float variant of dic_set_pair for real-valued images (pitch in elements,
+ * 4-byte aligned).  It serves differentiation with respect to the deformed
+ * image (dic_backward) and sub-pixel refinement of float data;
+ * dic_integer_search needs 8-bit images (exact sums) and returns
+ * DIC_ERR_UNSUPPORTED on a float pair. */
+dic_status dic_set_pair_f32(dic_t h, const float *ref_dev, const float *def_dev, int width,
+                            int height, int pitch_elems);
+
 /* Grid size of the bound pair: n_pois = nx * ny (0 if the image is too
  * small for one POI).  Any output pointer may be NULL. */
 dic_status dic_num_pois(dic_t h, int *n_pois, int *nx, int *ny);
@@ -141,6 +149,26 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int
                         const uint8_t *status0, float *u, float *v, float *ux, float *uy,
                         float *vx, float *vy, float *zncc, int32_t *iters,
                         uint8_t *status);
+
+/* Summed ZNSSD of the subsets at given shapes: for POI k,
+ *   L_k = sum_i [ (f_i - fbar)/df - (g(W(xi_i; p_k)) - gbar)/dg ]^2 = 2 - 2 C_k,
+ * C_k being Eq. 1 at shape p_k with bicubically interpolated g.
+ *   p6            device [n_pois][6] shapes (u, ux, uy, v, vx, vy)
+ *   loss_per_poi  device [n_pois] or NULL
+ *   loss_total    device scalar (zeroed, then summed into) or NULL
+ * A POI whose warped subset leaves [1, W-2) x [1, H-2), or whose reference
+ * or target subset is flat, contributes 0. */
+dic_status dic_znssd(dic_t h, const float *p6, float *loss_per_poi, float *loss_total);
+
+/* Adjoint of dic_znssd with the shapes held fixed (the gradient does not go
+ * through the iterative solver): with upstream weight
+ * w_k = scale * (grad_loss ? grad_loss[k] : 1),
+ *   dL_ddef  device [height][width] dense, zeroed by the callee, receives
+ *            sum_k w_k dL_k/dg through the transposed bicubic stencil
+ *   dL_dp    device [n_pois][6] or NULL, receives w_k dL_k/dp_k.
+ * Float atomics accumulate dL_ddef, so its summation order is not fixed. */
+dic_status dic_backward(dic_t h, const float *p6, const float *grad_loss, float scale,
+                        float *dL_ddef, float *dL_dp);
 
 /* Sub-pixel refinement that allocates no device memory.  The paper has no
  * counterpart; this call exists for callers that must not call cudaMalloc /

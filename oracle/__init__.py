@@ -60,7 +60,7 @@ def _load():
             lib.dico_subpixel.restype = i32
             lib.dico_bicubic.argtypes = [P, i32, i32, i32, dbl, dbl, P, P]
             lib.dico_bicubic.restype = dbl
-            lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P]
+            lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P, P]
             lib.dico_znssd.restype = i32
             _lib = lib
     return _lib
@@ -153,9 +153,10 @@ def bicubic(img: np.ndarray, x: float, y: float) -> tuple[float, float, float]:
 
 
 def znssd(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, p: np.ndarray,
-          poi_idx=None, grad: bool = True):
+          poi_idx=None, grad: bool = True, per_poi: bool = False):
     """Summed ZNSSD at shape parameters ``p`` (n x 6) and, optionally, its
-    gradient with respect to every pixel of ``g`` and every row of ``p``."""
+    gradient with respect to every pixel of ``g`` and every row of ``p``
+    (and the per-POI losses)."""
     f = np.ascontiguousarray(f, np.float64)
     g = np.ascontiguousarray(g, np.float64)
     H, W = f.shape
@@ -167,9 +168,13 @@ def znssd(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, p: 
     loss = C.c_double()
     dg = np.zeros((H, W), np.float64) if grad else None
     dp = np.zeros((n, 6), np.float64) if grad else None
+    lp = np.zeros(n, np.float64) if per_poi else None
     rc = _load().dico_znssd(_ptr(f), _ptr(g), W, H, W, subset, step, radius, _ptr(idx),
-                            n if idx is not None else -1, _ptr(p), C.byref(loss),
+                            n if idx is not None else -1, _ptr(p), C.byref(loss), _ptr(lp),
                             _ptr(dg), _ptr(dp))
     if rc:
         raise ValueError("oracle znssd failed")
-    return (loss.value, dg, dp) if grad else loss.value
+    out = (loss.value, dg, dp) if grad else (loss.value,)
+    if per_poi:
+        out = out + (lp,)
+    return out if len(out) > 1 else out[0]

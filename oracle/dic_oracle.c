@@ -492,7 +492,8 @@ int dico_subpixel(const double *f, const double *g, int W, int H, int pitch, int
  * and dL/dg_i is spread onto the 4x4 pixels with the bicubic weights. */
 int dico_znssd(const double *f, const double *g, int W, int H, int pitch, int subset,
                int step, int R, const int64_t *poi_idx, int64_t n_idx,
-               const double *p, double *loss, double *dL_dg, double *dL_dp) {
+               const double *p, double *loss, double *loss_poi, double *dL_dg,
+               double *dL_dp) {
   int nx, ny;
   if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
   const int M = subset / 2, S = subset, N = S * S;
@@ -507,6 +508,7 @@ int dico_znssd(const double *f, const double *g, int W, int H, int pitch, int su
     const double *pk = &p[k * 6];
     if (dL_dp)
       for (int a = 0; a < 6; ++a) dL_dp[k * 6 + a] = 0.0;
+    if (loss_poi) loss_poi[k] = 0.0;
     if (!in_bounds(pk, x0, y0, M, W, H)) continue;
     double fs = 0;
     for (int i = 0; i < N; ++i) {
@@ -529,6 +531,7 @@ int dico_znssd(const double *f, const double *g, int W, int H, int pitch, int su
       C += (fc[i] / df) * ((gv[i] - gbar) / dg);
     }
     total += Lk;
+    if (loss_poi) loss_poi[k] = Lk;
     if (!dL_dg && !dL_dp) continue;
     for (int i = 0; i < N; ++i) {
       int dx = i % S - M, dy = i / S - M;

@@ -46,7 +46,10 @@ SIGNATURES = {
     "dic_set_form": (i32, [P, i32]),
     "dic_set_solve_precision": (i32, [P, i32]),
     "dic_set_pair": (i32, [P, P, P, i32, i32, i32]),
+    "dic_set_pair_f32": (i32, [P, P, P, i32, i32, i32]),
     "dic_num_pois": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    "dic_znssd": (i32, [P, P, P, P]),
+    "dic_backward": (i32, [P, P, P, f32, P, P]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
     "dic_subpixel_noalloc": (i32, [P, P, i32, i32, i32, i32, i32, i32, i32, f32, i32, i32,
@@ -140,6 +143,25 @@ def dic_set_pair(h, ref, defm, width: int | None = None, height: int | None = No
     hgt, wid = ref.shape[-2:]
     _check(lib().dic_set_pair(h, _ptr(ref), _ptr(defm), width or wid, height or hgt,
                               pitch or ref.stride(-2)), h)
+
+
+def dic_set_pair_f32(h, ref, defm, width: int | None = None, height: int | None = None,
+                     pitch: int | None = None) -> None:
+    import torch
+    if ref.dtype != torch.float32 or defm.dtype != torch.float32:
+        raise RuntimeError("images must be float32")
+    hgt, wid = ref.shape[-2:]
+    _check(lib().dic_set_pair_f32(h, _ptr(ref), _ptr(defm), width or wid, height or hgt,
+                                  pitch or ref.stride(-2)), h)
+
+
+def dic_znssd(h, p6, loss_per_poi=None, loss_total=None) -> None:
+    _check(lib().dic_znssd(h, _ptr(p6), _ptr(loss_per_poi), _ptr(loss_total)), h)
+
+
+def dic_backward(h, p6, grad_loss, scale: float, dL_ddef, dL_dp=None) -> None:
+    _check(lib().dic_backward(h, _ptr(p6), _ptr(grad_loss), scale, _ptr(dL_ddef), _ptr(dL_dp)),
+           h)
 
 
 def dic_num_pois(h) -> tuple[int, int, int]:
@@ -239,3 +261,50 @@ class DIC:
         r = self.subpixel(s, method)
         r.update(s)
         return r
+
+
+# ------------------------------------------------------ differentiation
+def _autograd():
+    import torch
+
+    class ZNSSD(torch.autograd.Function):
+        """Summed ZNSSD of every subset at shapes ``p`` (n_pois x 6) over the
+        float deformed image ``g``; gradients with respect to ``g`` (through
+        the bicubic interpolation) and ``p`` come from the library's adjoint
+        kernel.  ``f`` is the fixed reference image."""
+
+        @staticmethod
+        def forward(ctx, g, p, f, h):
+            g = g.contiguous()
+            p = p.contiguous()
+            dic_set_pair_f32(h, f, g)
+            total = torch.empty((), dtype=torch.float32, device=g.device)
+            dic_znssd(h, p, None, total)
+            ctx.save_for_backward(g, p, f)
+            ctx.h = h
+            return total
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g, p, f = ctx.saved_tensors
+            h = ctx.h
+            dic_set_pair_f32(h, f, g)
+            n = p.shape[0]
+            w = grad_out.reshape(1).expand(n).contiguous()
+            dg = torch.empty_like(g)
+            dp = torch.empty_like(p)
+            dic_backward(h, p, w, 1.0, dg, dp)
+            return dg, dp, None, None
+
+    return ZNSSD
+
+
+_ZNSSD = None
+
+
+def znssd_loss(g, p, f, h):
+    """Differentiable summed ZNSSD (torch.autograd.Function over the C ABI)."""
+    global _ZNSSD
+    if _ZNSSD is None:
+        _ZNSSD = _autograd()
+    return _ZNSSD.apply(g, p, f, h)

@@ -134,8 +134,14 @@ dic_status dic_set_solve_precision(dic_t h, int bits) {
   return DIC_OK;
 }
 
-dic_status dic_set_pair(dic_t h, const uint8_t* ref, const uint8_t* def, int width, int height,
-                        int pitch) {
+}  // extern "C"
+
+namespace {
+
+// Common part of dic_set_pair / dic_set_pair_f32: geometry, scratch, and the
+// precompute launch.
+dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int width, int height,
+                     int pitch) {
   if (!h) return DIC_ERR_ARG;
   h->have_pair = false;
   if (!ref || !def) return fail(h, DIC_ERR_ARG, "null image pointer");
@@ -166,26 +172,97 @@ dic_status dic_set_pair(dic_t h, const uint8_t* ref, const uint8_t* def, int wid
     }
     cudaMemsetAsync(h->err_flag, 0, sizeof(unsigned int), h->stream);
   }
-  h->ref = ref;
-  h->def = def;
   h->g.W = width;
   h->g.H = height;
   h->g.pitch = pitch;
   h->g.nx = nx;
   h->g.ny = ny;
   h->g.n_pois = (int64_t)nx * ny;
-  // TMA staging needs 16-byte aligned bases and pitch, and boxes <= 256.
-  const int span = h->subset + 2 * h->R;
-  const int bwg = dic::tma_box_width(span), bwf = dic::tma_box_width(h->subset);
-  h->tma_ok = ((uintptr_t)ref % 16 == 0) && ((uintptr_t)def % 16 == 0) && (pitch % 16 == 0) &&
-              bwg <= 256 && span <= 256 &&
-              encode_u8(&h->tm_def, def, width, height, pitch, bwg, span) &&
-              encode_u8(&h->tm_ref, ref, width, height, pitch, bwf, h->subset);
-  cudaError_t e = dic::launch_precompute(ref, def, width, height, pitch, h->grad, h->lut,
-                                         h->stream);
+  cudaError_t e;
+  if (f32) {
+    h->ref = h->def = nullptr;
+    h->ref_f32 = static_cast<const float*>(ref);
+    h->def_f32 = static_cast<const float*>(def);
+    h->tma_ok = false;
+    e = dic::launch_precompute_f32(h->ref_f32, h->def_f32, width, height, pitch, h->grad, h->lut,
+                                   h->stream);
+  } else {
+    h->ref_f32 = h->def_f32 = nullptr;
+    h->ref = static_cast<const uint8_t*>(ref);
+    h->def = static_cast<const uint8_t*>(def);
+    // TMA staging needs 16-byte aligned bases and pitch, and boxes <= 256.
+    const int span = h->subset + 2 * h->R;
+    const int bwg = dic::tma_box_width(span), bwf = dic::tma_box_width(h->subset);
+    h->tma_ok = ((uintptr_t)ref % 16 == 0) && ((uintptr_t)def % 16 == 0) && (pitch % 16 == 0) &&
+                bwg <= 256 && span <= 256 &&
+                encode_u8(&h->tm_def, h->def, width, height, pitch, bwg, span) &&
+                encode_u8(&h->tm_ref, h->ref, width, height, pitch, bwf, h->subset);
+    e = dic::launch_precompute(h->ref, h->def, width, height, pitch, h->grad, h->lut, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "precompute launch");
   h->have_pair = true;
   return DIC_OK;
+}
+
+dic_status run_adjoint(dic_t h, const float* p6, float* loss_poi, float* loss_total, int backward,
+                       const float* grad_loss, float scale, float* dL_ddef, float* dL_dp) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->g.n_pois > 0 && !p6) return fail(h, DIC_ERR_ARG, "null shape array");
+  if (backward && !dL_ddef) return fail(h, DIC_ERR_ARG, "null image gradient");
+  if (loss_total) cudaMemsetAsync(loss_total, 0, sizeof(float), h->stream);
+  if (backward)
+    cudaMemsetAsync(dL_ddef, 0, sizeof(float) * (size_t)h->g.W * h->g.H, h->stream);
+  if (h->g.n_pois == 0) return DIC_OK;
+  dic::AdjointParams p;
+  p.ref = h->ref;
+  p.ref_f32 = h->ref_f32;
+  p.lut = h->lut;
+  p.W = h->g.W;
+  p.H = h->g.H;
+  p.pitch = h->g.pitch;
+  p.S = h->subset;
+  p.M = h->M;
+  p.R = h->R;
+  p.step = h->step;
+  p.nx = h->g.nx;
+  p.n_pois = h->g.n_pois;
+  p.p6 = p6;
+  p.loss_poi = loss_poi;
+  p.loss_total = loss_total;
+  p.backward = backward;
+  p.grad_loss = grad_loss;
+  p.scale = scale;
+  p.dL_ddef = dL_ddef;
+  p.dL_dp = dL_dp;
+  cudaError_t e = dic::launch_adjoint(p, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint launch");
+  return DIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dic_status dic_set_pair(dic_t h, const uint8_t* ref, const uint8_t* def, int width, int height,
+                        int pitch) {
+  return bind_pair(h, ref, def, false, width, height, pitch);
+}
+
+dic_status dic_set_pair_f32(dic_t h, const float* ref, const float* def, int width, int height,
+                            int pitch_elems) {
+  if (h && (((uintptr_t)ref | (uintptr_t)def) % 4 != 0))
+    return fail(h, DIC_ERR_ARG, "float images must be 4-byte aligned");
+  return bind_pair(h, ref, def, true, width, height, pitch_elems);
+}
+
+dic_status dic_znssd(dic_t h, const float* p6, float* loss_per_poi, float* loss_total) {
+  return run_adjoint(h, p6, loss_per_poi, loss_total, 0, nullptr, 0.f, nullptr, nullptr);
+}
+
+dic_status dic_backward(dic_t h, const float* p6, const float* grad_loss, float scale,
+                        float* dL_ddef, float* dL_dp) {
+  return run_adjoint(h, p6, nullptr, nullptr, 1, grad_loss, scale, dL_ddef, dL_dp);
 }
 
 dic_status dic_num_pois(dic_t h, int* n_pois, int* nx, int* ny) {
@@ -201,6 +278,8 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
                               uint8_t* status) {
   if (!h) return DIC_ERR_ARG;
   if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->ref_f32)
+    return fail(h, DIC_ERR_UNSUPPORTED, "integer search needs an 8-bit pair (exact sums)");
   if (h->g.n_pois == 0) return DIC_OK;
   if (!u0 || !v0 || !zncc0 || !status) return fail(h, DIC_ERR_ARG, "null output pointer");
   if (dic::search_smem_bytes(h->subset, h->R) > 227 * 1024)
@@ -240,6 +319,7 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int
     return fail(h, DIC_ERR_ARG, "null pointer");
   dic::SubpixelParams p;
   p.ref = h->ref;
+  p.ref_f32 = h->ref_f32;
   p.grad = h->grad;
   p.lut = h->lut;
   p.W = h->g.W;

@@ -47,9 +47,11 @@ struct SearchParams {
   unsigned int* err_flag;  // set when a bounded wait gives up
 };
 
-// Parameters of the sub-pixel kernels.
+// Parameters of the sub-pixel kernels.  The reference image is 8-bit
+// (ref) or float (ref_f32 != nullptr); pitch is in elements.
 struct SubpixelParams {
-  const uint8_t* ref;
+  const uint8_t* ref = nullptr;
+  const float* ref_f32 = nullptr;
   const float2* grad;  // central-difference gradients of f, W*H
   const float4* lut;   // bicubic coefficient planes of g, 4*W*H
   int W, H, pitch;
@@ -71,9 +73,30 @@ struct SubpixelParams {
   uint8_t* status;
 };
 
+// Parameters of the ZNSSD forward / adjoint kernel.
+struct AdjointParams {
+  const uint8_t* ref = nullptr;
+  const float* ref_f32 = nullptr;
+  const float4* lut;
+  int W, H, pitch;
+  int S, M, R, step, nx;
+  int64_t n_pois;
+  const float* p6;          // [n_pois][6]
+  float* loss_poi;          // may be null
+  float* loss_total;        // may be null (zeroed by the caller)
+  int backward;             // 0: forward only
+  const float* grad_loss;   // [n_pois] upstream weights or null (= 1)
+  float scale;
+  float* dL_ddef;           // [H][W], zeroed by the caller
+  float* dL_dp;             // [n_pois][6] or null
+};
+
 // Launchers (each returns the cudaError_t of its launch).
 cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int H,
                               int pitch, float2* grad, float4* lut, cudaStream_t st);
+cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int H,
+                                  int pitch, float2* grad, float4* lut, cudaStream_t st);
+cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
 cudaError_t launch_search(const SearchParams& p, const CUtensorMap* tm_ref,
                           const CUtensorMap* tm_def, cudaStream_t st);
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
@@ -94,6 +117,8 @@ struct dic_s {
   bool have_pair = false;
   const uint8_t* ref = nullptr;
   const uint8_t* def = nullptr;
+  const float* ref_f32 = nullptr;  // set instead of ref/def for float pairs
+  const float* def_f32 = nullptr;
   dic::PairGeom g;
 
   float4* lut = nullptr;

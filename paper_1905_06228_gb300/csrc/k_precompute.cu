@@ -17,6 +17,9 @@
 //                  the Keys a = -1/2 weights; valid cells 1 <= x <= W-3,
 //                  1 <= y <= H-3, zero elsewhere.
 //
+// Pixels are 8-bit or float (the float form serves differentiation with
+// respect to real-valued deformed-image pixels); pitch is in elements.
+//
 // Bytes per pixel: 1 (f) + 1 (g) read, 8 (grad) + 64 (lut) written.  Each
 // warp writes 32 consecutive float4 of one plane per store (512 B), so every
 // store is a full-line coalesced write.
@@ -38,8 +41,9 @@ __device__ __forceinline__ void keys_basis(float K[4][4]) {
   K[3][0] = -0.5f; K[3][1] = 1.5f;  K[3][2] = -1.5f; K[3][3] = 0.5f;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(TX* BY)
-precompute_kernel(const uint8_t* __restrict__ ref, const uint8_t* __restrict__ def, int W,
+precompute_kernel(const T* __restrict__ ref, const T* __restrict__ def, int W,
                   int H, int pitch, float2* __restrict__ grad, float4* __restrict__ lut) {
   __shared__ float sg[TY + 3][TX + 4];  // g rows y0-1 .. y0+TY+1, cols x0-1 .. x0+TX+2
   __shared__ float sf[TY + 2][TX + 3];  // f rows y0-1 .. y0+TY,   cols x0-1 .. x0+TX
@@ -109,7 +113,15 @@ cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int
                               float2* grad, float4* lut, cudaStream_t st) {
   dim3 block(TX, BY);
   dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
-  precompute_kernel<<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, lut);
+  precompute_kernel<uint8_t><<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, lut);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int H, int pitch,
+                                  float2* grad, float4* lut, cudaStream_t st) {
+  dim3 block(TX, BY);
+  dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
+  precompute_kernel<float><<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, lut);
   return cudaGetLastError();
 }
 

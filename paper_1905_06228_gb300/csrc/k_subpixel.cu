@@ -22,18 +22,13 @@
 // right-hand side follow exactly as in the formulas above.  The 6x6 solve is
 // FP32 or FP64 (Cholesky), chosen per launch.  The final ZNCC is Eq. 1 at
 // the returned shape (one extra pass).
+#include "dic_device.cuh"
 #include "dic_internal.cuh"
 
 namespace dic {
 namespace {
 
 constexpr int kWarpsPerCta = 4;
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Cholesky factorisation of a symmetric 6x6 (lower part used), in place.
 template <typename T>
@@ -75,74 +70,6 @@ __device__ __forceinline__ void chol6_solve(const T L[6][6], const T b[6], T x[6
     for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
     x[i] = s / L[i][i];
   }
-}
-
-// Bicubic value (and optionally derivatives) from one table cell.
-template <bool DERIV>
-__device__ __forceinline__ float bicubic(const float4* __restrict__ lut, size_t plane,
-                                         size_t cell, float tx, float ty, float& gx, float& gy) {
-  const float4 a0 = __ldg(lut + cell), a1 = __ldg(lut + plane + cell),
-               a2 = __ldg(lut + 2 * plane + cell), a3 = __ldg(lut + 3 * plane + cell);
-  const float r0 = fmaf(fmaf(fmaf(a0.w, tx, a0.z), tx, a0.y), tx, a0.x);
-  const float r1 = fmaf(fmaf(fmaf(a1.w, tx, a1.z), tx, a1.y), tx, a1.x);
-  const float r2 = fmaf(fmaf(fmaf(a2.w, tx, a2.z), tx, a2.y), tx, a2.x);
-  const float r3 = fmaf(fmaf(fmaf(a3.w, tx, a3.z), tx, a3.y), tx, a3.x);
-  if (DERIV) {
-    const float d0 = fmaf(fmaf(3.f * a0.w, tx, 2.f * a0.z), tx, a0.y);
-    const float d1 = fmaf(fmaf(3.f * a1.w, tx, 2.f * a1.z), tx, a1.y);
-    const float d2 = fmaf(fmaf(3.f * a2.w, tx, 2.f * a2.z), tx, a2.y);
-    const float d3 = fmaf(fmaf(3.f * a3.w, tx, 2.f * a3.z), tx, a3.y);
-    gx = fmaf(fmaf(fmaf(d3, ty, d2), ty, d1), ty, d0);
-    gy = fmaf(fmaf(3.f * r3, ty, 2.f * r2), ty, r1);
-  }
-  return fmaf(fmaf(fmaf(r3, ty, r2), ty, r1), ty, r0);
-}
-
-// Subset point walk of one lane: points i = lane, lane+32, ... in row-major
-// (dy outer) order, with (dx, dy) advanced incrementally.
-struct PtWalk {
-  int dx, dy, ddx, ddy, S, M;
-  __device__ __forceinline__ PtWalk(int lane, int S_, int M_) : S(S_), M(M_) {
-    dy = lane / S - M;
-    dx = lane % S - M;
-    ddy = 32 / S;
-    ddx = 32 % S;
-  }
-  __device__ __forceinline__ void next() {
-    dx += ddx;
-    dy += ddy;
-    if (dx > M) {
-      dx -= S;
-      dy += 1;
-    }
-  }
-};
-
-// Location of a warped point: table cell and fractional offsets.
-__device__ __forceinline__ size_t locate(const float p[6], int dx, int dy, int x0, int y0, int W,
-                                         int H, float& tx, float& ty) {
-  const float lx = fmaf(p[2], (float)dy, fmaf(1.f + p[1], (float)dx, p[0]));
-  const float ly = fmaf(1.f + p[5], (float)dy, fmaf(p[4], (float)dx, p[3]));
-  const float fx = floorf(lx), fy = floorf(ly);
-  tx = lx - fx;
-  ty = ly - fy;
-  int ix = x0 + (int)fx, iy = y0 + (int)fy;
-  ix = min(max(ix, 1), W - 3);  // memory safety only; bounds are checked on p
-  iy = min(max(iy, 1), H - 3);
-  return (size_t)iy * W + ix;
-}
-
-__device__ __forceinline__ bool corners_in(const float p[6], int x0, int y0, int M, int W, int H) {
-  bool ok = true;
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const float cx = (c & 1) ? (float)M : -(float)M, cy = (c & 2) ? (float)M : -(float)M;
-    const float lx = fmaf(p[2], cy, fmaf(1.f + p[1], cx, p[0]));
-    const float ly = fmaf(1.f + p[5], cy, fmaf(p[4], cx, p[3]));
-    const float x = (float)x0 + lx, y = (float)y0 + ly;
-    ok = ok && (x >= 1.f) && (x < (float)(W - 2)) && (y >= 1.f) && (y < (float)(H - 2));
-  }
-  return ok;
 }
 
 // W(p) <- W(p) W(dp)^-1 for the first-order warp.
@@ -189,7 +116,18 @@ __device__ __forceinline__ bool solve6(const float Hf[21], const float bf[6], fl
   return true;
 }
 
-template <bool FANR, typename TS>
+template <typename T>
+__device__ __forceinline__ const T* ref_ptr(const SubpixelParams& p);
+template <>
+__device__ __forceinline__ const uint8_t* ref_ptr<uint8_t>(const SubpixelParams& p) {
+  return p.ref;
+}
+template <>
+__device__ __forceinline__ const float* ref_ptr<float>(const SubpixelParams& p) {
+  return p.ref_f32;
+}
+
+template <bool FANR, typename TS, typename TP>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 subpixel_kernel(const SubpixelParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -231,7 +169,7 @@ subpixel_kernel(const SubpixelParams p) {
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
       const int x = x0 + w.dx, y = y0 + w.dy;
-      const float f = (float)p.ref[(size_t)y * p.pitch + x];
+      const float f = (float)ref_ptr<TP>(p)[(size_t)y * p.pitch + x];
       sgrad[i] = p.grad[(size_t)y * W + x];
       sfc[i] = f;
       fsum += f;
@@ -437,17 +375,17 @@ subpixel_kernel(const SubpixelParams p) {
   write_out(zn, it_done, st);
 }
 
-template <bool FANR, typename TS>
+template <bool FANR, typename TS, typename TP>
 cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
   const size_t smem = (size_t)kWarpsPerCta * p.S * p.S * (sizeof(float2) + sizeof(float));
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS>,
+    cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS, TP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const unsigned grid = (unsigned)((p.n_pois + kWarpsPerCta - 1) / kWarpsPerCta);
-  subpixel_kernel<FANR, TS><<<grid, 32 * kWarpsPerCta, smem, st>>>(p);
+  subpixel_kernel<FANR, TS, TP><<<grid, 32 * kWarpsPerCta, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -456,9 +394,18 @@ cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
                             cudaStream_t st) {
   if (p.n_pois == 0) return cudaSuccess;
+  if (p.ref_f32) {
+    if (method == DIC_ICGN)
+      return solve_fp64 ? launch_one<false, double, float>(p, st)
+                        : launch_one<false, float, float>(p, st);
+    return solve_fp64 ? launch_one<true, double, float>(p, st)
+                      : launch_one<true, float, float>(p, st);
+  }
   if (method == DIC_ICGN)
-    return solve_fp64 ? launch_one<false, double>(p, st) : launch_one<false, float>(p, st);
-  return solve_fp64 ? launch_one<true, double>(p, st) : launch_one<true, float>(p, st);
+    return solve_fp64 ? launch_one<false, double, uint8_t>(p, st)
+                      : launch_one<false, float, uint8_t>(p, st);
+  return solve_fp64 ? launch_one<true, double, uint8_t>(p, st)
+                    : launch_one<true, float, uint8_t>(p, st);
 }
 
 }  // namespace dic
