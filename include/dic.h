@@ -150,6 +150,57 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int
                         float *vx, float *vy, float *zncc, int32_t *iters,
                         uint8_t *status);
 
+/* ---------------------------------------------------------------- batches
+ * Many image pairs of uneven size in one go -- the GPU form of the paper's
+ * "image parallel" mode (Section 2.3, Table 6), where whole pairs are
+ * processed concurrently. */
+typedef struct {
+  const uint8_t *ref_dev;  /* device, borrowed (as dic_set_pair)             */
+  const uint8_t *def_dev;
+  int width, height, pitch_bytes;
+  int subset_size;         /* odd 3..63, or <= 0 for the handle's value      */
+  int grid_step;           /* >= 1, or <= 0 for the handle's value           */
+  int search_radius;       /* >= 0, or < 0 for the handle's value            */
+} dic_pair_desc;
+
+/* Outputs of a batch: device arrays of total_pois elements; the POIs of pair
+ * k occupy [offsets[k], offsets[k+1]) (see dic_batch_pois), each pair's in
+ * its own grid order.  Integer-search outputs and sub-pixel outputs as in
+ * dic_integer_search / dic_subpixel. */
+typedef struct {
+  int32_t *u0, *v0;
+  float *zncc0;
+  uint8_t *status0;
+  float *u, *v, *ux, *uy, *vx, *vy, *zncc;
+  int32_t *iters;
+  uint8_t *status;
+} dic_batch_out;
+
+/* Bind n_pairs pairs (host array of descriptors, copied).  Allocates the
+ * scratch of every pair (72 bytes per pixel in total; DIC_ERR_OOM on
+ * failure) and validates every descriptor (DIC_ERR_ARG); a pair whose search
+ * window does not fit in shared memory returns DIC_ERR_UNSUPPORTED naming it
+ * in dic_last_error.  Replaces any earlier batch. */
+dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc *descs);
+
+/* Total POIs of the bound batch and, if offsets is not NULL, the host array
+ * of n_pairs + 1 prefix offsets. */
+dic_status dic_batch_pois(dic_t h, int64_t *total, int64_t *offsets);
+
+/* Run precompute, integer search and sub-pixel refinement of the whole batch
+ * as one CUDA graph on the handle's stream: per-pair precompute launches,
+ * then persistent search kernels (one per subset-width class) and one
+ * persistent sub-pixel kernel whose warps take POIs from a global counter.
+ * The graph is built on the first call and rebuilt when method, outputs or
+ * tuning change; later calls only launch it.  Requires dic_set_pairs. */
+dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out *out);
+
+/* Time the batch under each candidate launch shape (sub-pixel warps per CTA
+ * 2/4/8 x persistent grid 1x/2x the resident CTAs) and keep the fastest for
+ * later dic_run_batch calls.  Runs the batch several times (outputs are
+ * overwritten).  chosen (may be NULL) receives {warps_per_cta, grid_mult}. */
+dic_status dic_autotune(dic_t h, dic_method method, const dic_batch_out *out, int *chosen);
+
 /* Summed ZNSSD of the subsets at given shapes: for POI k,
  *   L_k = sum_i [ (f_i - fbar)/df - (g(W(xi_i; p_k)) - gbar)/dg ]^2 = 2 - 2 C_k,
  * C_k being Eq. 1 at shape p_k with bicubically interpolated g.

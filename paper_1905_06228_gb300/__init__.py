@@ -36,6 +36,17 @@ P = C.c_void_p
 i32 = C.c_int
 f32 = C.c_float
 
+class dic_pair_desc(C.Structure):
+    _fields_ = [("ref_dev", P), ("def_dev", P), ("width", i32), ("height", i32),
+                ("pitch_bytes", i32), ("subset_size", i32), ("grid_step", i32),
+                ("search_radius", i32)]
+
+
+class dic_batch_out(C.Structure):
+    _fields_ = [(n, P) for n in ("u0", "v0", "zncc0", "status0", "u", "v", "ux", "uy", "vx", "vy",
+                                 "zncc", "iters", "status")]
+
+
 # name -> (restype, argtypes); mirrors include/dic.h
 SIGNATURES = {
     "dic_version": (i32, []),
@@ -49,6 +60,10 @@ SIGNATURES = {
     "dic_set_pair_f32": (i32, [P, P, P, i32, i32, i32]),
     "dic_num_pois": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "dic_znssd": (i32, [P, P, P, P]),
+    "dic_set_pairs": (i32, [P, i32, C.POINTER(dic_pair_desc)]),
+    "dic_batch_pois": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "dic_run_batch": (i32, [P, i32, C.POINTER(dic_batch_out)]),
+    "dic_autotune": (i32, [P, i32, C.POINTER(dic_batch_out), C.POINTER(i32)]),
     "dic_backward": (i32, [P, P, P, f32, P, P]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -162,6 +177,54 @@ def dic_znssd(h, p6, loss_per_poi=None, loss_total=None) -> None:
 def dic_backward(h, p6, grad_loss, scale: float, dL_ddef, dL_dp=None) -> None:
     _check(lib().dic_backward(h, _ptr(p6), _ptr(grad_loss), scale, _ptr(dL_ddef), _ptr(dL_dp)),
            h)
+
+
+def dic_set_pairs(h, pairs) -> None:
+    """pairs: sequence of (ref, def) 8-bit device tensors or
+    (ref, def, subset, step, radius) tuples."""
+    arr = (dic_pair_desc * len(pairs))()
+    for k, pr in enumerate(pairs):
+        ref, defm = pr[0], pr[1]
+        subset, step, radius = (pr[2], pr[3], pr[4]) if len(pr) > 2 else (0, 0, -1)
+        hgt, wid = ref.shape[-2:]
+        arr[k] = dic_pair_desc(_ptr(ref), _ptr(defm), wid, hgt, ref.stride(-2), subset, step,
+                               radius)
+    _check(lib().dic_set_pairs(h, len(pairs), arr), h)
+
+
+def dic_batch_pois(h, n_pairs: int):
+    total = C.c_int64()
+    offs = (C.c_int64 * (n_pairs + 1))()
+    _check(lib().dic_batch_pois(h, C.byref(total), offs), h)
+    return total.value, list(offs)
+
+
+def _batch_out(out: dict) -> dic_batch_out:
+    return dic_batch_out(*[_ptr(out[k]) for k in ("u0", "v0", "zncc0", "status0", "u", "v",
+                                                  "ux", "uy", "vx", "vy", "zncc", "iters",
+                                                  "status")])
+
+
+def dic_run_batch(h, method: int, out: dict) -> None:
+    o = _batch_out(out)
+    _check(lib().dic_run_batch(h, method, C.byref(o)), h)
+
+
+def dic_autotune(h, method: int, out: dict) -> tuple[int, int]:
+    o = _batch_out(out)
+    chosen = (i32 * 2)()
+    _check(lib().dic_autotune(h, method, C.byref(o), chosen), h)
+    return chosen[0], chosen[1]
+
+
+def batch_outputs(total: int, device):
+    import torch
+    out = {k: torch.empty(total, dtype=torch.int32, device=device) for k in ("u0", "v0", "iters")}
+    for k in ("zncc0", "u", "v", "ux", "uy", "vx", "vy", "zncc"):
+        out[k] = torch.empty(total, dtype=torch.float32, device=device)
+    for k in ("status0", "status"):
+        out[k] = torch.empty(total, dtype=torch.uint8, device=device)
+    return out
 
 
 def dic_num_pois(h) -> tuple[int, int, int]:

@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "dic_internal.cuh"
@@ -101,8 +102,33 @@ dic_status dic_create(dic_t* out, int subset_size, int grid_step, int search_rad
   return DIC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+void free_batch(dic::BatchState* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->lut) cudaFree(b->lut);
+  if (b->grad) cudaFree(b->grad);
+  if (b->d_pjobs) cudaFree(b->d_pjobs);
+  if (b->d_offsets) cudaFree(b->d_offsets);
+  if (b->d_counters) cudaFree(b->d_counters);
+  for (auto& c : b->classes) {
+    if (c.d_jobs) cudaFree(c.d_jobs);
+    if (c.d_offsets) cudaFree(c.d_offsets);
+  }
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
 void dic_destroy(dic_t h) {
   if (!h) return;
+  free_batch(h->batch);
   if (h->lut) cudaFree(h->lut);
   if (h->grad) cudaFree(h->grad);
   if (h->err_flag) cudaFree(h->err_flag);
@@ -348,6 +374,313 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int
   cudaError_t e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "subpixel launch");
   return DIC_OK;
+}
+
+// ------------------------------------------------------------------ batches
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(dst, sizeof(T) * v.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+// Fill the per-pair job arrays for the given outputs and copy them to the
+// device (synchronous; done only when the graph is rebuilt).
+dic_status write_jobs(dic_t h, const dic_batch_out& o, int solve_bits) {
+  dic::BatchState* b = h->batch;
+  std::vector<dic::SubpixelParams> pj(b->pairs.size());
+  for (size_t k = 0; k < b->pairs.size(); ++k) {
+    const dic::BatchPair& bp = b->pairs[k];
+    dic::SubpixelParams& p = pj[k];
+    p.ref = bp.d.ref_dev;
+    p.grad = b->grad + bp.px_off;
+    p.lut = b->lut + 4 * bp.px_off;
+    p.W = bp.d.width;
+    p.H = bp.d.height;
+    p.pitch = bp.d.pitch_bytes;
+    p.S = bp.S;
+    p.M = bp.M;
+    p.R = bp.R;
+    p.step = bp.step;
+    p.nx = bp.nx;
+    p.n_pois = bp.n;
+    p.max_iter = h->max_iter;
+    p.tol = h->tol;
+    p.u0 = o.u0 + bp.off;
+    p.v0 = o.v0 + bp.off;
+    p.st0 = o.status0 + bp.off;
+    p.u = o.u + bp.off;
+    p.v = o.v + bp.off;
+    p.ux = o.ux + bp.off;
+    p.uy = o.uy + bp.off;
+    p.vx = o.vx + bp.off;
+    p.vy = o.vy + bp.off;
+    p.zncc = o.zncc + bp.off;
+    p.iters = o.iters + bp.off;
+    p.status = o.status + bp.off;
+  }
+  if (cudaMemcpy(b->d_pjobs, pj.data(), sizeof(dic::SubpixelParams) * pj.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(h, DIC_ERR_CUDA, "job upload failed");
+  for (auto& c : b->classes) {
+    std::vector<dic::SearchParams> sj;
+    for (int k : c.pairs) {
+      const dic::BatchPair& bp = b->pairs[k];
+      dic::SearchParams q{};
+      q.ref = bp.d.ref_dev;
+      q.def = bp.d.def_dev;
+      q.W = bp.d.width;
+      q.H = bp.d.height;
+      q.pitch = bp.d.pitch_bytes;
+      q.S = bp.S;
+      q.M = bp.M;
+      q.R = bp.R;
+      q.step = bp.step;
+      q.nx = bp.nx;
+      q.n_pois = bp.n;
+      q.use_tma = 0;
+      q.u0 = o.u0 + bp.off;
+      q.v0 = o.v0 + bp.off;
+      q.zncc0 = o.zncc0 + bp.off;
+      q.status = o.status0 + bp.off;
+      q.err_flag = h->err_flag;
+      sj.push_back(q);
+    }
+    if (cudaMemcpy(c.d_jobs, sj.data(), sizeof(dic::SearchParams) * sj.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(h, DIC_ERR_CUDA, "job upload failed");
+  }
+  (void)solve_bits;
+  return DIC_OK;
+}
+
+dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
+  dic::BatchState* b = h->batch;
+  dic_status st = write_jobs(h, o, h->solve_bits);
+  if (st != DIC_OK) return st;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaStream_t cs = b->cap;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+  cudaError_t le = cudaMemsetAsync(b->d_counters, 0,
+                                   sizeof(unsigned long long) * (b->classes.size() + 1), cs);
+  for (const dic::BatchPair& bp : b->pairs) {
+    if (le != cudaSuccess) break;
+    le = dic::launch_precompute(bp.d.ref_dev, bp.d.def_dev, bp.d.width, bp.d.height,
+                                bp.d.pitch_bytes, b->grad + bp.px_off, b->lut + 4 * bp.px_off,
+                                cs);
+  }
+  for (size_t c = 0; c < b->classes.size() && le == cudaSuccess; ++c) {
+    dic::BatchClass& cl = b->classes[c];
+    int occ = dic::search_batch_occupancy(cl.tw, cl.smem);
+    int64_t items = 0;
+    for (int k : cl.pairs) items += b->pairs[k].n;
+    int64_t grid = (int64_t)(occ > 0 ? occ : 1) * sms * b->grid_mult;
+    if (grid > items) grid = items;
+    if (grid < 1) grid = 1;
+    le = dic::launch_search_batch(cl.tw, cl.d_jobs, cl.d_offsets, (int)cl.pairs.size(),
+                                  b->d_counters + c, cl.smem, (int)grid, cs);
+  }
+  if (le == cudaSuccess) {
+    // grid <= 0 asks the launcher for (resident CTAs x SMs) x -grid
+    le = dic::launch_subpixel_batch(b->d_pjobs, b->d_offsets, (int)b->pairs.size(), b->nmax,
+                                    (int)method, h->solve_bits == 64, b->wpc,
+                                    b->d_counters + b->classes.size(), -b->grid_mult, cs);
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, le, "batch launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph capture end");
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+  b->last_out = o;
+  b->last_method = (int)method;
+  b->last_wpc = b->wpc;
+  b->last_mult = b->grid_mult;
+  b->last_bits = h->solve_bits;
+  return DIC_OK;
+}
+
+bool same_out(const dic_batch_out& a, const dic_batch_out& b) {
+  return memcmp(&a, &b, sizeof a) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
+  if (!h) return DIC_ERR_ARG;
+  free_batch(h->batch);
+  h->batch = nullptr;
+  if (n_pairs < 1 || !descs) return fail(h, DIC_ERR_ARG, "need at least one pair descriptor");
+  dic::BatchState* b = new (std::nothrow) dic::BatchState;
+  if (!b) return DIC_ERR_OOM;
+  int64_t off = 0;
+  size_t px = 0;
+  for (int k = 0; k < n_pairs; ++k) {
+    dic::BatchPair bp;
+    bp.d = descs[k];
+    bp.S = bp.d.subset_size > 0 ? bp.d.subset_size : h->subset;
+    bp.step = bp.d.grid_step > 0 ? bp.d.grid_step : h->step;
+    bp.R = bp.d.search_radius >= 0 ? bp.d.search_radius : h->R;
+    bp.M = bp.S / 2;
+    if (!bp.d.ref_dev || !bp.d.def_dev || bp.d.width < 4 || bp.d.height < 4 ||
+        bp.d.pitch_bytes < bp.d.width || bp.S < 3 || bp.S > dic::kMaxSubset || (bp.S & 1) == 0 ||
+        bp.R > 1000) {
+      delete b;
+      return fail(h, DIC_ERR_ARG, "bad descriptor for pair %d", k);
+    }
+    if (dic::search_smem_bytes(bp.S, bp.R) > 227 * 1024) {
+      delete b;
+      return fail(h, DIC_ERR_UNSUPPORTED,
+                  "pair %d: search window (subset %d, radius %d) exceeds shared memory", k, bp.S,
+                  bp.R);
+    }
+    grid_of(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, &bp.nx, &bp.ny);
+    bp.n = (int64_t)bp.nx * bp.ny;
+    bp.off = off;
+    bp.px_off = px;
+    bp.tw = (bp.S + 3) / 4 * 4;
+    off += bp.n;
+    px += (size_t)bp.d.width * bp.d.height;
+    if (bp.S * bp.S > b->nmax) b->nmax = bp.S * bp.S;
+    b->pairs.push_back(bp);
+    bool placed = false;
+    for (auto& c : b->classes)
+      if (c.tw == bp.tw) {
+        c.pairs.push_back(k);
+        c.smem = std::max(c.smem, dic::search_smem_bytes(bp.S, bp.R));
+        placed = true;
+      }
+    if (!placed) {
+      dic::BatchClass c;
+      c.tw = bp.tw;
+      c.pairs.push_back(k);
+      c.smem = dic::search_smem_bytes(bp.S, bp.R);
+      b->classes.push_back(c);
+    }
+  }
+  b->total = off;
+  b->px_total = px;
+  h->batch = b;
+  if (!h->err_flag) {
+    if (cudaMalloc(&h->err_flag, sizeof(unsigned int)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, DIC_ERR_OOM, "cannot allocate error flag");
+    }
+    cudaMemset(h->err_flag, 0, sizeof(unsigned int));
+  }
+  std::vector<int64_t> offs;
+  for (auto& bp : b->pairs) offs.push_back(bp.off);
+  offs.push_back(off);
+  cudaError_t e = cudaMalloc(&b->lut, px * 4 * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc(&b->grad, px * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_pjobs, sizeof(dic::SubpixelParams) * n_pairs);
+  if (e == cudaSuccess) e = upload(&b->d_offsets, offs);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&b->d_counters, sizeof(unsigned long long) * (b->classes.size() + 1));
+  for (auto& c : b->classes) {
+    if (e != cudaSuccess) break;
+    std::vector<int64_t> co{0};
+    for (int k : c.pairs) co.push_back(co.back() + b->pairs[k].n);
+    e = cudaMalloc(&c.d_jobs, sizeof(dic::SearchParams) * c.pairs.size());
+    if (e == cudaSuccess) e = upload(&c.d_offsets, co);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    h->batch = nullptr;
+    return fail(h, DIC_ERR_OOM, "cannot allocate batch scratch (%zu pixels)", px);
+  }
+  return DIC_OK;
+}
+
+dic_status dic_batch_pois(dic_t h, int64_t* total, int64_t* offsets) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->batch) return fail(h, DIC_ERR_STATE, "no batch set");
+  if (total) *total = h->batch->total;
+  if (offsets) {
+    for (size_t k = 0; k < h->batch->pairs.size(); ++k) offsets[k] = h->batch->pairs[k].off;
+    offsets[h->batch->pairs.size()] = h->batch->total;
+  }
+  return DIC_OK;
+}
+
+dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out* out) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->batch) return fail(h, DIC_ERR_STATE, "no batch set");
+  if (method != DIC_ICGN && method != DIC_FANR) return fail(h, DIC_ERR_ARG, "unknown method");
+  if (!out) return fail(h, DIC_ERR_ARG, "null output descriptor");
+  dic::BatchState* b = h->batch;
+  if (b->total == 0) return DIC_OK;
+  const dic_batch_out& o = *out;
+  if (!o.u0 || !o.v0 || !o.zncc0 || !o.status0 || !o.u || !o.v || !o.ux || !o.uy || !o.vx ||
+      !o.vy || !o.zncc || !o.iters || !o.status)
+    return fail(h, DIC_ERR_ARG, "null output array");
+  if (!b->exec || !same_out(b->last_out, o) || b->last_method != (int)method ||
+      b->last_wpc != b->wpc || b->last_mult != b->grid_mult || b->last_bits != h->solve_bits) {
+    dic_status st = build_graph(h, method, o);
+    if (st != DIC_OK) return st;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+  return DIC_OK;
+}
+
+dic_status dic_autotune(dic_t h, dic_method method, const dic_batch_out* out, int* chosen) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->batch) return fail(h, DIC_ERR_STATE, "no batch set");
+  dic::BatchState* b = h->batch;
+  const int wpcs[3] = {2, 4, 8}, mults[2] = {1, 2};
+  float best = 1e30f;
+  int bw = b->wpc, bm = b->grid_mult;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int w : wpcs)
+    for (int m : mults) {
+      b->wpc = w;
+      b->grid_mult = m;
+      dic_status st = dic_run_batch(h, method, out);  // builds and warms up
+      if (st != DIC_OK) continue;
+      cudaEventRecord(e0, h->stream);
+      for (int r = 0; r < 3; ++r) dic_run_batch(h, method, out);
+      cudaEventRecord(e1, h->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bw = w;
+        bm = m;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->wpc = bw;
+  b->grid_mult = bm;
+  if (chosen) {
+    chosen[0] = bw;
+    chosen[1] = bm;
+  }
+  return best < 1e30f ? DIC_OK : fail(h, DIC_ERR_CUDA, "no candidate ran");
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "dic.h"
 
@@ -97,6 +98,17 @@ cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int
 cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int H,
                                   int pitch, float2* grad, float4* lut, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
+
+// Persistent multi-pair launchers.  jobs / offsets are device arrays; the
+// POIs of job k are items [offsets[k], offsets[k+1]); counter starts at 0.
+cudaError_t launch_search_batch(int tw, const SearchParams* jobs, const int64_t* offsets,
+                                int njobs, unsigned long long* counter, size_t smem, int grid,
+                                cudaStream_t st);
+int search_batch_occupancy(int tw, size_t smem);
+size_t search_smem_bytes(int S, int R);
+cudaError_t launch_subpixel_batch(const SubpixelParams* jobs, const int64_t* offsets, int njobs,
+                                  int nmax, int method, int solve_fp64, int wpc,
+                                  unsigned long long* counter, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchParams& p, const CUtensorMap* tm_ref,
                           const CUtensorMap* tm_def, cudaStream_t st);
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
@@ -105,6 +117,40 @@ cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
 // Size of the byte box that TMA stages for a subset / search window.
 __host__ __device__ inline int tma_box_width(int span) { return ((span + 15 + 15) / 16) * 16; }
 
+}  // namespace dic
+
+namespace dic {
+// State of a bound batch (dic_set_pairs).
+struct BatchPair {
+  dic_pair_desc d;
+  int S, M, R, step, nx, ny, tw;
+  int64_t n, off;
+  size_t px_off;
+};
+struct BatchClass {  // pairs sharing the search template width
+  int tw;
+  std::vector<int> pairs;
+  size_t smem;
+  SearchParams* d_jobs = nullptr;
+  int64_t* d_offsets = nullptr;
+};
+struct BatchState {
+  std::vector<BatchPair> pairs;
+  std::vector<BatchClass> classes;
+  int64_t total = 0;
+  int nmax = 0;
+  size_t px_total = 0;
+  float4* lut = nullptr;
+  float2* grad = nullptr;
+  SubpixelParams* d_pjobs = nullptr;
+  int64_t* d_offsets = nullptr;
+  unsigned long long* d_counters = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  dic_batch_out last_out{};
+  int last_method = -1, last_wpc = 0, last_mult = 0, last_bits = 0;
+  int wpc = 4, grid_mult = 1;
+};
 }  // namespace dic
 
 struct dic_s {
@@ -128,6 +174,8 @@ struct dic_s {
 
   bool tma_ok = false;
   CUtensorMap tm_ref{}, tm_def{};
+
+  dic::BatchState* batch = nullptr;
 
   std::string last_error;
 };

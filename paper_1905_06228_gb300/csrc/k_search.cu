@@ -112,15 +112,15 @@ __host__ __device__ inline Layout make_layout(int S, int R) {
   return L;
 }
 
+// The search of one POI by the whole CTA (any block size that is a multiple
+// of 32, up to kMaxThreads).  TMA staging is used when p.use_tma is set and
+// the tensor maps are given (one TMA transaction per call: parity 0).
 template <int TW>
-__global__ void __launch_bounds__(kMaxThreads)
-search_kernel(const SearchParams p, const __grid_constant__ CUtensorMap tm_ref,
-              const __grid_constant__ CUtensorMap tm_def) {
-  extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ void search_poi(const SearchParams& p, int64_t poi,
+                                           const CUtensorMap* tm_ref, const CUtensorMap* tm_def,
+                                           unsigned char* smem) {
   const int S = p.S, M = p.M, R = p.R;
   const Layout L = make_layout<TW>(S, R);
-  const int64_t poi = blockIdx.x;
-  if (poi >= p.n_pois) return;
   const int x0 = M + R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + R + 2 + (int)(poi / p.nx) * p.step;
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -136,7 +136,7 @@ search_kernel(const SearchParams p, const __grid_constant__ CUtensorMap tm_ref,
   // ---- stage bytes: template box at (x0-M, y0-M), window at (x0-M-R, y0-M-R)
   const int wx = x0 - M - R, wy = y0 - M - R, tx0 = x0 - M, ty0 = y0 - M;
   int ox_g, ox_f;
-  if (p.use_tma) {
+  if (p.use_tma && tm_ref && tm_def) {
     ox_g = wx & 15;
     ox_f = tx0 & 15;
     if (tid == 0) {
@@ -149,12 +149,12 @@ search_kernel(const SearchParams p, const __grid_constant__ CUtensorMap tm_ref,
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
           "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(wb)),
-          "l"(&tm_def), "r"(wx - ox_g), "r"(wy), "r"(b)
+          "l"(tm_def), "r"(wx - ox_g), "r"(wy), "r"(b)
           : "memory");
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
           "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(tb)),
-          "l"(&tm_ref), "r"(tx0 - ox_f), "r"(ty0), "r"(b)
+          "l"(tm_ref), "r"(tx0 - ox_f), "r"(ty0), "r"(b)
           : "memory");
     }
     __syncthreads();  // barrier initialised before anyone polls it
@@ -355,6 +355,44 @@ search_kernel(const SearchParams p, const __grid_constant__ CUtensorMap tm_ref,
   }
 }
 
+// One CTA per POI of one pair.
+template <int TW>
+__global__ void __launch_bounds__(kMaxThreads)
+search_kernel(const SearchParams p, const __grid_constant__ CUtensorMap tm_ref,
+              const __grid_constant__ CUtensorMap tm_def) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if ((int64_t)blockIdx.x >= p.n_pois) return;
+  search_poi<TW>(p, blockIdx.x, &tm_ref, &tm_def, smem);
+}
+
+// Persistent form over many pairs: each CTA takes the next POI of the whole
+// batch from a global counter (items ordered pair by pair, so one pair's
+// window data stays hot in L2), finds its pair by bisection of the prefix
+// offsets, and searches it with plain staging loads.
+template <int TW>
+__global__ void __launch_bounds__(kMaxThreads)
+search_batch_kernel(const SearchParams* __restrict__ jobs, const int64_t* __restrict__ offsets,
+                    int njobs, unsigned long long* counter) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ long long item_s;
+  const int64_t total = offsets[njobs];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t item = item_s;
+    __syncthreads();
+    if (item >= total) break;
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offsets[mid] <= item) lo = mid; else hi = mid;
+    }
+    const SearchParams p = jobs[lo];
+    search_poi<TW>(p, item - offsets[lo], nullptr, nullptr, smem);
+    __syncthreads();
+  }
+}
+
 template <int TW>
 cudaError_t launch_tw(const SearchParams& p, const CUtensorMap* tr, const CUtensorMap* td,
                       cudaStream_t st) {
@@ -373,9 +411,56 @@ cudaError_t launch_tw(const SearchParams& p, const CUtensorMap* tr, const CUtens
   return cudaGetLastError();
 }
 
+template <int TW>
+cudaError_t launch_batch_tw(const SearchParams* jobs, const int64_t* offsets, int njobs,
+                            unsigned long long* counter, size_t smem, int grid, cudaStream_t st) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(search_batch_kernel<TW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  search_batch_kernel<TW><<<grid, kMaxThreads, smem, st>>>(jobs, offsets, njobs, counter);
+  return cudaGetLastError();
+}
+
+template <int TW>
+int batch_ctas_per_sm(size_t smem) {
+  int n = 0;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(search_batch_kernel<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, search_batch_kernel<TW>, kMaxThreads, smem);
+  return n;
+}
+
 }  // namespace
 
 size_t search_smem_bytes(int S, int R);
+
+#define DIC_TW_SWITCH(tw, CALL)                                                          \
+  switch (tw) {                                                                          \
+    case 4: CALL(4); case 8: CALL(8); case 12: CALL(12); case 16: CALL(16);            \
+    case 20: CALL(20); case 24: CALL(24); case 28: CALL(28); case 32: CALL(32);        \
+    case 36: CALL(36); case 40: CALL(40); case 44: CALL(44); case 48: CALL(48);        \
+    case 52: CALL(52); case 56: CALL(56); case 60: CALL(60); case 64: CALL(64);        \
+    default: break;                                                                      \
+  }
+
+cudaError_t launch_search_batch(int tw, const SearchParams* jobs, const int64_t* offsets,
+                                int njobs, unsigned long long* counter, size_t smem, int grid,
+                                cudaStream_t st) {
+#define DIC_CALL(T) return launch_batch_tw<T>(jobs, offsets, njobs, counter, smem, grid, st)
+  DIC_TW_SWITCH(tw, DIC_CALL)
+#undef DIC_CALL
+  return cudaErrorInvalidValue;
+}
+
+int search_batch_occupancy(int tw, size_t smem) {
+#define DIC_CALL(T) return batch_ctas_per_sm<T>(smem)
+  DIC_TW_SWITCH(tw, DIC_CALL)
+#undef DIC_CALL
+  return 0;
+}
 
 cudaError_t launch_search(const SearchParams& p, const CUtensorMap* tm_ref,
                           const CUtensorMap* tm_def, cudaStream_t st) {

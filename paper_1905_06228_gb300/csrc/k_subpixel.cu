@@ -127,17 +127,11 @@ __device__ __forceinline__ const float* ref_ptr<float>(const SubpixelParams& p) 
   return p.ref_f32;
 }
 
+// Refinement of one POI by one warp; sgrad / sfc hold N entries.
 template <bool FANR, typename TS, typename TP>
-__global__ void __launch_bounds__(32 * kWarpsPerCta)
-subpixel_kernel(const SubpixelParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t poi = (int64_t)blockIdx.x * kWarpsPerCta + wid;
-  if (poi >= p.n_pois) return;
+__device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t poi, int lane,
+                                             float2* sgrad, float* sfc) {
   const int S = p.S, M = p.M, N = S * S;
-  float2* sgrad = reinterpret_cast<float2*>(smem) + (size_t)wid * N;
-  float* sfc = reinterpret_cast<float*>(smem + (size_t)kWarpsPerCta * N * sizeof(float2)) +
-               (size_t)wid * N;
   const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
   const int W = p.W, H = p.H;
@@ -375,6 +369,54 @@ subpixel_kernel(const SubpixelParams p) {
   write_out(zn, it_done, st);
 }
 
+// One warp per POI of one pair.
+template <bool FANR, typename TS, typename TP>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+subpixel_kernel(const SubpixelParams p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t poi = (int64_t)blockIdx.x * kWarpsPerCta + wid;
+  if (poi >= p.n_pois) return;
+  const int N = p.S * p.S;
+  float2* sgrad = reinterpret_cast<float2*>(smem) + (size_t)wid * N;
+  float* sfc = reinterpret_cast<float*>(smem + (size_t)kWarpsPerCta * N * sizeof(float2)) +
+               (size_t)wid * N;
+  subpixel_poi<FANR, TS, TP>(p, poi, lane, sgrad, sfc);
+}
+
+// Persistent form over many pairs: every warp repeatedly takes the next POI
+// of the batch from a global counter, so POIs with many iterations do not
+// hold back a whole CTA.  nmax = largest subset size N of the batch.
+template <bool FANR, typename TS, int WPC>
+__global__ void __launch_bounds__(32 * WPC)
+subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
+                      const int64_t* __restrict__ offsets, int njobs, int nmax,
+                      unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float2* sgrad = reinterpret_cast<float2*>(smem) + (size_t)wid * nmax;
+  float* sfc = reinterpret_cast<float*>(smem + (size_t)WPC * nmax * sizeof(float2)) +
+               (size_t)wid * nmax;
+  const int64_t total = offsets[njobs];
+  for (;;) {
+    long long item = 0;
+    if (lane == 0) item = (long long)atomicAdd(counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    int lo = 0, hi = njobs;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (offsets[mid] <= item) lo = mid; else hi = mid;
+    }
+    const SubpixelParams p = jobs[lo];
+    if (p.ref_f32)
+      subpixel_poi<FANR, TS, float>(p, item - offsets[lo], lane, sgrad, sfc);
+    else
+      subpixel_poi<FANR, TS, uint8_t>(p, item - offsets[lo], lane, sgrad, sfc);
+    __syncwarp();
+  }
+}
+
 template <bool FANR, typename TS, typename TP>
 cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
   const size_t smem = (size_t)kWarpsPerCta * p.S * p.S * (sizeof(float2) + sizeof(float));
@@ -389,7 +431,56 @@ cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <bool FANR, typename TS, int WPC>
+cudaError_t launch_batch_one(const SubpixelParams* jobs, const int64_t* offsets, int njobs,
+                             int nmax, unsigned long long* counter, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)WPC * nmax * (sizeof(float2) + sizeof(float));
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(subpixel_batch_kernel<FANR, TS, WPC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (grid <= 0) {  // (resident CTAs x SMs) x max(1, -grid)
+    int occ = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, subpixel_batch_kernel<FANR, TS, WPC>,
+                                                  32 * WPC, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = (occ > 0 ? occ : 1) * sms * (grid < 0 ? -grid : 1);
+  }
+  subpixel_batch_kernel<FANR, TS, WPC><<<grid, 32 * WPC, smem, st>>>(jobs, offsets, njobs, nmax,
+                                                                    counter);
+  return cudaGetLastError();
+}
+
+template <bool FANR, typename TS>
+cudaError_t launch_batch_wpc(int wpc, const SubpixelParams* jobs, const int64_t* offsets,
+                             int njobs, int nmax, unsigned long long* counter, int grid,
+                             cudaStream_t st) {
+  switch (wpc) {
+    case 2: return launch_batch_one<FANR, TS, 2>(jobs, offsets, njobs, nmax, counter, grid, st);
+    case 4: return launch_batch_one<FANR, TS, 4>(jobs, offsets, njobs, nmax, counter, grid, st);
+    case 8: return launch_batch_one<FANR, TS, 8>(jobs, offsets, njobs, nmax, counter, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_subpixel_batch(const SubpixelParams* jobs, const int64_t* offsets, int njobs,
+                                  int nmax, int method, int solve_fp64, int wpc,
+                                  unsigned long long* counter, int grid, cudaStream_t st) {
+  if (method == DIC_ICGN)
+    return solve_fp64 ? launch_batch_wpc<false, double>(wpc, jobs, offsets, njobs, nmax, counter,
+                                                        grid, st)
+                      : launch_batch_wpc<false, float>(wpc, jobs, offsets, njobs, nmax, counter,
+                                                       grid, st);
+  return solve_fp64 ? launch_batch_wpc<true, double>(wpc, jobs, offsets, njobs, nmax, counter,
+                                                     grid, st)
+                    : launch_batch_wpc<true, float>(wpc, jobs, offsets, njobs, nmax, counter,
+                                                    grid, st);
+}
 
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
                             cudaStream_t st) {
