@@ -31,6 +31,14 @@ BACKGROUND = 20.0
 CUTOFF = 4.0  # speckle support radius in units of r_k
 
 
+def _sin(x):
+    return x.sin() if hasattr(x, "sin") and not isinstance(x, np.ndarray) else np.sin(x)
+
+
+def _cos(x):
+    return x.cos() if hasattr(x, "cos") and not isinstance(x, np.ndarray) else np.cos(x)
+
+
 # ---------------------------------------------------------------------------
 # Deformation maps.  Each provides forward(x, y) -> (x', y') and
 # inverse(x', y') -> (x, y) on float64 arrays, plus the exact displacement
@@ -114,8 +122,8 @@ class Sinusoidal:
         x = xp - self.tx
         y = yp - self.ty
         for _ in range(iters):
-            x = xp - self.tx - self.au * np.sin(2 * np.pi * y / self.ly)
-            y = yp - self.ty - self.av * np.cos(2 * np.pi * x / self.lx)
+            x = xp - self.tx - self.au * _sin(2 * np.pi * y / self.ly)
+            y = yp - self.ty - self.av * _cos(2 * np.pi * x / self.lx)
         return x, y
 
     def displacement(self, x, y):
@@ -171,10 +179,11 @@ def _render(sp: SpeckleSet, width: int, height: int, inverse, forward,
     ox = ox.reshape(-1)
     pcx, pcy = forward(sp.cx, sp.cy)
     # reference coordinates of every target pixel, evaluated once
-    gy, gx = np.mgrid[0:height, 0:width].astype(np.float64)
+    gy, gx = torch.meshgrid(torch.arange(height, dtype=torch.float64, device=dev),
+                            torch.arange(width, dtype=torch.float64, device=dev), indexing="ij")
     inv_x, inv_y = inverse(gx, gy)
-    inv_x = torch.from_numpy(np.ascontiguousarray(inv_x, np.float64).ravel()).to(dev)
-    inv_y = torch.from_numpy(np.ascontiguousarray(inv_y, np.float64).ravel()).to(dev)
+    inv_x = inv_x.reshape(-1).contiguous()
+    inv_y = inv_y.reshape(-1).contiguous()
     del gx, gy
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).to(dev)
     cx, cy, r, amp = t(sp.cx), t(sp.cy), t(sp.r), t(sp.amp)
