@@ -60,8 +60,10 @@ typedef enum { DIC_ICGN = 0, DIC_FANR = 1 } dic_method;
 
 /* Integer-search arithmetic.  Both forms return the same argmax. */
 typedef enum {
-  DIC_FORM_PLAIN_FP32 = 0, /* FP32 FMA correlation, exact integer sums          */
-  DIC_FORM_BF16TC = 1      /* reserved: tensor-core correlation                 */
+  DIC_FORM_PLAIN_FP32 = 0, /* FP32 FMA correlation per POI, exact integer sums  */
+  DIC_FORM_BF16TC = 1      /* BF16 tensor-core correlation (tcgen05) across POIs,
+                              exact FP32 accumulation, exact re-rank of the top
+                              four candidates per POI                           */
 } dic_form;
 
 /* Per-POI status codes written by dic_integer_search / dic_subpixel. */
@@ -101,7 +103,11 @@ const char *dic_last_error(dic_t h);
 /* Stream for all later work (a cudaStream_t passed as void*; NULL = default). */
 dic_status dic_set_stream(dic_t h, void *cuda_stream);
 
-/* Integer-search arithmetic form (see dic_form). */
+/* Integer-search arithmetic form (see dic_form).  The tensor-core form needs
+ * at most 256 POIs whose search windows meet a 16x8 block of positions
+ * ((2R+16)/step + 1)*((2R+8)/step + 1) <= 256); dic_integer_search returns
+ * DIC_ERR_UNSUPPORTED otherwise.  It allocates per-POI scratch (a BF16 copy
+ * of every subset, 2*S*round16(S) bytes per POI) on first use. */
 dic_status dic_set_form(dic_t h, dic_form form);
 
 /* Precision of the per-POI 6x6 Gauss-Newton solve: 32 (FP32) or 64 (FP64

@@ -132,6 +132,9 @@ void dic_destroy(dic_t h) {
   if (h->lut) cudaFree(h->lut);
   if (h->grad) cudaFree(h->grad);
   if (h->err_flag) cudaFree(h->err_flag);
+  if (h->tc_bank) cudaFree(h->tc_bank);
+  if (h->tc_sums) cudaFree(h->tc_sums);
+  if (h->tc_slots) cudaFree(h->tc_slots);
   delete h;
 }
 
@@ -149,7 +152,10 @@ dic_status dic_set_form(dic_t h, dic_form form) {
     h->form = form;
     return DIC_OK;
   }
-  if (form == DIC_FORM_BF16TC) return fail(h, DIC_ERR_UNSUPPORTED, "tensor-core form not built");
+  if (form == DIC_FORM_BF16TC) {
+    h->form = form;
+    return DIC_OK;
+  }
   return fail(h, DIC_ERR_ARG, "unknown form %d", (int)form);
 }
 
@@ -308,6 +314,53 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
     return fail(h, DIC_ERR_UNSUPPORTED, "integer search needs an 8-bit pair (exact sums)");
   if (h->g.n_pois == 0) return DIC_OK;
   if (!u0 || !v0 || !zncc0 || !status) return fail(h, DIC_ERR_ARG, "null output pointer");
+  if (h->form == DIC_FORM_BF16TC) {
+    dic::SearchTcParams t{};
+    if (!dic::search_tc_geometry(h->g.W, h->g.H, h->subset, h->step, h->R, h->g.nx, h->g.ny,
+                                 &t) ||
+        dic::search_tc_smem(t) > 227 * 1024)
+      return fail(h, DIC_ERR_UNSUPPORTED,
+                  "tensor-core search: POI block of a tile exceeds 256 (grid step too small "
+                  "for this radius) or shared memory");
+    const size_t bank = (size_t)h->g.n_pois * h->subset * t.twk;
+    const size_t slots = (size_t)h->g.n_pois * t.nslots;
+    if (bank > h->tc_bank_elems || (size_t)h->g.n_pois > h->tc_pois ||
+        slots > h->tc_slot_elems) {
+      if (h->tc_bank) cudaFree(h->tc_bank);
+      if (h->tc_sums) cudaFree(h->tc_sums);
+      if (h->tc_slots) cudaFree(h->tc_slots);
+      h->tc_bank = nullptr;
+      h->tc_sums = nullptr;
+      h->tc_slots = nullptr;
+      h->tc_bank_elems = h->tc_pois = h->tc_slot_elems = 0;
+      if (cudaMalloc(&h->tc_bank, bank * sizeof(uint16_t)) != cudaSuccess ||
+          cudaMalloc(&h->tc_sums, (size_t)h->g.n_pois * sizeof(longlong2)) != cudaSuccess ||
+          cudaMalloc(&h->tc_slots, slots * sizeof(dic::SlotCand)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DIC_ERR_OOM, "cannot allocate tensor-core search scratch");
+      }
+      h->tc_bank_elems = bank;
+      h->tc_pois = (size_t)h->g.n_pois;
+      h->tc_slot_elems = slots;
+    }
+    t.ref = h->ref;
+    t.def = h->def;
+    t.W = h->g.W;
+    t.H = h->g.H;
+    t.pitch = h->g.pitch;
+    t.n_pois = h->g.n_pois;
+    t.bank = h->tc_bank;
+    t.sums = h->tc_sums;
+    t.slots = h->tc_slots;
+    t.u0 = u0;
+    t.v0 = v0;
+    t.zncc0 = zncc0;
+    t.status = status;
+    t.err_flag = h->err_flag;
+    cudaError_t e = dic::launch_search_tc(t, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "tensor-core search launch");
+    return DIC_OK;
+  }
   if (dic::search_smem_bytes(h->subset, h->R) > 227 * 1024)
     return fail(h, DIC_ERR_UNSUPPORTED, "search window too large for shared memory");
   dic::SearchParams p;

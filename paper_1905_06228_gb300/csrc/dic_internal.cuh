@@ -48,6 +48,36 @@ struct SearchParams {
   unsigned int* err_flag;  // set when a bounded wait gives up
 };
 
+// Best candidate of one (position tile, POI) pair in the tensor-core search.
+struct SlotCand {
+  long long num, dg;
+  int l, pad;
+};
+
+// Parameters of the tensor-core integer search (k_search_tc.cu).
+struct SearchTcParams {
+  const uint8_t* ref;
+  const uint8_t* def;
+  int W, H, pitch;
+  int S, M, R, step, nx, ny;
+  int64_t n_pois;
+  int twk;           // template row width padded to 16 taps
+  int npad;          // N of the MMA (POIs per tile block, padded to 16)
+  int ncols_max, nrows_max;
+  int rows_per_acc;  // template rows per exact FP32 accumulator
+  int tmem_cols;
+  int xmin, ymin, ntx, nty;
+  int slots_x, slots_y, nslots;
+  uint16_t* bank;    // [n_pois][S][twk] bf16 templates
+  longlong2* sums;   // [n_pois] (sum a, sum a^2)
+  SlotCand* slots;   // [n_pois][nslots]
+  int32_t* u0;
+  int32_t* v0;
+  float* zncc0;
+  uint8_t* status;
+  unsigned int* err_flag;
+};
+
 // Parameters of the sub-pixel kernels.  The reference image is 8-bit
 // (ref) or float (ref_f32 != nullptr); pitch is in elements.
 struct SubpixelParams {
@@ -98,6 +128,10 @@ cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int
 cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int H,
                                   int pitch, float2* grad, float4* lut, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
+
+bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, SearchTcParams* g);
+size_t search_tc_smem(const SearchTcParams& g);
+cudaError_t launch_search_tc(const SearchTcParams& p, cudaStream_t st);
 
 // Persistent multi-pair launchers.  jobs / offsets are device arrays; the
 // POIs of job k are items [offsets[k], offsets[k+1]); counter starts at 0.
@@ -176,6 +210,12 @@ struct dic_s {
   CUtensorMap tm_ref{}, tm_def{};
 
   dic::BatchState* batch = nullptr;
+
+  // scratch of the tensor-core search form
+  uint16_t* tc_bank = nullptr;
+  longlong2* tc_sums = nullptr;
+  dic::SlotCand* tc_slots = nullptr;
+  size_t tc_bank_elems = 0, tc_pois = 0, tc_slot_elems = 0;
 
   std::string last_error;
 };

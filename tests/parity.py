@@ -15,7 +15,8 @@ NAMES = ("u", "ux", "uy", "v", "vx", "vy")
 
 def run_gpu(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
             method: int = 0, solve_bits: int = 32, tol: float = 1e-3, max_iter: int = 50,
-            device: str = "cuda:0", pitch_pad: int = 0, subpixel: bool = True) -> dict:
+            device: str = "cuda:0", pitch_pad: int = 0, subpixel: bool = True,
+            form: int = 0) -> dict:
     import torch
 
     import paper_1905_06228_gb300 as dic
@@ -35,6 +36,8 @@ def run_gpu(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
     try:
         if solve_bits != 32:
             dic.dic_set_solve_precision(h, solve_bits)
+        if form:
+            dic.dic_set_form(h, form)
         dic.dic_set_pair(h, tf, tg, W, H, pitch)
         n, nx, ny = dic.dic_num_pois(h)
         out = {"n": n, "nx": nx, "ny": ny}

@@ -1,0 +1,103 @@
+"""Tensor-core form of the integer search (tcgen05, BF16 x BF16 -> FP32)
+against the FP32 form (bitwise: same exact integers) and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import configs
+from workloads.speckle import Affine, Rigid
+
+from parity import compare_search, run_gpu
+
+pytestmark = pytest.mark.gpu
+TC = 1
+INT_KEYS = ("u0", "v0", "zncc0", "status0")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _both(f, g, s, st, r):
+    a = run_gpu(f, g, s, st, r, subpixel=False, form=0)
+    b = run_gpu(f, g, s, st, r, subpixel=False, form=TC)
+    assert a["n"] == b["n"]
+    for k in INT_KEYS:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    return b
+
+
+def test_rigid256(rigid256):
+    p = rigid256
+    b = _both(p.ref, p.defm, p.subset, p.step, p.radius)
+    compare_search(b, oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius))
+
+
+def test_affine1024(affine1024):
+    p = affine1024
+    b = _both(p.ref, p.defm, p.subset, p.step, p.radius)
+    idx = np.sort(np.random.default_rng(3).choice(b["n"], 800, replace=False))
+    compare_search(b, oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius,
+                                            poi_idx=idx), idx)
+
+
+@pytest.mark.parametrize("subset,step,radius,size", [
+    (5, 2, 3, 28), (9, 4, 0, 40), (11, 4, 3, 96), (15, 5, 5, 128), (21, 7, 8, 200),
+    (33, 9, 4, 96), (41, 12, 6, 120), (51, 20, 5, 140), (63, 30, 3, 150),
+])
+def test_sizes(subset, step, radius, size):
+    f, g = configs.tiny(2000 + subset, size, size - 4, int(0.03 * size * size),
+                        Affine(0.003, -0.002, 0.4, 1.2, -0.8, size / 2, size / 2), noise=1.5)
+    b = _both(f, g, subset, step, radius)
+    compare_search(b, oracle.integer_search(f, g, subset, step, radius))
+
+
+def test_mixed_and_sine_pairs():
+    for p in (configs.mixed(2), configs.mixed(0), configs.sine2048(0)):
+        b = _both(p.ref, p.defm, p.subset, p.step, p.radius)
+        idx = np.sort(np.random.default_rng(4).choice(b["n"], min(b["n"], 300), replace=False))
+        compare_search(b, oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius,
+                                                poi_idx=idx), idx)
+
+
+def test_ties_flat_and_planted():
+    rng = np.random.default_rng(3)
+    period = rng.integers(0, 256, (40, 3)).astype(np.uint8)
+    gg = np.ascontiguousarray(np.tile(period, (1, 14)))
+    ff = np.ascontiguousarray(np.roll(gg, -1, axis=1))
+    b = _both(ff, gg, 5, 5, 3)
+    assert (b["u0"] == -2).all()
+    flat = np.full((40, 40), 90, np.uint8)
+    g, _ = configs.tiny(4, 40, 40, 60)
+    _both(flat, g, 5, 5, 2)
+    _both(g, flat, 5, 5, 2)
+    big, _ = configs.tiny(11, 140, 140, 700)
+    f = np.ascontiguousarray(big[20:120, 20:120])
+    g = np.ascontiguousarray(big[20 + 5:120 + 5, 20 - 7:120 - 7])
+    b = _both(f, g, 15, 6, 10)
+    assert (b["u0"] == 7).all() and (b["v0"] == -5).all()
+
+
+def test_unsupported_geometry_is_reported():
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    f, g = configs.tiny(8, 120, 120, 300)
+    h = dic.dic_create(9, 1, 10)   # step 1: 35 x 27 POIs would meet one tile
+    try:
+        dic.dic_set_form(h, TC)
+        tf = torch.from_numpy(f).cuda()
+        tg = torch.from_numpy(g).cuda()
+        dic.dic_set_pair(h, tf, tg)
+        n, _, _ = dic.dic_num_pois(h)
+        z = torch.empty(n, dtype=torch.int32, device="cuda")
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_integer_search(h, z, z, z.float(), z.to(torch.uint8))
+        assert e.value.code == dic.DIC_ERR_UNSUPPORTED
+    finally:
+        dic.dic_destroy(h)
