@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--solve-bits", type=int, default=64)
+    ap.add_argument("--form", default="tc", choices=["tc", "fp32"],
+                    help="integer-search form of the chosen configuration")
     ap.add_argument("--cpu-sample", type=int, default=8192,
                     help="POIs in the oracle's CPU sample")
     ap.add_argument("--workload", default="affine1024",
@@ -149,11 +151,13 @@ def run_gpu(args):
     stream = torch.cuda.Stream(dev)
     props = torch.cuda.get_device_properties(dev)
 
-    def make(solve_bits):
+    def make(solve_bits, form):
         d = dic.DIC(SUBSET, STEP, RADIUS, TOL, MAX_ITER, solve_bits=solve_bits, stream=stream)
+        if form == "tc":
+            dic.dic_set_form(d.h, dic.DIC_FORM_BF16TC)
         return d
 
-    d = make(args.solve_bits)
+    d = make(args.solve_bits, args.form)
     n, nx, ny = d.set_pair(ref_d, def_d)
     with torch.cuda.stream(stream):
         s_out = d.integer_search()
@@ -218,11 +222,12 @@ def run_gpu(args):
     ms_per_step = total_ms / args.steps
     value = conv_all * args.steps / (total_ms / 1e3)
 
-    # plain FP32 form (FP32 6x6 solve) on the same input, same timing rules
-    d32 = make(32)
+    # plain form (FP32 search, FP32 6x6 solve) on the same input, same rules
+    d32 = make(32, "fp32")
     d32.set_pair(ref_d, def_d)
-    st32, _, conv32, _, _ = timed_loop(d32, max(10, args.steps // 4), 3)
+    st32, se32, conv32, _, _ = timed_loop(d32, max(10, args.steps // 4), 3)
     plain_value = conv32 * len(st32) / (sum(st32) / 1e3)
+    plain_search_ms = statistics.mean(se32)
     d32.close()
 
     # e2e through the public call with host buffers: H2D of both images,
@@ -255,14 +260,27 @@ def run_gpu(args):
            "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_out.values())
                                      + sum(v.numel() * v.element_size() for v in h_s.values()))}
 
-    # roofline of the dominant kernel (integer search): FP32 FMA pipe
+    # roofline of the dominant kernel (integer search), algorithmic flops
+    # 2 N (2R+1)^2 per POI (the padded / wasted MACs are not counted)
     search_avg_s = statistics.mean(search_ms) / 1e3
     flops = 2.0 * SUBSET * SUBSET * (2 * RADIUS + 1) ** 2 * n
     peak_mhz = 2070.0
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    if args.form == "tc":
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        bound, kernel = "tensor", "integer search, tensor-core form (bank + tile + reduce kernels)"
+        basis = ("measured dense BF16 (cuBLAS burst) " + ("of measured" if peaks else "of fallback"))
+        prof = os.path.join(ROOT, "profiles", "search_tc_affine1024_traffic.json")
+    else:
+        peak = fp32_peak
+        bound, kernel = "alu", "search_kernel (FP32 FMA correlation)"
+        basis = (f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
+                 "(nominal max clock)")
+        prof = os.path.join(ROOT, "profiles", "search_affine1024_traffic.json")
     achieved = flops / search_avg_s / 1e12
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "search_affine1024_traffic.json")
     if os.path.exists(prof):
         # counters apply only while the kernel source is the one they were taken on
         try:
@@ -273,12 +291,13 @@ def run_gpu(args):
                 traffic = meta.get("bytes_per_launch")
         except (OSError, ValueError, KeyError):
             traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "search_kernel (FP32 FMA correlation)",
-                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                              f"{peak_mhz:.0f} MHz (nominal max clock)",
-                "search_ms": search_avg_s * 1e3}
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                "peak_basis": basis, "search_ms": search_avg_s * 1e3,
+                "plain_fp32_search": {"ms": plain_search_ms,
+                                      "achieved_tflops": flops / (plain_search_ms / 1e3) / 1e12,
+                                      "frac_of_fp32_peak": flops / (plain_search_ms / 1e3) / 1e12
+                                      / fp32_peak}}
 
     cpu = None
     if rank == 0:
@@ -289,10 +308,13 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic (seeded speckle renders)",
-                "config": config_dict(world), "e2e": e2e, "gpu_launches": 3 * args.steps,
+                "dtype": "bf16+f32" if args.form == "tc" else "f32",
+                "data": "synthetic (seeded speckle renders)",
+                "config": config_dict(world), "e2e": e2e,
+                "gpu_launches": (5 if args.form == "tc" else 3) * args.steps,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "forms": {"chosen": {"search": "fp32-exact", "solve": f"fp{args.solve_bits}",
+                "forms": {"chosen": {"search": "bf16-tensor-core-exact" if args.form == "tc"
+                                     else "fp32-exact", "solve": f"fp{args.solve_bits}",
                                      "value": value},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
                                          "value": plain_value}},

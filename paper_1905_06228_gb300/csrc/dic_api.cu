@@ -132,9 +132,10 @@ void dic_destroy(dic_t h) {
   if (h->lut) cudaFree(h->lut);
   if (h->grad) cudaFree(h->grad);
   if (h->err_flag) cudaFree(h->err_flag);
-  if (h->tc_bank) cudaFree(h->tc_bank);
-  if (h->tc_sums) cudaFree(h->tc_sums);
+  if (h->tc_phase) cudaFree(h->tc_phase);
+  if (h->tc_fbox) cudaFree(h->tc_fbox);
   if (h->tc_slots) cudaFree(h->tc_slots);
+  if (h->tc_posbox) cudaFree(h->tc_posbox);
   delete h;
 }
 
@@ -322,24 +323,21 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
       return fail(h, DIC_ERR_UNSUPPORTED,
                   "tensor-core search: POI block of a tile exceeds 256 (grid step too small "
                   "for this radius) or shared memory");
-    const size_t bank = (size_t)h->g.n_pois * h->subset * t.twk;
+    const size_t phase = dic::search_tc_phase_elems(t);
     const size_t slots = (size_t)h->g.n_pois * t.nslots;
-    if (bank > h->tc_bank_elems || (size_t)h->g.n_pois > h->tc_pois ||
+    if (phase > h->tc_phase_elems || (size_t)h->g.n_pois > h->tc_pois ||
         slots > h->tc_slot_elems) {
-      if (h->tc_bank) cudaFree(h->tc_bank);
-      if (h->tc_sums) cudaFree(h->tc_sums);
+      if (h->tc_phase) cudaFree(h->tc_phase);
       if (h->tc_slots) cudaFree(h->tc_slots);
-      h->tc_bank = nullptr;
-      h->tc_sums = nullptr;
+      h->tc_phase = nullptr;
       h->tc_slots = nullptr;
-      h->tc_bank_elems = h->tc_pois = h->tc_slot_elems = 0;
-      if (cudaMalloc(&h->tc_bank, bank * sizeof(uint16_t)) != cudaSuccess ||
-          cudaMalloc(&h->tc_sums, (size_t)h->g.n_pois * sizeof(longlong2)) != cudaSuccess ||
+      h->tc_phase_elems = h->tc_pois = h->tc_slot_elems = 0;
+      if (cudaMalloc(&h->tc_phase, phase * sizeof(uint16_t)) != cudaSuccess ||
           cudaMalloc(&h->tc_slots, slots * sizeof(dic::SlotCand)) != cudaSuccess) {
         cudaGetLastError();
         return fail(h, DIC_ERR_OOM, "cannot allocate tensor-core search scratch");
       }
-      h->tc_bank_elems = bank;
+      h->tc_phase_elems = phase;
       h->tc_pois = (size_t)h->g.n_pois;
       h->tc_slot_elems = slots;
     }
@@ -349,9 +347,25 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
     t.H = h->g.H;
     t.pitch = h->g.pitch;
     t.n_pois = h->g.n_pois;
-    t.bank = h->tc_bank;
-    t.sums = h->tc_sums;
+    const size_t pbe = dic::search_tc_posbox_elems(t);
+    if (pbe > h->tc_posbox_elems) {
+      if (h->tc_posbox) cudaFree(h->tc_posbox);
+      if (h->tc_fbox) cudaFree(h->tc_fbox);
+      h->tc_posbox = nullptr;
+      h->tc_fbox = nullptr;
+      h->tc_posbox_elems = 0;
+      if (cudaMalloc(&h->tc_posbox, pbe * sizeof(int2)) != cudaSuccess ||
+          cudaMalloc(&h->tc_fbox, pbe * sizeof(int2)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DIC_ERR_OOM, "cannot allocate tensor-core search scratch");
+      }
+      h->tc_posbox_elems = pbe;
+    }
+    t.fph = h->tc_phase;
+    t.gph = h->tc_phase + phase / 2;
+    t.fbox = h->tc_fbox;
     t.slots = h->tc_slots;
+    t.posbox = h->tc_posbox;
     t.u0 = u0;
     t.v0 = v0;
     t.zncc0 = zncc0;

@@ -68,9 +68,12 @@ struct SearchTcParams {
   int tmem_cols;
   int xmin, ymin, ntx, nty;
   int slots_x, slots_y, nslots;
-  uint16_t* bank;    // [n_pois][S][twk] bf16 templates
-  longlong2* sums;   // [n_pois] (sum a, sum a^2)
+  uint16_t* fph;     // [8][phh][phw] centred BF16 copies of f shifted by 0..7
+  uint16_t* gph;     // same for g
+  int phh, phw;
+  int2* fbox;        // like posbox, for the reference image (POI sums)
   SlotCand* slots;   // [n_pois][nslots]
+  int2* posbox;      // [nty*16][ntx*8] box sums of the position domain
   int32_t* u0;
   int32_t* v0;
   float* zncc0;
@@ -131,6 +134,8 @@ cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
 
 bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, SearchTcParams* g);
 size_t search_tc_smem(const SearchTcParams& g);
+size_t search_tc_posbox_elems(const SearchTcParams& g);
+size_t search_tc_phase_elems(const SearchTcParams& g);
 cudaError_t launch_search_tc(const SearchTcParams& p, cudaStream_t st);
 
 // Persistent multi-pair launchers.  jobs / offsets are device arrays; the
@@ -212,10 +217,11 @@ struct dic_s {
   dic::BatchState* batch = nullptr;
 
   // scratch of the tensor-core search form
-  uint16_t* tc_bank = nullptr;
-  longlong2* tc_sums = nullptr;
+  uint16_t* tc_phase = nullptr;
+  int2* tc_fbox = nullptr;
   dic::SlotCand* tc_slots = nullptr;
-  size_t tc_bank_elems = 0, tc_pois = 0, tc_slot_elems = 0;
+  int2* tc_posbox = nullptr;
+  size_t tc_phase_elems = 0, tc_pois = 0, tc_slot_elems = 0, tc_posbox_elems = 0;
 
   std::string last_error;
 };
