@@ -15,6 +15,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Bicubic value (and optionally derivatives) from one table cell.
+// The table is four planes of float4: plane n holds, per cell, the
+// coefficients of ty^n (1, tx, tx^2, tx^3).  Lanes of a warp interpolate
+// consecutive pixels of a subset row, so each plane load of a warp covers
+// contiguous cache lines.
 template <bool DERIV>
 __device__ __forceinline__ float bicubic(const float4* __restrict__ lut, size_t plane,
                                          size_t cell, float tx, float ty, float& gx, float& gy) {

@@ -22,7 +22,8 @@
 //
 // Bytes per pixel: 1 (f) + 1 (g) read, 8 (grad) + 64 (lut) written.  Each
 // warp writes 32 consecutive float4 of one plane per store (512 B), so every
-// store is a full-line coalesced write.
+// store is a full-line coalesced write; the sub-pixel kernels read the
+// planes the same way (lanes interpolate consecutive pixels).
 #include "dic_internal.cuh"
 
 namespace dic {

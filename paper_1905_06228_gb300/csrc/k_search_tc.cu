@@ -83,11 +83,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
   return false;
 }
 
-__device__ __forceinline__ uint16_t to_bf16_bits(int v) {
-  // small integers are exact in bf16: take the top half of the float
-  return (uint16_t)(__float_as_uint((float)v) >> 16);
-}
-
 struct Cand {
   long long num, dg;
   int l;

@@ -20,8 +20,20 @@
 // lane accumulates S0 = sum (g-c), S1 = sum (g-c)^2 and sum SD_k (g-c) (or
 // the FA-NR sums); then gbar = c + S0/N, dg^2 = S1 - S0^2/N and the
 // right-hand side follow exactly as in the formulas above.  The 6x6 solve is
-// FP32 or FP64 (Cholesky), chosen per launch.  The final ZNCC is Eq. 1 at
+// FP32 or FP64, chosen per launch: a Cholesky factorisation whose diagonal
+// reciprocals come from a refined reciprocal square root (no divisions);
+// IC-GN factors H once and keeps H^-1 (row k on lane k), FA-NR factors its
+// Gauss-Newton matrix every iteration.  The final ZNCC is Eq. 1 at
 // the returned shape (one extra pass).
+// resident CTAs per SM requested from the register allocator, and the
+// unroll of the per-point loop (memory-level parallelism of the table loads)
+#ifndef DIC_SUB_MINB
+#define DIC_SUB_MINB 1
+#endif
+#ifndef DIC_SUB_UNROLL
+#define DIC_SUB_UNROLL 1
+#endif
+
 #include "dic_device.cuh"
 #include "dic_internal.cuh"
 
@@ -29,46 +41,93 @@ namespace dic {
 namespace {
 
 constexpr int kWarpsPerCta = 4;
+constexpr int kPointUnroll = DIC_SUB_UNROLL;
 
-// Cholesky factorisation of a symmetric 6x6 (lower part used), in place.
+// 1/sqrt(d): FP32 estimate refined by Newton's iteration for 1/y^2 = d,
+// y <- y (3/2 - d y^2 / 2), which doubles the correct bits per step.
 template <typename T>
-__device__ __forceinline__ bool chol6(T A[6][6]) {
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    T d = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-    if (!(d > T(0))) return false;
-    d = sqrt(d);
-    A[j][j] = d;
-    const T inv = T(1) / d;
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      T s = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
-      A[i][j] = s * inv;
-    }
-  }
-  return true;
+__device__ __forceinline__ T rsqrt_refined(T d);
+template <>
+__device__ __forceinline__ float rsqrt_refined<float>(float d) {
+  float y = rsqrtf(d);
+  return y * (1.5f - 0.5f * d * y * y);
+}
+template <>
+__device__ __forceinline__ double rsqrt_refined<double>(double d) {
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y * (1.5 - 0.5 * d * y * y);
 }
 
+// Cholesky factor L (lower) of the symmetric 6x6 given as 21 packed lower
+// entries (row-major), with the reciprocals of its diagonal; no divisions.
 template <typename T>
-__device__ __forceinline__ void chol6_solve(const T L[6][6], const T b[6], T x[6]) {
+__device__ __forceinline__ bool chol6_packed(const float Hp[21], T L[6][6], T rinv[6]) {
+  int k0 = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) L[i][j] = (T)Hp[k0++];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    T d = L[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    ok = ok && (d > T(0)) && (d < T(3e38));
+    const T r = rsqrt_refined<T>(ok ? d : T(1));
+    L[j][j] = d * r;
+    rinv[j] = r;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      T sacc = L[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) sacc -= L[i][k] * L[j][k];
+      L[i][j] = sacc * r;
+    }
+  }
+  return ok;
+}
+
+// Column k of (L L^T)^-1 (forward then backward substitution of e_k).
+template <typename T>
+__device__ __forceinline__ void chol6_inverse_col(const T L[6][6], const T rinv[6], int k,
+                                                  T x[6]) {
   T y[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    T s = b[i];
+    T sacc = (i == k) ? T(1) : T(0);
 #pragma unroll
-    for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
-    y[i] = s / L[i][i];
+    for (int j = 0; j < i; ++j) sacc -= L[i][j] * y[j];
+    y[i] = sacc * rinv[i];
   }
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
-    T s = y[i];
+    T sacc = y[i];
 #pragma unroll
-    for (int k = i + 1; k < 6; ++k) s -= L[k][i] * x[k];
-    x[i] = s / L[i][i];
+    for (int j = i + 1; j < 6; ++j) sacc -= L[j][i] * x[j];
+    x[i] = sacc * rinv[i];
+  }
+}
+
+// Solve (L L^T) x = b with the stored reciprocals.
+template <typename T>
+__device__ __forceinline__ void chol6_solve_r(const T L[6][6], const T rinv[6], const T b[6],
+                                              T x[6]) {
+  T y[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T sacc = b[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) sacc -= L[i][j] * y[j];
+    y[i] = sacc * rinv[i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    T sacc = y[i];
+#pragma unroll
+    for (int j = i + 1; j < 6; ++j) sacc -= L[j][i] * x[j];
+    x[i] = sacc * rinv[i];
   }
 }
 
@@ -96,21 +155,12 @@ __device__ __forceinline__ void compose_inverse(float p[6], const float dp[6]) {
 template <typename T>
 __device__ __forceinline__ bool solve6(const float Hf[21], const float bf[6], float out[6],
                                        bool negate) {
-  T A[6][6];
-  int k = 0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      A[i][j] = (T)Hf[k];
-      A[j][i] = (T)Hf[k];
-      ++k;
-    }
-  if (!chol6<T>(A)) return false;
+  T L[6][6], rinv[6];
+  if (!chol6_packed<T>(Hf, L, rinv)) return false;
   T b[6], x[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) b[i] = (T)bf[i];
-  chol6_solve<T>(A, b, x);
+  chol6_solve_r<T>(L, rinv, b, x);
 #pragma unroll
   for (int i = 0; i < 6; ++i) out[i] = negate ? (float)(-x[i]) : (float)x[i];
   return true;
@@ -213,22 +263,16 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       bfv[k] = warp_sum(bfv[k]);
     }
   }
-  // IC-GN: factor H once (in the solve precision)
-  TS L[6][6];
+  // IC-GN: factor H once (in the solve precision); lane k < 6 keeps row k of
+  // H^-1, so each iteration's solve is six multiply-adds per lane
+  TS hrow[6];
   if (!FANR) {
-    int k = 0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        L[i][j] = (TS)Hs[k];
-        L[j][i] = (TS)Hs[k];
-        ++k;
-      }
-    if (!chol6<TS>(L)) {
+    TS L[6][6], rinv[6];
+    if (!chol6_packed<TS>(Hs, L, rinv)) {
       write_out(0.f, 0, kSingular);
       return;
     }
+    chol6_inverse_col<TS>(L, rinv, lane < 6 ? lane : 0, hrow);
   }
   if (!corners_in(prm, x0, y0, M, W, H)) {
     write_out(0.f, 0, kOutOfBounds);
@@ -246,6 +290,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 #pragma unroll
     for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = 0.f;
     PtWalk w(lane, S, M);
+#pragma unroll kPointUnroll
     for (int i = lane; i < N; i += 32, w.next()) {
       const int dx = w.dx, dy = w.dy;
       float tx, ty, gx = 0.f, gy = 0.f;
@@ -296,12 +341,12 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const float ratio = df / dg;
 #pragma unroll
       for (int a = 0; a < 6; ++a) rhs[a] = bfv[a] - ratio * (acc[a] - gm * sdsum[a]);
-      TS bb[6], xx[6];
+      TS acc6 = TS(0);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) bb[a] = (TS)rhs[a];
-      chol6_solve<TS>(L, bb, xx);
+      for (int a = 0; a < 6; ++a) acc6 += hrow[a] * (TS)rhs[a];
+      const float mine = (float)(-acc6);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) dp[a] = (float)(-xx[a]);
+      for (int a = 0; a < 6; ++a) dp[a] = __shfl_sync(0xffffffffu, mine, a);
       ok = true;
     } else {
       const float ratio = dg / df;
@@ -371,7 +416,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 
 // One warp per POI of one pair.
 template <bool FANR, typename TS, typename TP>
-__global__ void __launch_bounds__(32 * kWarpsPerCta)
+__global__ void __launch_bounds__(32 * kWarpsPerCta, DIC_SUB_MINB)
 subpixel_kernel(const SubpixelParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
