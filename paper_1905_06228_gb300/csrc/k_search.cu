@@ -314,7 +314,7 @@ __device__ __forceinline__ void search_poi(const SearchParams& p, int64_t poi,
       if (du >= L.ow) break;
       const int2 bx = hs[dv * L.ow + du];
       const long long sb = bx.x, sbb = bx.y;
-      const long long sab = (long long)iacc[j] + (long long)__float2ll_rn(acc[j]);
+      const long long sab = (long long)iacc[j] + (long long)__float2int_rn(acc[j]);
       const long long dg = N * sbb - sb * sb;
       if (dg == 0) continue;
       Cand c{N * sab - Sa * sb, dg, dv * L.ow + du};

@@ -88,6 +88,14 @@ struct Cand {
   int l;
 };
 
+// float of an exact 64-bit integer without the 64-bit conversion (which runs
+// on the FP64 pipe): hi * 2^32 + lo, relative error ~1e-7
+__device__ __forceinline__ float ll_to_float(long long v) {
+  const int hi = (int)(v >> 32);
+  const unsigned lo = (unsigned)(v & 0xffffffffll);
+  return fmaf((float)hi, 4294967296.0f, (float)lo);
+}
+
 __device__ __forceinline__ bool zncc_greater(long long na, long long da, long long nb,
                                              long long db) {
   if (na >= 0 && nb < 0) return true;
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
     const long long dg = N * (long long)bx.y - (long long)bx.x * bx.x;
     pdg[tid] = dg;
     psb[tid] = bx.x;
-    pinv[tid] = dg ? 1.0f / (float)dg : 0.f;
+    pinv[tid] = dg ? 1.0f / ll_to_float(dg) : 0.f;
   }
   // ---- A buffer: eight shifted copies per image row and 8-tap block,
   //   abuf[row*sboA + kb*128 + r*16 + e*2] = g[Y0+row][X0 + r + 8kb + e] - 128,
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
         const long long dg = pdg[m];
         if (dg == 0) continue;
         const long long num = N * (long long)drow[m] - sa * (long long)psb[m];
-        const float fn = (float)num;
+        const float fn = ll_to_float(num);
         const float score = fn * fabsf(fn) * pinv[m];  // sign(C) C^2 Df
         if (score < best_f - 1e-5f * fabsf(best_f) - 1e-30f) continue;
         Cand c{num, dg, (dv + R) * ow + (du + R)};
@@ -495,9 +503,9 @@ __device__ __forceinline__ void insert4(Cand t[4], Cand c) {
     }
 }
 
-__device__ __forceinline__ double cand_score(const Cand& c) {
-  const double n = (double)c.num;
-  return n * fabs(n) / (double)c.dg;  // sign(C) C^2 Df
+__device__ __forceinline__ float cand_score(const Cand& c) {
+  const float n = ll_to_float(c.num);
+  return n * fabsf(n) / ll_to_float(c.dg);  // sign(C) C^2 Df
 }
 
 __global__ void reduce_kernel(const SearchTcParams p) {
@@ -530,13 +538,13 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   }
   Cand top[4];
   int ntop = 0;
-  double w0 = 0.0;
+  float w0 = 0.f;
   for (int k = 0; k < 4; ++k) {
     if (k == 1) {
       // later rounds only if some remaining candidate scores within 1e-3 of
       // the winner (only those can be reordered by the re-rank)
-      const double sc = loc[0].l == INT_MAX ? -1e300 : cand_score(loc[0]);
-      if (!__any_sync(0xffffffffu, sc >= w0 - 1e-3 * fabs(w0))) break;
+      const float sc = loc[0].l == INT_MAX ? -3.0e38f : cand_score(loc[0]);
+      if (!__any_sync(0xffffffffu, sc >= w0 - 1e-3f * fabsf(w0))) break;
     }
     Cand c = loc[0];
 #pragma unroll
@@ -558,9 +566,9 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     }
   }
   Cand best{0, 1, INT_MAX};
-  const double w = ntop ? cand_score(top[0]) : 0.0;
+  const float w = ntop ? cand_score(top[0]) : 0.f;
   for (int k = 0; k < ntop; ++k) {
-    if (k > 0 && cand_score(top[k]) < w - 1e-3 * fabs(w)) continue;
+    if (k > 0 && cand_score(top[k]) < w - 1e-3f * fabsf(w)) continue;
     const int du = top[k].l % ow - R, dv = top[k].l / ow - R;
     long long sab = 0, sb = 0, sbb = 0;
     for (int ty = 0; ty < S; ++ty) {
