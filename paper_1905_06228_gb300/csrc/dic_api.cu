@@ -67,6 +67,42 @@ bool encode_u8(CUtensorMap* tm, const uint8_t* base, int W, int H, int pitch, in
   return r == CUDA_SUCCESS;
 }
 
+// Tensor maps of the tensor-core search (BF16).  A box lands as 8-row
+// groups of operand rows of TWK taps (2*TWK bytes, the swizzle width):
+//  A: 3-D over the eight phase images [8][phh][phw]: (column, phase r,
+//     image row), box (TWK, 8, tile rows): image row = group, r = row;
+//  B: 4-D over the template bank [ny][S][nx][twk]: (tap, POI column, POI
+//     row, template row), box (TWK, ncols, nrows, 1): a tile's POI block.
+bool encode_tc(CUtensorMap* tma, CUtensorMap* tmb, const dic::SearchTcParams& t) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const CUtensorMapSwizzle sw = t.twk == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : t.twk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                              : CU_TENSOR_MAP_SWIZZLE_32B;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)t.phw, 8, (cuuint64_t)t.phh};
+    cuuint64_t str[2] = {(cuuint64_t)t.phh * t.phw * 2, (cuuint64_t)t.phw * 2};
+    cuuint32_t box[3] = {(cuuint32_t)t.twk, 8, (cuuint32_t)t.arows};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (fn(tma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, t.gph, dims, str, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    const cuuint64_t row = (cuuint64_t)t.nx * t.twk * 2;  // bytes per template row
+    cuuint64_t dims[4] = {(cuuint64_t)t.twk, (cuuint64_t)t.nx, (cuuint64_t)t.ny, (cuuint64_t)t.S};
+    cuuint64_t str[3] = {(cuuint64_t)t.twk * 2, row * t.S, row};
+    cuuint32_t box[4] = {(cuuint32_t)t.twk, (cuuint32_t)t.ncols_max, (cuuint32_t)t.nrows_max, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if (fn(tmb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, t.bank, dims, str, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 void grid_of(int W, int H, int S, int step, int R, int* nx, int* ny) {
   const int B = S / 2 + R + 2;
   const int ax = W - 1 - 2 * B, ay = H - 1 - 2 * B;
@@ -361,8 +397,8 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
       }
       h->tc_posbox_elems = pbe;
     }
-    t.fph = h->tc_phase;
-    t.gph = h->tc_phase + phase / 2;
+    t.gph = h->tc_phase;
+    t.bank = h->tc_phase + dic::search_tc_gph_elems(t);
     t.fbox = h->tc_fbox;
     t.slots = h->tc_slots;
     t.posbox = h->tc_posbox;
@@ -371,7 +407,10 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
     t.zncc0 = zncc0;
     t.status = status;
     t.err_flag = h->err_flag;
-    cudaError_t e = dic::launch_search_tc(t, h->stream);
+    CUtensorMap tma, tmb;
+    if (!encode_tc(&tma, &tmb, t))
+      return fail(h, DIC_ERR_UNSUPPORTED, "tensor-core search: tensor map encoding failed");
+    cudaError_t e = dic::launch_search_tc(t, &tma, &tmb, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "tensor-core search launch");
     return DIC_OK;
   }

@@ -63,13 +63,15 @@ struct SearchTcParams {
   int64_t n_pois;
   int twk;           // template row width padded to 16 taps
   int npad;          // N of the MMA (POIs per tile block, padded to 16)
-  int ncols_max, nrows_max;
+  int ncols_max, nrows_max;  // POI block of a tile (columns, rows)
+  int arows;                 // image rows of a tile's A buffer
   int rows_per_acc;  // template rows per exact FP32 accumulator
   int tmem_cols;
+  int stages;        // template-row stages of the tile kernel's ring
   int xmin, ymin, ntx, nty;
   int slots_x, slots_y, nslots;
-  uint16_t* fph;     // [8][phh][phw] centred BF16 copies of f shifted by 0..7
-  uint16_t* gph;     // same for g
+  uint16_t* bank;    // [ny][S][nx][twk] centred BF16 subsets of f (POI-major rows)
+  uint16_t* gph;     // [8][phh][phw] centred BF16 copies of g shifted by 0..7
   int phh, phw;
   int2* fbox;        // like posbox, for the reference image (POI sums)
   SlotCand* slots;   // [n_pois][nslots]
@@ -135,8 +137,10 @@ cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
 bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, SearchTcParams* g);
 size_t search_tc_smem(const SearchTcParams& g);
 size_t search_tc_posbox_elems(const SearchTcParams& g);
-size_t search_tc_phase_elems(const SearchTcParams& g);
-cudaError_t launch_search_tc(const SearchTcParams& p, cudaStream_t st);
+size_t search_tc_phase_elems(const SearchTcParams& g);  // phase images + template bank
+size_t search_tc_gph_elems(const SearchTcParams& g);
+cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
+                             const CUtensorMap* tmB, cudaStream_t st);
 
 // Persistent multi-pair launchers.  jobs / offsets are device arrays; the
 // POIs of job k are items [offsets[k], offsets[k+1]); counter starts at 0.

@@ -44,20 +44,25 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kTileQ = 16;  // position rows per tile
 constexpr int kTileR = 8;   // position columns per tile
-constexpr int kStages = 3;  // template-row stages in flight
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// 64-bit shared-memory matrix descriptor: K-major, no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// 64-bit shared-memory matrix descriptor, K-major with a row swizzle of
+// `rb` bytes (32, 64 or 128: each operand row holds rb bytes of K, 8-row
+// groups are 8*rb bytes apart, 16-byte chunks XOR-permuted within a group
+// exactly as the TMA's swizzle of the same width writes them).  Steps of K
+// inside a row advance the start address; the leading offset is unused.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, int rb) {
+  const uint64_t layout = rb == 128 ? 2 : rb == 64 ? 4 : 6;  // SWIZZLE_128B / 64B / 32B
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
-  return d;               // base offset 0, relative LBO, layout "no swizzle" (0)
+  d |= (uint64_t)1 << 16;                               // leading byte offset (unused)
+  d |= (uint64_t)(((8 * rb) >> 4) & 0x3FFF) << 32;      // stride byte offset: 8-row group
+  d |= (uint64_t)1 << 46;                               // descriptor version for tcgen05
+  d |= layout << 61;
+  return d;
 }
 
 // Instruction descriptor: kind::f16, BF16 A and B, FP32 D, both K-major.
@@ -69,14 +74,19 @@ __host__ __device__ __forceinline__ uint32_t make_idesc(int M, int N) {
          | ((uint32_t)(M >> 4) << 24); // M / 16
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
-  for (long long i = 0; i < limit; ++i) {
+// Wait for the phase of the given parity to complete.  Each try_wait may
+// park the thread for up to kSuspendNs (it wakes when the phase completes),
+// so waiting threads take no issue slots; after `limit` tries (about
+// limit * 10 us) the wait gives up and returns false.
+constexpr uint32_t kSuspendNs = 10000;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; "
         "selp.u32 %0, 1, 0, p; }"
         : "=r"(done)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
   }
@@ -89,11 +99,12 @@ struct Cand {
 };
 
 // float of an exact 64-bit integer without the 64-bit conversion (which runs
-// on the FP64 pipe): hi * 2^32 + lo, relative error ~1e-7
+// on the FP64 pipe): sign * (hi * 2^32 + lo) of the magnitude, relative
+// error below 2^-23 for |v| < 2^56
 __device__ __forceinline__ float ll_to_float(long long v) {
-  const int hi = (int)(v >> 32);
-  const unsigned lo = (unsigned)(v & 0xffffffffll);
-  return fmaf((float)hi, 4294967296.0f, (float)lo);
+  const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+  const float f = fmaf((float)(unsigned)(a >> 32), 4294967296.0f, (float)(unsigned)a);
+  return v < 0 ? -f : f;
 }
 
 __device__ __forceinline__ bool zncc_greater(long long na, long long da, long long nb,
@@ -116,22 +127,18 @@ __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
 }
 
 // ------------------------------------------------------------ phase images
-// Eight copies of each image shifted by s = 0..7 pixels, as centred BF16:
-//   ph[img][s][y][c] = I[y][c + s] - 128  (0 outside the image)
+// Eight copies of the deformed image shifted by s = 0..7 pixels, as centred
+// BF16:  ph[s][y][c] = g[y][c + s] - 128  (0 outside the image),
 // so that any run of 8 consecutive pixels starting at column x is one
 // aligned 16-byte chunk: copy s = x mod 8 at column x - s.  One thread per
 // 16-byte chunk.
 __global__ void phase_kernel(const SearchTcParams p) {
   const int64_t chunk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int cpr = p.phw / 8;  // chunks per row
-  const int64_t per_img = (int64_t)8 * p.phh * cpr;
-  if (chunk >= 2 * per_img) return;
-  const int im = (int)(chunk / per_img);
-  int64_t rem = chunk % per_img;
-  const int sft = (int)(rem / ((int64_t)p.phh * cpr));
-  rem %= (int64_t)p.phh * cpr;
+  if (chunk >= (int64_t)8 * p.phh * cpr) return;
+  const int sft = (int)(chunk / ((int64_t)p.phh * cpr));
+  const int64_t rem = chunk % ((int64_t)p.phh * cpr);
   const int y = (int)(rem / cpr), c = (int)(rem % cpr) * 8;
-  const uint8_t* src = im ? p.def : p.ref;
   uint32_t w[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -139,13 +146,46 @@ __global__ void phase_kernel(const SearchTcParams p) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int x = c + sft + 2 * e + k;
-      const int v = (x < p.W && y < p.H) ? (int)src[(size_t)y * p.pitch + x] - 128 : 0;
+      const int v = (x < p.W && y < p.H) ? (int)p.def[(size_t)y * p.pitch + x] - 128 : 0;
       h2[k] = __float_as_uint((float)v) >> 16;  // small integers are exact in BF16
     }
     w[e] = h2[0] | (h2[1] << 16);
   }
-  uint16_t* dst = (im ? p.gph : p.fph) + ((size_t)sft * p.phh + y) * p.phw + c;
+  uint16_t* dst = p.gph + ((size_t)sft * p.phh + y) * p.phw + c;
   *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// ------------------------------------------------------------ template bank
+// Every POI's subset of f, centred BF16, rows padded to TWK taps with zeros:
+//   bank[((kr*S + ty)*nx + kc)*TWK + tx] = f[yl+ty][xl+tx] - 128  (tx < S)
+// with (xl, yl) the subset's top-left.  Row ty of the POIs of one grid row
+// is contiguous, so a tile's template rows stream as runs of 16-byte chunks.
+// One thread per 16-byte chunk.
+__global__ void bank_kernel(const SearchTcParams p) {
+  const int KB = p.twk / 8;
+  const int64_t chunk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (chunk >= (int64_t)p.ny * p.S * p.nx * KB) return;
+  const int kb = (int)(chunk % KB);
+  int64_t rest = chunk / KB;
+  const int kc = (int)(rest % p.nx);
+  rest /= p.nx;
+  const int ty = (int)(rest % p.S), kr = (int)(rest / p.S);
+  const int B = p.M + p.R + 2;
+  const int xl = B + kc * p.step - p.M, yl = B + kr * p.step - p.M;
+  const uint8_t* src = p.ref + (size_t)(yl + ty) * p.pitch + xl;
+  uint32_t w[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    uint32_t h2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int tx = 8 * kb + 2 * e + k;
+      const int v = tx < p.S ? (int)src[tx] - 128 : 0;
+      h2[k] = __float_as_uint((float)v) >> 16;
+    }
+    w[e] = h2[0] | (h2[1] << 16);
+  }
+  *reinterpret_cast<uint4*>(p.bank + chunk * 8) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // ------------------------------------------------------------ box-sum map
@@ -156,7 +196,7 @@ constexpr int kBoxT = 32;
 __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p, int which) {
   const uint8_t* img = which ? p.def : p.ref;
   int2* out = which ? p.posbox : p.fbox;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   const int S = p.S, span = kBoxT + S - 1;
   int* rowb = reinterpret_cast<int*>(smem);          // [span][span] bytes - 128
   int2* hs = reinterpret_cast<int2*>(rowb + span * span);  // [span][kBoxT]
@@ -194,54 +234,209 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p, int
 }
 
 // ------------------------------------------------------------ tile kernel
+// Roles.  Thread 0 streams the template rows B(ty) into a ring of p.stages
+// shared-memory stages with TMA (one box per 8-POI group, arriving on
+// full[ty]); thread 32 issues the MMAs of row ty once full[ty] completes and
+// commits them to empty[ty], which lets the producer refill that stage.  The
+// other threads wait at the block barrier before the epilogue.
+constexpr int kMaxStages = 6;
+constexpr int kWaitLimit = 1 << 17;  // try_wait calls before giving up (~1.3 s)
+
 struct TileLayout {
   int rows;    // image rows of the tile: kTileQ + S - 1
-  int KB;      // 8-tap blocks per template row: TWK / 8
-  int sboA;    // bytes per image row in the A buffer: KB * 128
-  int stageB;  // bytes per template-row stage: KB * Npad * 16 (8-row groups of KB*128)
-  size_t off_bar, off_tmem, off_pos, off_a, off_b, off_d, total;
+  int RB;      // bytes of one operand row (TWK taps): the swizzle width
+  int grp;     // bytes of an 8-row group: 8 * RB (one image row of A)
+  int stageB;  // bytes per template-row stage: Npad * RB
+  size_t off_bar, off_tmem, off_pos, off_poi, off_red, off_a, off_b, off_d, total;
 };
 
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline TileLayout tile_layout(int S, int TWK, int npad) {
+constexpr int kPos = kTileQ * kTileR;  // positions per tile (the MMA's M)
+constexpr int kDs = kPos + 1;          // row stride of the transposed sums
+
+__host__ __device__ inline TileLayout tile_layout(int S, int TWK, int npad, int stages) {
   TileLayout L;
   L.rows = kTileQ + S - 1;
-  L.KB = TWK / 8;
-  L.sboA = L.KB * 128;
-  L.stageB = L.KB * npad * 16;
+  L.RB = 2 * TWK;
+  L.grp = 8 * L.RB;
+  L.stageB = npad * L.RB;
   size_t o = 0;
-  L.off_bar = o;  o += 8 * (kStages + 1);
+  L.off_bar = o;  o += 8 * (2 * kMaxStages + 2);
   L.off_tmem = o; o += 8;
-  o = al(o, 16);  L.off_pos = o;  o += (size_t)kTileQ * kTileR * 16;  // dg, sb, 1/dg
-  o = al(o, 128);
-  // A buffer and B stages; the transposed accumulator reuses this region
-  // once the last MMA has completed
-  const size_t ab = (size_t)L.rows * L.sboA + (size_t)kStages * L.stageB;
-  const size_t dd = (size_t)npad * (kTileQ * kTileR + 1) * 4;
+  o = al(o, 16);  L.off_pos = o;  o += (size_t)kPos * 16;    // dg, sb, 1/dg
+  L.off_poi = o;  o += (size_t)npad * 16;                    // per-POI window and sums
+  L.off_red = o;  o += (size_t)4 * npad * 8;                 // per-quarter best two
+  o = al(o, 1024);  // swizzle atoms of the operands start on 1024-byte boundaries
+  // A buffer and B stages; the transposed sums reuse this region once the
+  // last MMA has completed
+  const size_t ab = (size_t)L.rows * L.grp + (size_t)stages * L.stageB;
+  const size_t dd = (size_t)npad * kDs * 4;
   L.off_a = o;
-  L.off_b = o + (size_t)L.rows * L.sboA;
+  L.off_b = o + (size_t)L.rows * L.grp;
   L.off_d = o;
   o += ab > dd ? ab : dd;
   L.total = o;
   return L;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams p) {
+// Per-POI data of a tile's block.  cx, cy: left / top end of the POI's
+// window in tile coordinates (a position (q, r) of the tile is in the window
+// iff 0 <= r - cx <= 2R and 0 <= q - cy <= 2R); kNoPoi for a padding column
+// or a POI without reference variance.
+struct PoiInfo {
+  int cx, cy;
+  float saf;  // Sa as float (exact: |Sa| < 2^24)
+  int sa;
+};
+constexpr int kNoPoi = -(1 << 20);
+constexpr int kSlotNearTie = 1 << 30;  // flag in SlotCand::l: tile winner not certain
+
+// Order-preserving map of a float onto int (larger float -> larger int).
+__device__ __forceinline__ int f2key(float s) {
+  const int i = __float_as_int(s);
+  return i ^ ((i >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float key2f(int k) {
+  return __int_as_float(k ^ ((k >> 31) & 0x7fffffff));
+}
+
+// Best-two merge of (largest, second largest) key pairs.
+__device__ __forceinline__ void merge2(int& mx, int& sc, int omx, int osc) {
+  sc = max(max(sc, osc), min(mx, omx));
+  mx = max(mx, omx);
+}
+
+// One halving step of the warp reduce-scatter: 2H (largest, second) pairs
+// per lane become H, each merged with the partner lane's matching pair.
+template <int H>
+__device__ __forceinline__ void bfly(int (&mx)[8], int (&sc)[8], bool up, int o) {
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const int smx = up ? mx[i] : mx[i + H], ssc = up ? sc[i] : sc[i + H];
+    int kmx = up ? mx[i + H] : mx[i], ksc = up ? sc[i + H] : sc[i];
+    const int rmx = __shfl_xor_sync(0xffffffffu, smx, o);
+    const int rsc = __shfl_xor_sync(0xffffffffu, ssc, o);
+    merge2(kmx, ksc, rmx, rsc);
+    mx[i] = kmx;
+    sc[i] = ksc;
+  }
+}
+
+// Scores of one (quarter, 16-column) block of the accumulator and their
+// per-POI best two over the quarter's 32 positions.
+//
+// Position m = 32*quarter + lane (row q = m/8, column r = m%8 of the tile)
+// holds the sums of POIs c0..c0+15.  The score sign(num) num^2 / Dg orders a
+// POI's candidates like its ZNCC.  Without wide sums (one accumulator,
+// |Sab| < 2^24 exact in FP32) num is formed in FP32 from exact operands:
+// Sa*Sb as an exact two-float product, N*Sab - hi in one FMA, then - lo;
+// its error is at most 2^-23 |num| + 2^-14.  With wide sums num is exact in
+// 64-bit integers and only the final conversion rounds.  Either way a
+// score's relative error, including the position index packed into the
+// low 7 bits of its key, stays below 1.5e-4 for num != 0, and |score| <
+// 4e-9 when num = 0; the winner test in the tile kernel relies on this.
+template <bool kWide>
+__device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tmem, int nacc,
+                                            int quarter, int lane, int c0, int rr, int q,
+                                            float sbf, int sb, float pinv_m, const PoiInfo* poi,
+                                            int* dsm, int2* red) {
+  const int NP = p.npad, R2 = 2 * p.R, m = quarter * 32 + lane;
+  const long long N = (long long)p.S * p.S;
+  const float Nf = (float)N;
+  // val: the exact FP32 sums (one accumulator) or int32 sums (several)
+  uint32_t val[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) val[k] = 0;
+  for (int a = 0; a < nacc; ++a) {
+    uint32_t v[16];
+    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * NP + c0);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      val[k] = kWide ? (uint32_t)((int)val[k] + __float2int_rn(__uint_as_float(v[k]))) : v[k];
+  }
+  int mx[8], sc[8];
+  int key[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    dsm[(c0 + k) * kDs + m] = (int)val[k];
+    const PoiInfo pi = poi[c0 + k];
+    const bool in = (unsigned)(rr - pi.cx) <= (unsigned)R2 && (unsigned)(q - pi.cy) <= (unsigned)R2;
+    float nf;
+    if (kWide) {
+      nf = ll_to_float(N * (long long)(int)val[k] - (long long)pi.sa * sb);
+    } else {
+      const float hi = pi.saf * sbf;
+      const float lo = fmaf(pi.saf, sbf, -hi);
+      nf = fmaf(Nf, __uint_as_float(val[k]), -hi) - lo;
+    }
+    const float s = nf * fabsf(nf) * pinv_m;
+    key[k] = in ? ((f2key(s) & ~127) | m) : INT_MIN;
+  }
+  // reduce-scatter over the 32 lanes: 16 -> 8 -> 4 -> 2 -> 1 pairs
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int s_ = up ? key[i] : key[i + 8];
+      const int k_ = up ? key[i + 8] : key[i];
+      const int r_ = __shfl_xor_sync(0xffffffffu, s_, 16);
+      mx[i] = max(k_, r_);
+      sc[i] = min(k_, r_);
+    }
+  }
+  bfly<4>(mx, sc, lane & 8, 8);
+  bfly<2>(mx, sc, lane & 4, 4);
+  bfly<1>(mx, sc, lane & 2, 2);
+  {
+    const int rmx = __shfl_xor_sync(0xffffffffu, mx[0], 1);
+    const int rsc = __shfl_xor_sync(0xffffffffu, sc[0], 1);
+    merge2(mx[0], sc[0], rmx, rsc);
+  }
+  if ((lane & 1) == 0) {
+    const int j = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                  ((lane >> 1) & 1);
+    red[quarter * NP + c0 + j] = make_int2(mx[0], sc[0]);
+  }
+}
+
+// POI n of a tile's block (row-major over ncols_max x nrows_max): operand
+// row n of B.
+__device__ __forceinline__ void block_poi(const SearchTcParams& p, int n, int& bi, int& bj) {
+  bi = n / p.ncols_max;
+  bj = n % p.ncols_max;
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+    tile_kernel(const SearchTcParams p, const __grid_constant__ CUtensorMap tmA,
+                const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = p.S, M = p.M, R = p.R, TWK = p.twk, NP = p.npad;
-  const TileLayout L = tile_layout(S, TWK, NP);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  const int S = p.S, M = p.M, R = p.R, TWK = p.twk, NP = p.npad, NST = p.stages;
+  const TileLayout L = tile_layout(S, TWK, NP, NST);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  uint64_t* empty = full + kMaxStages;
+  uint64_t* done = empty + kMaxStages;
+  uint64_t* abar = done + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.off_tmem);
   long long* pdg = reinterpret_cast<long long*>(smem + L.off_pos);  // Dg per position
-  int* psb = reinterpret_cast<int*>(pdg + kTileQ * kTileR);            // Sb per position
-  float* pinv = reinterpret_cast<float*>(psb + kTileQ * kTileR);       // 1 / Dg
+  int* psb = reinterpret_cast<int*>(pdg + kPos);                     // Sb per position
+  float* pinv = reinterpret_cast<float*>(psb + kPos);                // 1 / Dg
+  PoiInfo* poi = reinterpret_cast<PoiInfo*>(smem + L.off_poi);
+  int2* red = reinterpret_cast<int2*>(smem + L.off_red);
   unsigned char* abuf = smem + L.off_a;
   unsigned char* bbuf = smem + L.off_b;
   int* dsm = reinterpret_cast<int*>(smem + L.off_d);
 
-  // tile origin (absolute positions) and its POI block
+  // tile origin (absolute positions; X0 is a multiple of 8) and its POI block
   const int tile = blockIdx.x;
   const int X0 = p.xmin + (tile % p.ntx) * kTileR;
   const int Y0 = p.ymin + (tile / p.ntx) * kTileQ;
@@ -253,13 +448,36 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
   const int kr0 = max(0, ceil_div(Y0 + M - R - B, p.step));
   const int kc1 = min(p.nx - 1, floor_div(X0 + kTileR - 1 + M + R - B, p.step));
   const int kr1 = min(p.ny - 1, floor_div(Y0 + kTileQ - 1 + M + R - B, p.step));
+  const int nbr = kr1 - kr0 + 1, nbc = kc1 - kc0 + 1;
+  const long long N = (long long)S * S;
+  const int nblock = p.ncols_max * p.nrows_max;  // POIs (operand rows) loaded per row
+  const uint32_t row_bytes = (uint32_t)(nblock * L.RB);
 
-  // ---- setup: barriers, TMEM allocation (warp 0)
+  // ---- setup: barriers and the A buffer (one TMA: for image rows Y0 ..
+  // Y0+rows-1 and positions r = 0..7 of the tile's row, the TWK taps from
+  // column X0 + r, i.e. row r of phase image r; 8-row group = image row):
+  //   A row (row, r), tap k = g[Y0+row][X0 + r + k] - 128  (0 beyond the
+  // phase images; taps at or beyond S meet zero template taps),
+  // then TMEM allocation (warp 0)
   const uint32_t ncols = p.tmem_cols;
   if (tid == 0) {
-    for (int i = 0; i <= kStages; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+    for (int i = 0; i < NST; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(abar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(abar)),
+                 "r"((uint32_t)(L.rows * L.grp))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(abuf)),
+        "l"(&tmA), "r"(X0), "r"(0), "r"(Y0), "r"(smem_u32(abar))
+        : "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -269,8 +487,7 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   // ---- per-position box statistics (from the map)
-  const long long N = (long long)S * S;
-  if (tid < kTileQ * kTileR) {
+  if (tid < kPos) {
     const int q = tid / kTileR, r = tid % kTileR;
     const int2 bx = p.posbox[(size_t)(Y0 - p.ymin + q) * (p.ntx * 8) + (X0 - p.xmin + r)];
     const long long dg = N * (long long)bx.y - (long long)bx.x * bx.x;
@@ -278,76 +495,69 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
     psb[tid] = bx.x;
     pinv[tid] = dg ? 1.0f / ll_to_float(dg) : 0.f;
   }
-  // ---- A buffer: eight shifted copies per image row and 8-tap block,
-  //   abuf[row*sboA + kb*128 + r*16 + e*2] = g[Y0+row][X0 + r + 8kb + e] - 128,
-  // one aligned 16-byte chunk of phase image (X0 + r) mod 8 each; taps at or
-  // beyond S are zero-filled (the template's padding)
-  for (int i = tid; i < L.rows * L.KB * 8; i += kThreads) {
-    const int row = i / (L.KB * 8), rem = i % (L.KB * 8), kb = rem >> 3, r = rem & 7;
-    const int x = X0 + r + 8 * kb, sft = x & 7;
-    const uint16_t* src = p.gph + ((size_t)sft * p.phh + (Y0 + row)) * p.phw + (x - sft);
-    const int valid = min(max(S - 8 * kb, 0), 8);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(
-                     smem_u32(abuf + row * L.sboA + kb * 128 + r * 16)),
-                 "l"(src), "r"(2 * valid)
-                 : "memory");
+  // ---- per-POI window and reference sums
+  for (int n = tid; n < NP; n += kThreads) {
+    int bi, bj;
+    block_poi(p, n, bi, bj);
+    PoiInfo pi{kNoPoi, kNoPoi, 0.f, 0};
+    if (n < nblock && bi < nbr && bj < nbc) {
+      const int xl = B + (kc0 + bj) * p.step - M, yl = B + (kr0 + bi) * p.step - M;
+      const int2 fb = p.fbox[(size_t)(yl - p.ymin) * (p.ntx * 8) + (xl - p.xmin)];
+      // a POI without reference variance is decided by the reduce kernel
+      if (N * (long long)fb.y - (long long)fb.x * fb.x != 0)
+        pi = PoiInfo{xl - X0 - R, yl - Y0 - R, (float)fb.x, fb.x};
+    }
+    poi[n] = pi;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // ---- main loop over template rows: B(ty) streams two rows ahead of the
-  // MMAs; a stage is refilled once the MMAs that read it have committed
-  const int nbr = kr1 - kr0 + 1, nbc = kc1 - kc0 + 1;
-  const uint32_t idesc = make_idesc(128, NP);
   const int rows_per_acc = p.rows_per_acc;
-  // this thread's 16-byte copies (same for every ty): POI n of the block,
-  // 8-tap block kb; at most NP*KB/256 <= 8 per thread
-  constexpr int kMaxCopies = 8;
-  const uint16_t* csrc[kMaxCopies];
-  uint32_t cdst[kMaxCopies], cbytes[kMaxCopies];
-  int ncopy = 0;
-  for (int i = tid; i < NP * L.KB && ncopy < kMaxCopies; i += kThreads, ++ncopy) {
-    const int n = i % NP, kb = i / NP;
-    const int bi = n / p.ncols_max, bj = n % p.ncols_max;
-    const bool have = n < p.nrows_max * p.ncols_max && bi < nbr && bj < nbc;
-    // template row ty of POI (kr, kc): f[yl + ty][xl + 8kb .. +7]
-    const int xl = have ? B + (kc0 + bj) * p.step - M : 0;
-    const int yl = have ? B + (kr0 + bi) * p.step - M : 0;
-    const int x = xl + 8 * kb, sft = x & 7;
-    csrc[ncopy] = p.fph + ((size_t)sft * p.phh + yl) * p.phw + (x - sft);
-    cdst[ncopy] = (uint32_t)((n >> 3) * L.KB * 128 + kb * 128 + (n & 7) * 16);
-    cbytes[ncopy] = have ? 16u : 0u;
-  }
-  const uint32_t bbase = smem_u32(bbuf);
-  auto issue_b = [&](int row) {
-    const uint32_t stage = bbase + (uint32_t)((row % kStages) * L.stageB);
-    for (int k = 0; k < ncopy; ++k)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(stage + cdst[k]),
-                   "l"(csrc[k] + (size_t)row * p.phw), "r"(cbytes[k])
+  int failed = 0, issued = 0;
+  if (tid == 0) {
+    // ---- producer: template row ty of every POI of the block into stage
+    // ty % NST with one TMA: the ncols_max x nrows_max patch of the bank
+    // lands as operand rows n = bi * ncols_max + bj of TWK taps (swizzled)
+    const uint32_t bbase = smem_u32(bbuf);
+    for (int ty = 0; ty < S; ++ty, ++issued) {
+      const int st = ty % NST;
+      if (ty >= NST &&
+          !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((ty / NST) - 1) & 1), kWaitLimit)) {
+        failed = 1;
+        break;
+      }
+      const uint32_t fb = smem_u32(&full[st]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                   "r"(row_bytes)
                    : "memory");
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  int failed = 0;
-  issue_b(0);
-  if (S > 1) issue_b(1);
-  for (int ty = 0; ty < S; ++ty) {
-    if (ty + 1 < S)
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+      const uint32_t stage = bbase + (uint32_t)(st * L.stageB);
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+          "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(stage),
+          "l"(&tmB), "r"(0), "r"(kc0), "r"(kr0), "r"(ty), "r"(fb)
+          : "memory");
+    }
+  } else if (tid == 32) {
+    // ---- MMA issuer
+    const uint32_t idesc = make_idesc(128, NP);
+    const uint32_t bbase = smem_u32(bbuf);
+    if (!mbar_wait(smem_u32(abar), 0, kWaitLimit)) failed = 1;
+    for (int ty = 0; ty < S && !failed; ++ty) {
+      const int st = ty % NST;
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((ty / NST) & 1), kWaitLimit)) {
+        failed = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int acc = ty / rows_per_acc;
       const uint32_t dcol = tmem + (uint32_t)(acc * NP);
-      const uint32_t a_base = smem_u32(abuf) + (uint32_t)(ty * L.sboA);
-      const uint32_t b_base = bbase + (uint32_t)((ty % kStages) * L.stageB);
-      for (int j = 0; j < TWK / 16; ++j) {
-        const uint64_t ad = make_desc(a_base + j * 256, 128, (uint32_t)L.sboA);
-        const uint64_t bd = make_desc(b_base + j * 256, 128, (uint32_t)L.sboA);
+      const uint32_t a_base = smem_u32(abuf) + (uint32_t)(ty * L.grp);
+      const uint32_t b_base = bbase + (uint32_t)(st * L.stageB);
+      for (int j = 0; j < TWK / 16; ++j) {  // 16 taps (32 bytes) per MMA
+        const uint64_t ad = make_desc(a_base + j * 32, L.RB);
+        const uint64_t bd = make_desc(b_base + j * 32, L.RB);
         const uint32_t accum = (ty % rows_per_acc == 0 && j == 0) ? 0u : 1u;
         asm volatile(
             "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
@@ -357,70 +567,42 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&bars[ty % kStages]))
+              smem_u32(&empty[st]))
           : "memory");
     }
-    if (ty + 2 < S) {
-      // stage (ty+2) % 3 was read by the MMAs of row ty-1: one thread polls
-      // their commit, the others sleep at the barrier
-      if (ty >= 1) {
-        if (tid == 0) {
-          const int prev = ty - 1;
-          const uint32_t par = (uint32_t)((prev / kStages) & 1);
-          if (!mbar_wait(smem_u32(&bars[prev % kStages]), par, 1ll << 26)) failed = 1;
-        }
-        __syncthreads();
-      }
-      issue_b(ty + 2);
-    }
-  }
-  bool ok = !__syncthreads_or(failed);
-  // all MMAs done: commit once more on the last barrier and wait
-  if (ok && tid == 0) {
+    // every MMA issued so far (all of them, or those before a failure)
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&bars[kStages]))
+            smem_u32(done))
         : "memory");
+    if (!mbar_wait(smem_u32(done), 0, kWaitLimit)) failed = 1;
   }
-  {
-    const int failed = (ok && tid == 0) ? !mbar_wait(smem_u32(&bars[kStages]), 0, 1ll << 26) : 0;
-    if (__syncthreads_or(failed)) ok = false;
-  }
-  if (!ok) {
-    if (tid == 0) {
-      atomicOr(p.err_flag, 2u);
-      // give in-flight tensor-core work a bounded chance to finish
-      mbar_wait(smem_u32(&bars[kStages]), 0, 1ll << 24);
-    }
-    __syncthreads();
+  const bool ok = !__syncthreads_or(failed);
+  if (!ok && tid == 0) {
+    atomicOr(p.err_flag, 2u);
+    // let the copies still in flight land (bounded) before the CTA leaves
+    mbar_wait(smem_u32(abar), 0, kWaitLimit / 16);
+    for (int j = max(0, issued - NST); j < issued; ++j)
+      mbar_wait(smem_u32(&full[j % NST]), (uint32_t)((j / NST) & 1), kWaitLimit / 16);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  // ---- accumulators -> shared memory, transposed: dsm[n][m] (int32 sums)
+  // ---- scores: each warp takes one lane quarter of the accumulator (32
+  // positions) and 16-column blocks of POIs; sums also go to shared memory,
+  // transposed (dsm[n][m]), for the exact winner
   const int nacc = (S + rows_per_acc - 1) / rows_per_acc;
   if (ok) {
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
-    const int m = quarter * 32 + lane;
+    const int quarter = warp & 3, m = quarter * 32 + lane, q = m / kTileR, r = m % kTileR;
+    const int rr = pdg[m] != 0 ? r : r + (1 << 21);  // Dg = 0: in no window
+    const float pinv_m = pinv[m];
+    const int sb = psb[m];
+    const float sbf = (float)sb;
     for (int c0 = (warp >> 2) * 16; c0 < NP; c0 += (kThreads / 128) * 16) {
-      int sum[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) sum[k] = 0;
-      for (int a = 0; a < nacc; ++a) {
-        uint32_t v[16];
-        const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * NP + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(addr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sum[k] += __float2int_rn(__uint_as_float(v[k]));
-      }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) dsm[(c0 + k) * (kTileQ * kTileR + 1) + m] = sum[k];
+      if (nacc > 1)
+        score_block<true>(p, tmem, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, dsm, red);
+      else
+        score_block<false>(p, tmem, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, dsm,
+                           red);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -432,80 +614,66 @@ __global__ void __launch_bounds__(kThreads, 3) tile_kernel(const SearchTcParams 
   }
   if (!ok) return;
 
-  // ---- per-POI scan of the tile's positions (two threads per POI when the
-  // block has at most 128 POIs: even and odd position rows)
-  const int split = NP <= kThreads / 2 ? 2 : 1;
-  const int n = tid / split, half = tid % split;
-  const bool active = n < NP;
-  const int bi = active ? n / p.ncols_max : 0, bj = active ? n % p.ncols_max : 0;
-  const bool valid_poi =
-      active && n < p.nrows_max * p.ncols_max && bi < nbr && bj < nbc;
-  const int kr = kr0 + bi, kc = kc0 + bj;
-  const int64_t poi = (int64_t)kr * p.nx + kc;
-  const int xl = B + kc * p.step - M, yl = B + kr * p.step - M;  // POI's subset top-left
+  // ---- per-POI winner of the tile: merge the four quarters' best two.  The
+  // float winner's sums are exact; it is the exact winner of the tile if it
+  // clears every other candidate by 1e-3 (relative) and is above 1e-8 (score
+  // errors stay below 1.5e-4 and num != 0 there).  Otherwise the slot is
+  // flagged (kSlotNearTie) and the reduce kernel resolves it exactly if it
+  // can matter.
+  const int wide = nacc > 1;
   const int ow = 2 * R + 1;
-  Cand best{0, 1, INT_MAX};
-  if (valid_poi) {
-    const int2 fb = p.fbox[(size_t)(yl - p.ymin) * (p.ntx * 8) + (xl - p.xmin)];
-    const long long sa = fb.x;
-    float best_f = -3.0e38f;
-    const int* drow = dsm + n * (kTileQ * kTileR + 1);
-    const int r_lo = max(0, xl - R - X0), r_hi = min(kTileR - 1, xl + R - X0);
-    const int q_lo = max(0, yl - R - Y0), q_hi = min(kTileQ - 1, yl + R - Y0);
-    for (int q = q_lo + half; q <= q_hi; q += split)
-      for (int r = r_lo; r <= r_hi; ++r) {
-        const int m = q * kTileR + r;
-        const int du = X0 + r - xl, dv = Y0 + q - yl;
-        const long long dg = pdg[m];
-        if (dg == 0) continue;
-        const long long num = N * (long long)drow[m] - sa * (long long)psb[m];
-        const float fn = ll_to_float(num);
-        const float score = fn * fabsf(fn) * pinv[m];  // sign(C) C^2 Df
-        if (score < best_f - 1e-5f * fabsf(best_f) - 1e-30f) continue;
-        Cand c{num, dg, (dv + R) * ow + (du + R)};
-        if (cand_better(c, best)) {
-          best = c;
-          best_f = fmaxf(best_f, score);
-        }
-      }
+  for (int n = tid; n < NP; n += kThreads) {
+    const PoiInfo pi = poi[n];
+    if (pi.cx == kNoPoi) continue;
+    int mx = red[n].x, sc = red[n].y;
+#pragma unroll
+    for (int qq = 1; qq < 4; ++qq) merge2(mx, sc, red[qq * NP + n].x, red[qq * NP + n].y);
+    long long num = 0, dg = 1;
+    int l = INT_MAX;
+    if (mx != INT_MIN) {
+      const int m = mx & 127;
+      const int raw = dsm[n * kDs + m];
+      const int sab = wide ? raw : __float2int_rn(__int_as_float(raw));
+      num = N * (long long)sab - (long long)pi.sa * psb[m];
+      dg = pdg[m];
+      l = (m / kTileR - pi.cy) * ow + (m % kTileR - pi.cx);
+      const float fm = key2f(mx);
+      if (!(fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm))) l |= kSlotNearTie;
+    }
+    int bi, bj;
+    block_poi(p, n, bi, bj);
+    const int64_t poi_k = (int64_t)(kr0 + bi) * p.nx + (kc0 + bj);
+    const int xl = pi.cx + X0 + R, yl = pi.cy + Y0 + R;
+    // slot of this tile among the POI's tiles
+    const int tx_first = (xl - R - p.xmin) / kTileR, ty_first = (yl - R - p.ymin) / kTileQ;
+    const int slot = ((Y0 - p.ymin) / kTileQ - ty_first) * p.slots_x +
+                     ((X0 - p.xmin) / kTileR - tx_first);
+    SlotCand* s = p.slots + (size_t)poi_k * p.nslots + slot;
+    s->num = num;
+    s->dg = dg;
+    s->l = l;
   }
-  if (split == 2) {  // partner threads are adjacent lanes
-    Cand o;
-    o.num = __shfl_xor_sync(0xffffffffu, best.num, 1);
-    o.dg = __shfl_xor_sync(0xffffffffu, best.dg, 1);
-    o.l = __shfl_xor_sync(0xffffffffu, best.l, 1);
-    if (cand_better(o, best)) best = o;
-  }
-  if (!valid_poi || half) return;
-  // slot of this tile among the POI's tiles
-  const int tx_first = (xl - R - p.xmin) / kTileR, ty_first = (yl - R - p.ymin) / kTileQ;
-  const int slot = ((Y0 - p.ymin) / kTileQ - ty_first) * p.slots_x + ((X0 - p.xmin) / kTileR -
-                                                                     tx_first);
-  SlotCand* sc = p.slots + (size_t)poi * p.nslots + slot;
-  sc->num = best.num;
-  sc->dg = best.dg;
-  sc->l = best.l;
 }
 
 // ------------------------------------------------------------ final reduce
-// One warp per POI: exact top four over the POI's slots (each lane keeps a
-// sorted top four of its slots, then four warp-wide exact argmax rounds),
-// then the re-rank: the winner, and every other of the four whose score is
-// within 1e-3 of it, get their sums recomputed from the images on the CUDA
-// cores and are compared exactly again.
-__device__ __forceinline__ void insert4(Cand t[4], Cand c) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if (cand_better(c, t[k])) {
-      const Cand x = t[k];
-      t[k] = c;
-      c = x;
-    }
+// One warp per POI.  Each lane scores its slots in float from their exact
+// sums (relative error below 1e-6, plus 2^-15 from the slot index packed
+// into the key) and the warp keeps the best two.  If the best slot is
+// certain (not kSlotNearTie), positive above 1e-8 and clears the second by
+// 1e-3, its candidate is the POI's exact winner.  Otherwise every slot
+// within 2e-3 of the best (all of them if the best is not above 1e-8) is
+// resolved exactly: its own candidate, or, for a flagged slot, every
+// position of its tile inside the POI's window with the sums recomputed
+// from the images; the exact maximum wins, lowest linear index on ties.
+// A flagged slot's tile maximum exceeds its stored candidate by at most
+// 3e-4 (relative), so slots below the 2e-3 band cannot hold the winner.
+__device__ __forceinline__ float cand_score(long long num, long long dg) {
+  const float n = ll_to_float(num);
+  return n * fabsf(n) / ll_to_float(dg);  // sign(C) C^2 Df
 }
 
-__device__ __forceinline__ float cand_score(const Cand& c) {
-  const float n = ll_to_float(c.num);
-  return n * fabsf(n) / ll_to_float(c.dg);  // sign(C) C^2 Df
+__device__ __forceinline__ void consider(Cand& best, const Cand& c) {
+  if (cand_better(c, best)) best = c;
 }
 
 __global__ void reduce_kernel(const SearchTcParams p) {
@@ -515,10 +683,10 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   const int S = p.S, M = p.M, R = p.R, ow = 2 * R + 1;
   const int x0 = M + R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + R + 2 + (int)(poi / p.nx) * p.step;
-  const int2 fb = p.fbox[(size_t)(y0 - M - p.ymin) * (p.ntx * 8) + (x0 - M - p.xmin)];
-  const longlong2 fs = make_longlong2(fb.x, fb.y);
+  const int xl = x0 - M, yl = y0 - M;
+  const int2 fb = p.fbox[(size_t)(yl - p.ymin) * (p.ntx * 8) + (xl - p.xmin)];
   const long long N = (long long)S * S;
-  const long long Df = N * fs.y - fs.x * fs.x;
+  const long long Df = N * (long long)fb.y - (long long)fb.x * fb.x;
   if (Df == 0) {
     if (lane == 0) {
       p.u0[poi] = 0;
@@ -528,67 +696,80 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     }
     return;
   }
-  Cand loc[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) loc[k] = Cand{0, 1, INT_MAX};
-  for (int s0 = lane; s0 < p.nslots; s0 += 32) {
-    const SlotCand sc = p.slots[(size_t)poi * p.nslots + s0];
-    // an unwritten slot (all bits set) or a tile without a candidate
-    if (sc.l >= 0 && sc.l < ow * ow) insert4(loc, Cand{sc.num, sc.dg, sc.l});
+  const SlotCand* sl = p.slots + (size_t)poi * p.nslots;
+  auto valid = [&](int l) { return l >= 0 && (l & ~kSlotNearTie) < ow * ow; };
+  int mx = INT_MIN, sc = INT_MIN;
+  for (int s = lane; s < p.nslots; s += 32) {
+    const SlotCand c = sl[s];
+    if (!valid(c.l)) continue;
+    merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~255) | s, INT_MIN);
   }
-  Cand top[4];
-  int ntop = 0;
-  float w0 = 0.f;
-  for (int k = 0; k < 4; ++k) {
-    if (k == 1) {
-      // later rounds only if some remaining candidate scores within 1e-3 of
-      // the winner (only those can be reordered by the re-rank)
-      const float sc = loc[0].l == INT_MAX ? -3.0e38f : cand_score(loc[0]);
-      if (!__any_sync(0xffffffffu, sc >= w0 - 1e-3f * fabsf(w0))) break;
-    }
-    Cand c = loc[0];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      Cand d;
-      d.num = __shfl_xor_sync(0xffffffffu, c.num, o);
-      d.dg = __shfl_xor_sync(0xffffffffu, c.dg, o);
-      d.l = __shfl_xor_sync(0xffffffffu, c.l, o);
-      if (cand_better(d, c)) c = d;
-    }
-    if (c.l == INT_MAX) break;
-    if (k == 0) w0 = cand_score(c);
-    top[ntop++] = c;
-    if (loc[0].l == c.l) {  // positions are unique across slots
-      loc[0] = loc[1];
-      loc[1] = loc[2];
-      loc[2] = loc[3];
-      loc[3] = Cand{0, 1, INT_MAX};
-    }
+  for (int o = 16; o; o >>= 1) {
+    const int omx = __shfl_xor_sync(0xffffffffu, mx, o);
+    const int osc = __shfl_xor_sync(0xffffffffu, sc, o);
+    merge2(mx, sc, omx, osc);
   }
   Cand best{0, 1, INT_MAX};
-  const float w = ntop ? cand_score(top[0]) : 0.f;
-  for (int k = 0; k < ntop; ++k) {
-    if (k > 0 && cand_score(top[k]) < w - 1e-3f * fabsf(w)) continue;
-    const int du = top[k].l % ow - R, dv = top[k].l / ow - R;
-    long long sab = 0, sb = 0, sbb = 0;
-    for (int ty = 0; ty < S; ++ty) {
-      const uint8_t* fr = p.ref + (size_t)(y0 - M + ty) * p.pitch + (x0 - M);
-      const uint8_t* gr = p.def + (size_t)(y0 - M + ty + dv) * p.pitch + (x0 - M + du);
-      for (int tx = lane; tx < S; tx += 32) {
-        const int a = (int)fr[tx] - 128, b = (int)gr[tx] - 128;
-        sab += a * b;
-        sb += b;
-        sbb += b * b;
+  if (mx != INT_MIN) {
+    const SlotCand w = sl[mx & 255];
+    const float fm = key2f(mx);
+    if (!(w.l & kSlotNearTie) && fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm)) {
+      best = Cand{w.num, w.dg, w.l};
+    } else {
+      const int tx_first = (xl - R - p.xmin) / kTileR, ty_first = (yl - R - p.ymin) / kTileQ;
+      for (int s0 = 0; s0 < p.nslots; s0 += 32) {
+        const int s = s0 + lane;
+        bool take = false, flagged = false;
+        if (s < p.nslots) {
+          const SlotCand c = sl[s];
+          if (valid(c.l)) {
+            const float f = cand_score(c.num, c.dg);
+            take = !(fm > 1e-8f) || f >= fm - 2e-3f * fm;
+            flagged = c.l & kSlotNearTie;
+            if (take && !flagged) consider(best, Cand{c.num, c.dg, c.l});
+          }
+        }
+        unsigned amb = __ballot_sync(0xffffffffu, take && flagged);
+        while (amb) {
+          const int j = s0 + __ffs(amb) - 1;
+          amb &= amb - 1;
+          // every position of slot j's tile in the window, one lane each
+          const int X0 = p.xmin + (tx_first + j % p.slots_x) * kTileR;
+          const int Y0 = p.ymin + (ty_first + j / p.slots_x) * kTileQ;
+          for (int m = lane; m < kPos; m += 32) {
+            const int du = X0 + m % kTileR - xl, dv = Y0 + m / kTileR - yl;
+            if (du < -R || du > R || dv < -R || dv > R) continue;
+            long long sab = 0, sb = 0, sbb = 0;
+            for (int ty = 0; ty < S; ++ty) {
+              const uint8_t* fr = p.ref + (size_t)(yl + ty) * p.pitch + xl;
+              const uint8_t* gr = p.def + (size_t)(yl + dv + ty) * p.pitch + (xl + du);
+              int rab = 0, rb = 0, rbb = 0;
+              for (int tx = 0; tx < S; ++tx) {
+                const int a = (int)fr[tx] - 128, b = (int)gr[tx] - 128;
+                rab += a * b;
+                rb += b;
+                rbb += b * b;
+              }
+              sab += rab;
+              sb += rb;
+              sbb += rbb;
+            }
+            const long long dg = N * sbb - sb * sb;
+            if (dg != 0)
+              consider(best, Cand{N * sab - (long long)fb.x * sb, dg, (dv + R) * ow + (du + R)});
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        Cand d;
+        d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
+        d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
+        d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
+        consider(best, d);
       }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      sab += __shfl_xor_sync(0xffffffffu, sab, o);
-      sb += __shfl_xor_sync(0xffffffffu, sb, o);
-      sbb += __shfl_xor_sync(0xffffffffu, sbb, o);
-    }
-    const Cand c{N * sab - fs.x * sb, N * sbb - sb * sb, top[k].l};
-    if (c.dg != 0 && cand_better(c, best)) best = c;
   }
   if (lane == 0) {
     if (best.l == INT_MAX) {
@@ -617,11 +798,11 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->step = step;
   g->nx = nx;
   g->ny = ny;
-  g->twk = (S + 15) / 16 * 16;
+  if (S > 64) return false;
+  g->twk = S <= 16 ? 16 : S <= 32 ? 32 : 64;  // one swizzle width per operand row
   g->ncols_max = (2 * R + kTileR - 1) / step + 1;
   g->nrows_max = (2 * R + kTileQ - 1) / step + 1;
-  const int nused = g->ncols_max * g->nrows_max;
-  g->npad = (nused + 15) / 16 * 16;
+  g->npad = (g->ncols_max * g->nrows_max + 15) / 16 * 16;
   if (g->npad > 256 || nx == 0 || ny == 0) return false;
   g->rows_per_acc = 1024 / g->twk;
   if (g->rows_per_acc > S) g->rows_per_acc = S;
@@ -630,7 +811,20 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   while (cols < nacc * g->npad) cols *= 2;
   if (cols > 512) return false;
   g->tmem_cols = cols;
-  g->xmin = B - M - R;
+  // template-row stages: as many as fit beside the A buffer inside the
+  // region the transposed sums need anyway (at least 3, fewer only if the
+  // shared memory would not hold them)
+  {
+    const int rows = kTileQ + S - 1;
+    const size_t abuf = (size_t)rows * 16 * g->twk, stage = (size_t)2 * g->twk * g->npad;
+    const size_t dd = (size_t)g->npad * kDs * 4;
+    int st = 3;
+    while (st < kMaxStages && abuf + (st + 1) * stage <= dd) ++st;
+    while (st > 2 && tile_layout(S, g->twk, g->npad, st).total > 227 * 1024) --st;
+    g->stages = st;
+  }
+  g->arows = kTileQ + S - 1;
+  g->xmin = (B - M - R) & ~7;  // tile columns start at multiples of 8 (TMA of A)
   g->ymin = B - M - R;
   const int xmax = B + (nx - 1) * step - M + R, ymax = B + (ny - 1) * step - M + R;
   g->ntx = (xmax - g->xmin) / kTileR + 1;
@@ -639,6 +833,9 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->slots_x = (2 * R + kTileR - 1) / kTileR + 1;
   g->slots_y = (2 * R + kTileQ - 1) / kTileQ + 1;
   g->nslots = g->slots_x * g->slots_y;
+  if (g->nslots > 256) return false;  // slot index packed in 8 bits by the reduce
+  // template bank offsets are 32-bit element counts
+  if ((double)nx * ny * S * g->twk >= 4294967296.0) return false;
   // phase images cover every A row / column a tile touches and every
   // template row, with room for an 8-column chunk past the last tap
   const int wneed = std::max(W, g->xmin + g->ntx * kTileR + g->twk + 16);
@@ -649,24 +846,29 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
 }
 
 size_t search_tc_smem(const SearchTcParams& g) {
-  return tile_layout(g.S, g.twk, g.npad).total;
+  return tile_layout(g.S, g.twk, g.npad, g.stages).total;
 }
 
+size_t search_tc_gph_elems(const SearchTcParams& g) { return (size_t)8 * g.phh * g.phw; }
+
 size_t search_tc_phase_elems(const SearchTcParams& g) {
-  return (size_t)2 * 8 * g.phh * g.phw;
+  return search_tc_gph_elems(g) + (size_t)g.nx * g.ny * g.S * g.twk;
 }
 
 size_t search_tc_posbox_elems(const SearchTcParams& g) {
   return (size_t)g.ntx * 8 * (size_t)g.nty * 16;
 }
 
-cudaError_t launch_search_tc(const SearchTcParams& p, cudaStream_t st) {
+cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
+                             const CUtensorMap* tmB, cudaStream_t st) {
   if (p.n_pois == 0) return cudaSuccess;
   const unsigned wblocks = (unsigned)((p.n_pois + 7) / 8);
   cudaError_t e;
   {
-    const int64_t chunks = (int64_t)2 * 8 * p.phh * (p.phw / 8);
+    const int64_t chunks = (int64_t)8 * p.phh * (p.phw / 8);
     phase_kernel<<<(unsigned)((chunks + 255) / 256), 256, 0, st>>>(p);
+    const int64_t bchunks = (int64_t)p.ny * p.S * p.nx * (p.twk / 8);
+    bank_kernel<<<(unsigned)((bchunks + 255) / 256), 256, 0, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -691,7 +893,7 @@ cudaError_t launch_search_tc(const SearchTcParams& p, cudaStream_t st) {
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  tile_kernel<<<(unsigned)(p.ntx * p.nty), kThreads, smem, st>>>(p);
+  tile_kernel<<<(unsigned)(p.ntx * p.nty), kThreads, smem, st>>>(p, *tmA, *tmB);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_kernel<<<wblocks, 256, 0, st>>>(p);
