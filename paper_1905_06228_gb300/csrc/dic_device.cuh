@@ -95,4 +95,21 @@ __device__ __forceinline__ void keys_weights(float t, float w[4]) {
   w[3] = 0.5f * t3 - 0.5f * t2;
 }
 
+// float of an exact 64-bit integer without the 64-bit conversion (which runs
+// on the FP64 pipe): sign * (hi * 2^32 + lo) of the magnitude, relative
+// error below 2^-23 for |v| < 2^56.
+__device__ __forceinline__ float ll_to_float(long long v) {
+  const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+  const float f = fmaf((float)(unsigned)(a >> 32), 4294967296.0f, (float)(unsigned)a);
+  return v < 0 ? -f : f;
+}
+
+// ZNCC C = num / sqrt(Df Dg) of Eq. 1 from the exact integer sums
+// (num = N Sab - Sa Sb, Df = N Saa - Sa^2, Dg = N Sbb - Sb^2), in FP32:
+// three conversions, a product, a square root and a quotient, so the
+// relative error stays below 1e-6.  Both integer-search forms report this.
+__device__ __forceinline__ float zncc_of(long long num, long long df, long long dg) {
+  return ll_to_float(num) / sqrtf(ll_to_float(df) * ll_to_float(dg));
+}
+
 }  // namespace dic

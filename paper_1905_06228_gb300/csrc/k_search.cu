@@ -23,6 +23,7 @@
 // against num_b^2 Dg_a in 128-bit integers -- first within a thread, then by
 // warp shuffles, then across warps; ties keep the lowest linear index
 // (dv+R)(2R+1)+(du+R).  Dg = 0 (flat target) is never preferred.
+#include "dic_device.cuh"
 #include "dic_internal.cuh"
 
 namespace dic {
@@ -349,7 +350,7 @@ __device__ __forceinline__ void search_poi(const SearchParams& p, int64_t poi,
     } else {
       p.u0[poi] = b.l % L.ow - R;
       p.v0[poi] = b.l / L.ow - R;
-      p.zncc0[poi] = (float)((double)b.num / sqrt((double)Df * (double)b.dg));
+      p.zncc0[poi] = zncc_of(b.num, Df, b.dg);
       p.status[poi] = kOk;
     }
   }

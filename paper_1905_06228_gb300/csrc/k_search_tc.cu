@@ -36,6 +36,7 @@
 // the FP32 form and to the oracle.
 #include <algorithm>
 
+#include "dic_device.cuh"
 #include "dic_internal.cuh"
 
 namespace dic {
@@ -97,15 +98,6 @@ struct Cand {
   long long num, dg;
   int l;
 };
-
-// float of an exact 64-bit integer without the 64-bit conversion (which runs
-// on the FP64 pipe): sign * (hi * 2^32 + lo) of the magnitude, relative
-// error below 2^-23 for |v| < 2^56
-__device__ __forceinline__ float ll_to_float(long long v) {
-  const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
-  const float f = fmaf((float)(unsigned)(a >> 32), 4294967296.0f, (float)(unsigned)a);
-  return v < 0 ? -f : f;
-}
 
 __device__ __forceinline__ bool zncc_greater(long long na, long long da, long long nb,
                                              long long db) {
@@ -247,7 +239,7 @@ struct TileLayout {
   int RB;      // bytes of one operand row (TWK taps): the swizzle width
   int grp;     // bytes of an 8-row group: 8 * RB (one image row of A)
   int stageB;  // bytes per template-row stage: Npad * RB
-  size_t off_bar, off_tmem, off_pos, off_poi, off_red, off_a, off_b, off_d, total;
+  size_t off_bar, off_tmem, off_pos, off_poi, off_red, off_tie, off_a, off_b, off_d, total;
 };
 
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -267,6 +259,7 @@ __host__ __device__ inline TileLayout tile_layout(int S, int TWK, int npad, int 
   o = al(o, 16);  L.off_pos = o;  o += (size_t)kPos * 16;    // dg, sb, 1/dg
   L.off_poi = o;  o += (size_t)npad * 16;                    // per-POI window and sums
   L.off_red = o;  o += (size_t)4 * npad * 8;                 // per-quarter best two
+  L.off_tie = o;  o += (size_t)npad * 8 + 16;                // near-tie list + count
   o = al(o, 1024);  // swizzle atoms of the operands start on 1024-byte boundaries
   // A buffer and B stages; the transposed sums reuse this region once the
   // last MMA has completed
@@ -290,7 +283,6 @@ struct PoiInfo {
   int sa;
 };
 constexpr int kNoPoi = -(1 << 20);
-constexpr int kSlotNearTie = 1 << 30;  // flag in SlotCand::l: tile winner not certain
 
 // Order-preserving map of a float onto int (larger float -> larger int).
 __device__ __forceinline__ int f2key(float s) {
@@ -432,6 +424,8 @@ __global__ void __launch_bounds__(kThreads, 3)
   float* pinv = reinterpret_cast<float*>(psb + kPos);                // 1 / Dg
   PoiInfo* poi = reinterpret_cast<PoiInfo*>(smem + L.off_poi);
   int2* red = reinterpret_cast<int2*>(smem + L.off_red);
+  int2* ties = reinterpret_cast<int2*>(smem + L.off_tie);  // (POI n, threshold bits)
+  int* nties = reinterpret_cast<int*>(ties + NP);
   unsigned char* abuf = smem + L.off_a;
   unsigned char* bbuf = smem + L.off_b;
   int* dsm = reinterpret_cast<int*>(smem + L.off_d);
@@ -461,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   // then TMEM allocation (warp 0)
   const uint32_t ncols = p.tmem_cols;
   if (tid == 0) {
+    *nties = 0;
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
     for (int i = 0; i < NST; ++i) {
@@ -615,31 +610,22 @@ __global__ void __launch_bounds__(kThreads, 3)
   if (!ok) return;
 
   // ---- per-POI winner of the tile: merge the four quarters' best two.  The
-  // float winner's sums are exact; it is the exact winner of the tile if it
-  // clears every other candidate by 1e-3 (relative) and is above 1e-8 (score
-  // errors stay below 1.5e-4 and num != 0 there).  Otherwise the slot is
-  // flagged (kSlotNearTie) and the reduce kernel resolves it exactly if it
-  // can matter.
+  // float winner is the exact winner if it is positive above 1e-8 and clears
+  // the second by 5e-4 (relative): float scores err by less than 1.5e-4 and
+  // num != 0 there.  Otherwise (a near tie) one warp compares exactly the
+  // POI's positions whose float score is within 5e-4 (+1e-8) of the best,
+  // lowest linear index on ties; no position outside that band can be the
+  // tile's maximum.
   const int wide = nacc > 1;
   const int ow = 2 * R + 1;
-  for (int n = tid; n < NP; n += kThreads) {
-    const PoiInfo pi = poi[n];
-    if (pi.cx == kNoPoi) continue;
-    int mx = red[n].x, sc = red[n].y;
-#pragma unroll
-    for (int qq = 1; qq < 4; ++qq) merge2(mx, sc, red[qq * NP + n].x, red[qq * NP + n].y);
-    long long num = 0, dg = 1;
-    int l = INT_MAX;
-    if (mx != INT_MIN) {
-      const int m = mx & 127;
-      const int raw = dsm[n * kDs + m];
-      const int sab = wide ? raw : __float2int_rn(__int_as_float(raw));
-      num = N * (long long)sab - (long long)pi.sa * psb[m];
-      dg = pdg[m];
-      l = (m / kTileR - pi.cy) * ow + (m % kTileR - pi.cx);
-      const float fm = key2f(mx);
-      if (!(fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm))) l |= kSlotNearTie;
-    }
+  const float Nf = (float)N;
+  auto exact = [&](const PoiInfo& pi, int n, int m) {
+    const int raw = dsm[n * kDs + m];
+    const int sab = wide ? raw : __float2int_rn(__int_as_float(raw));
+    return Cand{N * (long long)sab - (long long)pi.sa * psb[m], pdg[m],
+                (m / kTileR - pi.cy) * ow + (m % kTileR - pi.cx)};
+  };
+  auto write_slot = [&](const PoiInfo& pi, int n, const Cand& best) {
     int bi, bj;
     block_poi(p, n, bi, bj);
     const int64_t poi_k = (int64_t)(kr0 + bi) * p.nx + (kc0 + bj);
@@ -649,31 +635,73 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int slot = ((Y0 - p.ymin) / kTileQ - ty_first) * p.slots_x +
                      ((X0 - p.xmin) / kTileR - tx_first);
     SlotCand* s = p.slots + (size_t)poi_k * p.nslots + slot;
-    s->num = num;
-    s->dg = dg;
-    s->l = l;
+    s->num = best.num;
+    s->dg = best.dg;
+    s->l = best.l;
+  };
+  for (int n = tid; n < NP; n += kThreads) {
+    const PoiInfo pi = poi[n];
+    if (pi.cx == kNoPoi) continue;
+    int mx = red[n].x, sc = red[n].y;
+#pragma unroll
+    for (int qq = 1; qq < 4; ++qq) merge2(mx, sc, red[qq * NP + n].x, red[qq * NP + n].y);
+    if (mx == INT_MIN) {
+      write_slot(pi, n, Cand{0, 1, INT_MAX});
+      continue;
+    }
+    const float fm = key2f(mx);
+    if (fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 5e-4f * fm)) {
+      write_slot(pi, n, exact(pi, n, mx & 127));
+    } else {
+      const int k = atomicAdd(nties, 1);
+      ties[k] = make_int2(n, __float_as_int(fm - 5e-4f * fabsf(fm) - 1e-8f));
+    }
+  }
+  __syncthreads();
+  for (int k = warp; k < *nties; k += kThreads / 32) {
+    const int n = ties[k].x;
+    const float thr = __int_as_float(ties[k].y);
+    const PoiInfo pi = poi[n];
+    Cand best{0, 1, INT_MAX};
+    for (int m = lane; m < kPos; m += 32) {
+      const int q = m / kTileR, r = m % kTileR;
+      if ((unsigned)(r - pi.cx) > (unsigned)(2 * R) || (unsigned)(q - pi.cy) > (unsigned)(2 * R) ||
+          pdg[m] == 0)
+        continue;
+      const int raw = dsm[n * kDs + m];
+      float nf;
+      if (wide) {
+        nf = ll_to_float(N * (long long)raw - (long long)pi.sa * psb[m]);
+      } else {
+        const float sbf = (float)psb[m], hi = pi.saf * sbf, lo = fmaf(pi.saf, sbf, -hi);
+        nf = fmaf(Nf, __int_as_float(raw), -hi) - lo;
+      }
+      if (nf * fabsf(nf) * pinv[m] < thr) continue;
+      const Cand c = exact(pi, n, m);
+      if (cand_better(c, best)) best = c;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      Cand d;
+      d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
+      d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
+      d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
+      if (cand_better(d, best)) best = d;
+    }
+    if (lane == 0) write_slot(pi, n, best);
   }
 }
 
 // ------------------------------------------------------------ final reduce
-// One warp per POI.  Each lane scores its slots in float from their exact
-// sums (relative error below 1e-6, plus 2^-15 from the slot index packed
-// into the key) and the warp keeps the best two.  If the best slot is
-// certain (not kSlotNearTie), positive above 1e-8 and clears the second by
-// 1e-3, its candidate is the POI's exact winner.  Otherwise every slot
-// within 2e-3 of the best (all of them if the best is not above 1e-8) is
-// resolved exactly: its own candidate, or, for a flagged slot, every
-// position of its tile inside the POI's window with the sums recomputed
-// from the images; the exact maximum wins, lowest linear index on ties.
-// A flagged slot's tile maximum exceeds its stored candidate by at most
-// 3e-4 (relative), so slots below the 2e-3 band cannot hold the winner.
+// One warp per POI.  Each slot holds the exact winner of one tile (or no
+// candidate).  Lanes score their slots in float from the exact sums (error
+// below 1e-6 plus 2^-15 from the slot index packed into the key) and the
+// warp keeps the best two; if the best is positive above 1e-8 and clears the
+// second by 1e-3 it is the POI's winner, otherwise the slots within 2e-3
+// (+1e-8) of the best are compared exactly, lowest linear index on ties.
 __device__ __forceinline__ float cand_score(long long num, long long dg) {
   const float n = ll_to_float(num);
   return n * fabsf(n) / ll_to_float(dg);  // sign(C) C^2 Df
-}
-
-__device__ __forceinline__ void consider(Cand& best, const Cand& c) {
-  if (cand_better(c, best)) best = c;
 }
 
 __global__ void reduce_kernel(const SearchTcParams p) {
@@ -683,8 +711,7 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   const int S = p.S, M = p.M, R = p.R, ow = 2 * R + 1;
   const int x0 = M + R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + R + 2 + (int)(poi / p.nx) * p.step;
-  const int xl = x0 - M, yl = y0 - M;
-  const int2 fb = p.fbox[(size_t)(yl - p.ymin) * (p.ntx * 8) + (xl - p.xmin)];
+  const int2 fb = p.fbox[(size_t)(y0 - M - p.ymin) * (p.ntx * 8) + (x0 - M - p.xmin)];
   const long long N = (long long)S * S;
   const long long Df = N * (long long)fb.y - (long long)fb.x * fb.x;
   if (Df == 0) {
@@ -697,12 +724,12 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     return;
   }
   const SlotCand* sl = p.slots + (size_t)poi * p.nslots;
-  auto valid = [&](int l) { return l >= 0 && (l & ~kSlotNearTie) < ow * ow; };
+  // an unwritten slot (all bits set) or a tile without a candidate
+  auto valid = [&](int l) { return l >= 0 && l < ow * ow; };
   int mx = INT_MIN, sc = INT_MIN;
   for (int s = lane; s < p.nslots; s += 32) {
     const SlotCand c = sl[s];
-    if (!valid(c.l)) continue;
-    merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~255) | s, INT_MIN);
+    if (valid(c.l)) merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~255) | s, INT_MIN);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -712,53 +739,17 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   }
   Cand best{0, 1, INT_MAX};
   if (mx != INT_MIN) {
-    const SlotCand w = sl[mx & 255];
     const float fm = key2f(mx);
-    if (!(w.l & kSlotNearTie) && fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm)) {
+    if (fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm)) {
+      const SlotCand w = sl[mx & 255];
       best = Cand{w.num, w.dg, w.l};
     } else {
-      const int tx_first = (xl - R - p.xmin) / kTileR, ty_first = (yl - R - p.ymin) / kTileQ;
-      for (int s0 = 0; s0 < p.nslots; s0 += 32) {
-        const int s = s0 + lane;
-        bool take = false, flagged = false;
-        if (s < p.nslots) {
-          const SlotCand c = sl[s];
-          if (valid(c.l)) {
-            const float f = cand_score(c.num, c.dg);
-            take = !(fm > 1e-8f) || f >= fm - 2e-3f * fm;
-            flagged = c.l & kSlotNearTie;
-            if (take && !flagged) consider(best, Cand{c.num, c.dg, c.l});
-          }
-        }
-        unsigned amb = __ballot_sync(0xffffffffu, take && flagged);
-        while (amb) {
-          const int j = s0 + __ffs(amb) - 1;
-          amb &= amb - 1;
-          // every position of slot j's tile in the window, one lane each
-          const int X0 = p.xmin + (tx_first + j % p.slots_x) * kTileR;
-          const int Y0 = p.ymin + (ty_first + j / p.slots_x) * kTileQ;
-          for (int m = lane; m < kPos; m += 32) {
-            const int du = X0 + m % kTileR - xl, dv = Y0 + m / kTileR - yl;
-            if (du < -R || du > R || dv < -R || dv > R) continue;
-            long long sab = 0, sb = 0, sbb = 0;
-            for (int ty = 0; ty < S; ++ty) {
-              const uint8_t* fr = p.ref + (size_t)(yl + ty) * p.pitch + xl;
-              const uint8_t* gr = p.def + (size_t)(yl + dv + ty) * p.pitch + (xl + du);
-              int rab = 0, rb = 0, rbb = 0;
-              for (int tx = 0; tx < S; ++tx) {
-                const int a = (int)fr[tx] - 128, b = (int)gr[tx] - 128;
-                rab += a * b;
-                rb += b;
-                rbb += b * b;
-              }
-              sab += rab;
-              sb += rb;
-              sbb += rbb;
-            }
-            const long long dg = N * sbb - sb * sb;
-            if (dg != 0)
-              consider(best, Cand{N * sab - (long long)fb.x * sb, dg, (dv + R) * ow + (du + R)});
-          }
+      const float thr = fm - 2e-3f * fabsf(fm) - 1e-8f;
+      for (int s = lane; s < p.nslots; s += 32) {
+        const SlotCand c = sl[s];
+        if (valid(c.l) && cand_score(c.num, c.dg) >= thr) {
+          const Cand d{c.num, c.dg, c.l};
+          if (cand_better(d, best)) best = d;
         }
       }
 #pragma unroll
@@ -767,7 +758,7 @@ __global__ void reduce_kernel(const SearchTcParams p) {
         d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
         d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
         d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
-        consider(best, d);
+        if (cand_better(d, best)) best = d;
       }
     }
   }
@@ -780,7 +771,7 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     } else {
       p.u0[poi] = best.l % ow - R;
       p.v0[poi] = best.l / ow - R;
-      p.zncc0[poi] = (float)((double)best.num / sqrt((double)Df * (double)best.dg));
+      p.zncc0[poi] = zncc_of(best.num, Df, best.dg);
       p.status[poi] = kOk;
     }
   }
