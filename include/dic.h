@@ -19,7 +19,7 @@
  *    and owns them; the library never frees caller memory and keeps image
  *    pointers only as borrowed references between dic_set_pair and the next
  *    dic_set_pair / dic_destroy (the images must stay alive and unchanged).
- *  - The library owns its scratch (bicubic coefficient table, gradient
+ *  - The library owns its scratch (float copy of the deformed image, gradient
  *    field), allocates it in dic_set_pair and frees it in dic_destroy.
  *  - Work is enqueued asynchronously on the stream given to dic_set_stream
  *    (default: the legacy default stream).  Argument errors are returned
@@ -234,9 +234,9 @@ dic_status dic_backward(dic_t h, const float *p6, const float *grad_loss, float 
  * the whole device-memory budget through its own allocator.
  *
  * Same arithmetic as dic_set_pair (precompute) followed by dic_subpixel, but
- * without a handle: the bicubic table and gradient field go to one fixed
- * array inside the library (a static device symbol of 4.5 MiB, held by every
- * GPU that loads the library until the process exits).
+ * without a handle: the float deformed image and the gradient field go to one
+ * fixed array inside the library (a static device symbol of 768 KiB, held by
+ * every GPU that loads the library until the process exits).
  *   - width * height must be <= 65536 pixels (e.g. 256 x 256); larger
  *     images, and every other invalid argument, return DIC_ERR_ARG before any
  *     GPU work is enqueued.  Other arguments as in dic_create / dic_set_pair /

@@ -145,7 +145,7 @@ namespace {
 void free_batch(dic::BatchState* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->lut) cudaFree(b->lut);
+  if (b->gimg) cudaFree(b->gimg);
   if (b->grad) cudaFree(b->grad);
   if (b->d_pjobs) cudaFree(b->d_pjobs);
   if (b->d_offsets) cudaFree(b->d_offsets);
@@ -165,7 +165,7 @@ extern "C" {
 void dic_destroy(dic_t h) {
   if (!h) return;
   free_batch(h->batch);
-  if (h->lut) cudaFree(h->lut);
+  if (h->gimg) cudaFree(h->gimg);
   if (h->grad) cudaFree(h->grad);
   if (h->err_flag) cudaFree(h->err_flag);
   if (h->tc_phase) cudaFree(h->tc_phase);
@@ -220,17 +220,17 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
   grid_of(width, height, h->subset, h->step, h->R, &nx, &ny);
   const size_t px = (size_t)width * height;
   if (px > h->scratch_px) {
-    if (h->lut) cudaFree(h->lut);
+    if (h->gimg) cudaFree(h->gimg);
     if (h->grad) cudaFree(h->grad);
-    h->lut = nullptr;
+    h->gimg = nullptr;
     h->grad = nullptr;
     h->scratch_px = 0;
-    if (cudaMalloc(&h->lut, px * 4 * sizeof(float4)) != cudaSuccess ||
+    if (cudaMalloc(&h->gimg, px * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->grad, px * sizeof(float2)) != cudaSuccess) {
       cudaGetLastError();
-      if (h->lut) cudaFree(h->lut);
-      h->lut = nullptr;
-      return fail(h, DIC_ERR_OOM, "cannot allocate %zu bytes of scratch", px * 72);
+      if (h->gimg) cudaFree(h->gimg);
+      h->gimg = nullptr;
+      return fail(h, DIC_ERR_OOM, "cannot allocate %zu bytes of scratch", px * 12);
     }
     h->scratch_px = px;
   }
@@ -253,7 +253,7 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
     h->ref_f32 = static_cast<const float*>(ref);
     h->def_f32 = static_cast<const float*>(def);
     h->tma_ok = false;
-    e = dic::launch_precompute_f32(h->ref_f32, h->def_f32, width, height, pitch, h->grad, h->lut,
+    e = dic::launch_precompute_f32(h->ref_f32, h->def_f32, width, height, pitch, h->grad, h->gimg,
                                    h->stream);
   } else {
     h->ref_f32 = h->def_f32 = nullptr;
@@ -266,7 +266,7 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
                 bwg <= 256 && span <= 256 &&
                 encode_u8(&h->tm_def, h->def, width, height, pitch, bwg, span) &&
                 encode_u8(&h->tm_ref, h->ref, width, height, pitch, bwf, h->subset);
-    e = dic::launch_precompute(h->ref, h->def, width, height, pitch, h->grad, h->lut, h->stream);
+    e = dic::launch_precompute(h->ref, h->def, width, height, pitch, h->grad, h->gimg, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "precompute launch");
   h->have_pair = true;
@@ -286,7 +286,7 @@ dic_status run_adjoint(dic_t h, const float* p6, float* loss_poi, float* loss_to
   dic::AdjointParams p;
   p.ref = h->ref;
   p.ref_f32 = h->ref_f32;
-  p.lut = h->lut;
+  p.gimg = h->gimg;
   p.W = h->g.W;
   p.H = h->g.H;
   p.pitch = h->g.pitch;
@@ -453,7 +453,7 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int
   p.ref = h->ref;
   p.ref_f32 = h->ref_f32;
   p.grad = h->grad;
-  p.lut = h->lut;
+  p.gimg = h->gimg;
   p.W = h->g.W;
   p.H = h->g.H;
   p.pitch = h->g.pitch;
@@ -505,7 +505,7 @@ dic_status write_jobs(dic_t h, const dic_batch_out& o, int solve_bits) {
     dic::SubpixelParams& p = pj[k];
     p.ref = bp.d.ref_dev;
     p.grad = b->grad + bp.px_off;
-    p.lut = b->lut + 4 * bp.px_off;
+    p.gimg = b->gimg + bp.px_off;
     p.W = bp.d.width;
     p.H = bp.d.height;
     p.pitch = bp.d.pitch_bytes;
@@ -584,7 +584,7 @@ dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
   for (const dic::BatchPair& bp : b->pairs) {
     if (le != cudaSuccess) break;
     le = dic::launch_precompute(bp.d.ref_dev, bp.d.def_dev, bp.d.width, bp.d.height,
-                                bp.d.pitch_bytes, b->grad + bp.px_off, b->lut + 4 * bp.px_off,
+                                bp.d.pitch_bytes, b->grad + bp.px_off, b->gimg + bp.px_off,
                                 cs);
   }
   for (size_t c = 0; c < b->classes.size() && le == cudaSuccess; ++c) {
@@ -695,7 +695,7 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
   std::vector<int64_t> offs;
   for (auto& bp : b->pairs) offs.push_back(bp.off);
   offs.push_back(off);
-  cudaError_t e = cudaMalloc(&b->lut, px * 4 * sizeof(float4));
+  cudaError_t e = cudaMalloc(&b->gimg, px * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&b->grad, px * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_pjobs, sizeof(dic::SubpixelParams) * n_pairs);
   if (e == cudaSuccess) e = upload(&b->d_offsets, offs);

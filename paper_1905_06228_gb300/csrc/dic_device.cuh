@@ -1,6 +1,6 @@
 // dic_device.cuh -- device helpers shared by the sub-pixel and adjoint
 // kernels: warp reductions, the walk over a lane's subset points, bicubic
-// evaluation from the coefficient table, and the subset-in-image test.
+// evaluation from the float image, and the subset-in-image test.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,29 +14,55 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Bicubic value (and optionally derivatives) from one table cell.
-// The table is four planes of float4: plane n holds, per cell, the
-// coefficients of ty^n (1, tx, tx^2, tx^3).  Lanes of a warp interpolate
-// consecutive pixels of a subset row, so each plane load of a warp covers
-// contiguous cache lines.
+// Keys (a = -1/2) weights of the taps -1, 0, 1, 2 at fractional offset t.
+__device__ __forceinline__ void keys_weights(float t, float w[4]) {
+  const float t2 = t * t, t3 = t2 * t;
+  w[0] = fmaf(-0.5f, t3, fmaf(-0.5f, t, t2));
+  w[1] = fmaf(1.5f, t3, fmaf(-2.5f, t2, 1.f));
+  w[2] = fmaf(-1.5f, t3, fmaf(2.f, t2, 0.5f * t));
+  w[3] = 0.5f * (t3 - t2);
+}
+
+// Derivatives dw/dt of the Keys weights.
+__device__ __forceinline__ void keys_dweights(float t, float w[4]) {
+  const float t2 = t * t;
+  w[0] = fmaf(-1.5f, t2, fmaf(2.f, t, -0.5f));
+  w[1] = fmaf(4.5f, t2, -5.f * t);
+  w[2] = fmaf(-4.5f, t2, fmaf(4.f, t, 0.5f));
+  w[3] = fmaf(1.5f, t2, -t);
+}
+
+// Bicubic (Keys a = -1/2) value of the image at (x + tx, y + ty), cell =
+// y*W + x, from the 4x4 pixels y-1..y+2, x-1..x+2 (and, with DERIV, the
+// derivatives along x and y).  Lanes of a warp interpolate consecutive
+// pixels of a subset row, so each of the 16 loads of a warp covers one or
+// two cache lines of a small, L1-resident footprint.
 template <bool DERIV>
-__device__ __forceinline__ float bicubic(const float4* __restrict__ lut, size_t plane,
-                                         size_t cell, float tx, float ty, float& gx, float& gy) {
-  const float4 a0 = __ldg(lut + cell), a1 = __ldg(lut + plane + cell),
-               a2 = __ldg(lut + 2 * plane + cell), a3 = __ldg(lut + 3 * plane + cell);
-  const float r0 = fmaf(fmaf(fmaf(a0.w, tx, a0.z), tx, a0.y), tx, a0.x);
-  const float r1 = fmaf(fmaf(fmaf(a1.w, tx, a1.z), tx, a1.y), tx, a1.x);
-  const float r2 = fmaf(fmaf(fmaf(a2.w, tx, a2.z), tx, a2.y), tx, a2.x);
-  const float r3 = fmaf(fmaf(fmaf(a3.w, tx, a3.z), tx, a3.y), tx, a3.x);
-  if (DERIV) {
-    const float d0 = fmaf(fmaf(3.f * a0.w, tx, 2.f * a0.z), tx, a0.y);
-    const float d1 = fmaf(fmaf(3.f * a1.w, tx, 2.f * a1.z), tx, a1.y);
-    const float d2 = fmaf(fmaf(3.f * a2.w, tx, 2.f * a2.z), tx, a2.y);
-    const float d3 = fmaf(fmaf(3.f * a3.w, tx, 2.f * a3.z), tx, a3.y);
-    gx = fmaf(fmaf(fmaf(d3, ty, d2), ty, d1), ty, d0);
-    gy = fmaf(fmaf(3.f * r3, ty, 2.f * r2), ty, r1);
+__device__ __forceinline__ float bicubic(const float* __restrict__ img, int W, size_t cell,
+                                         float tx, float ty, float& gx, float& gy) {
+  float wx[4], wy[4];
+  keys_weights(tx, wx);
+  keys_weights(ty, wy);
+  const float* r = img + cell - W - 1;
+  float row[4], drow[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const float p0 = __ldg(r), p1 = __ldg(r + 1), p2 = __ldg(r + 2), p3 = __ldg(r + 3);
+    row[l] = fmaf(wx[3], p3, fmaf(wx[2], p2, fmaf(wx[1], p1, wx[0] * p0)));
+    if (DERIV) {
+      float dx[4];
+      keys_dweights(tx, dx);
+      drow[l] = fmaf(dx[3], p3, fmaf(dx[2], p2, fmaf(dx[1], p1, dx[0] * p0)));
+    }
+    r += W;
   }
-  return fmaf(fmaf(fmaf(r3, ty, r2), ty, r1), ty, r0);
+  if (DERIV) {
+    float dy[4];
+    keys_dweights(ty, dy);
+    gx = fmaf(wy[3], drow[3], fmaf(wy[2], drow[2], fmaf(wy[1], drow[1], wy[0] * drow[0])));
+    gy = fmaf(dy[3], row[3], fmaf(dy[2], row[2], fmaf(dy[1], row[1], dy[0] * row[0])));
+  }
+  return fmaf(wy[3], row[3], fmaf(wy[2], row[2], fmaf(wy[1], row[1], wy[0] * row[0])));
 }
 
 // Subset point walk of one lane: points i = lane, lane+32, ... in row-major
@@ -59,7 +85,7 @@ struct PtWalk {
   }
 };
 
-// Location of a warped point: table cell and fractional offsets.
+// Location of a warped point: its cell (top-left pixel) and fractional offsets.
 __device__ __forceinline__ size_t locate(const float p[6], int dx, int dy, int x0, int y0, int W,
                                          int H, float& tx, float& ty) {
   const float lx = fmaf(p[2], (float)dy, fmaf(1.f + p[1], (float)dx, p[0]));
@@ -86,14 +112,6 @@ __device__ __forceinline__ bool corners_in(const float p[6], int x0, int y0, int
   return ok;
 }
 
-// Keys (a = -1/2) weights of the taps -1, 0, 1, 2 at fractional offset t.
-__device__ __forceinline__ void keys_weights(float t, float w[4]) {
-  const float t2 = t * t, t3 = t2 * t;
-  w[0] = -0.5f * t3 + t2 - 0.5f * t;
-  w[1] = 1.5f * t3 - 2.5f * t2 + 1.f;
-  w[2] = -1.5f * t3 + 2.f * t2 + 0.5f * t;
-  w[3] = 0.5f * t3 - 0.5f * t2;
-}
 
 // float of an exact 64-bit integer without the 64-bit conversion (which runs
 // on the FP64 pipe): sign * (hi * 2^32 + lo) of the magnitude, relative

@@ -89,7 +89,7 @@ struct SubpixelParams {
   const uint8_t* ref = nullptr;
   const float* ref_f32 = nullptr;
   const float2* grad;  // central-difference gradients of f, W*H
-  const float4* lut;   // bicubic coefficient planes of g, 4*W*H
+  const float* gimg;   // deformed image as float, W*H
   int W, H, pitch;
   int S, M, R, step, nx;
   int64_t n_pois;
@@ -113,7 +113,7 @@ struct SubpixelParams {
 struct AdjointParams {
   const uint8_t* ref = nullptr;
   const float* ref_f32 = nullptr;
-  const float4* lut;
+  const float* gimg;   // deformed image as float, W*H
   int W, H, pitch;
   int S, M, R, step, nx;
   int64_t n_pois;
@@ -129,9 +129,9 @@ struct AdjointParams {
 
 // Launchers (each returns the cudaError_t of its launch).
 cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int H,
-                              int pitch, float2* grad, float4* lut, cudaStream_t st);
+                              int pitch, float2* grad, float* gimg, cudaStream_t st);
 cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int H,
-                                  int pitch, float2* grad, float4* lut, cudaStream_t st);
+                                  int pitch, float2* grad, float* gimg, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
 
 bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, SearchTcParams* g);
@@ -183,7 +183,7 @@ struct BatchState {
   int64_t total = 0;
   int nmax = 0;
   size_t px_total = 0;
-  float4* lut = nullptr;
+  float* gimg = nullptr;
   float2* grad = nullptr;
   SubpixelParams* d_pjobs = nullptr;
   int64_t* d_offsets = nullptr;
@@ -210,7 +210,7 @@ struct dic_s {
   const float* def_f32 = nullptr;
   dic::PairGeom g;
 
-  float4* lut = nullptr;
+  float* gimg = nullptr;
   float2* grad = nullptr;
   size_t scratch_px = 0;  // capacity in pixels
   unsigned int* err_flag = nullptr;

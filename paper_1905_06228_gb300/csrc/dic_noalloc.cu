@@ -6,7 +6,7 @@
 // inside a host application whose own allocator owns the device memory
 // budget, where a stray allocation breaks its accounting.
 //
-// The regular path keeps the bicubic coefficient table and the reference
+// The regular path keeps the float deformed image and the reference
 // gradient field in scratch that dic_set_pair allocates.  Here the same two
 // kernels (precompute, then sub-pixel refinement) run on a fixed scratch
 // array that lives in this file as a static __device__ symbol.  Every GPU
@@ -20,10 +20,10 @@ namespace {
 
 // Largest image (width * height, pixels) this entry point accepts.
 constexpr size_t kNoAllocMaxPixels = 256 * 256;
-// Bicubic table (4 float4 per pixel) followed by the gradient field
-// (one float2 per pixel).
-constexpr size_t kLutBytes = kNoAllocMaxPixels * 4 * sizeof(float4);
-constexpr size_t kNoAllocScratchBytes = kLutBytes + kNoAllocMaxPixels * sizeof(float2);
+// Float deformed image (one float per pixel) followed by the gradient
+// field (one float2 per pixel): 768 KiB.
+constexpr size_t kGimgBytes = kNoAllocMaxPixels * sizeof(float);
+constexpr size_t kNoAllocScratchBytes = kGimgBytes + kNoAllocMaxPixels * sizeof(float2);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -77,21 +77,21 @@ extern "C" dic_status dic_subpixel_noalloc(
 
   unsigned char* scratch = nullptr;
   if (scratch_on_current_device(&scratch) != cudaSuccess) return DIC_ERR_CUDA;
-  float4* lut = reinterpret_cast<float4*>(scratch);
-  float2* grad = reinterpret_cast<float2*>(scratch + kLutBytes);
+  float* gimg = reinterpret_cast<float*>(scratch);
+  float2* grad = reinterpret_cast<float2*>(scratch + kGimgBytes);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-  // The precompute kernel writes every table cell and gradient of the
+  // The precompute kernel writes every float pixel and gradient of the
   // width x height image (zeros on the border), so nothing left over from an
   // earlier call is ever read and no clearing is needed.
-  if (dic::launch_precompute(ref_dev, def_dev, width, height, pitch_bytes, grad, lut, st) !=
+  if (dic::launch_precompute(ref_dev, def_dev, width, height, pitch_bytes, grad, gimg, st) !=
       cudaSuccess)
     return DIC_ERR_CUDA;
 
   dic::SubpixelParams p;
   p.ref = ref_dev;
   p.grad = grad;
-  p.lut = lut;
+  p.gimg = gimg;
   p.W = width;
   p.H = height;
   p.pitch = pitch_bytes;

@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(32 * kWarps) adjoint_kernel(const AdjointParam
                 (size_t)wid * kTile * kTile;
   const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
-  const size_t plane = (size_t)W * H;
   float prm[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) prm[k] = p.p6[poi * 6 + k];
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(32 * kWarps) adjoint_kernel(const AdjointParam
     for (int i = lane; i < N; i += 32, w.next()) {
       float tx, ty, gx, gy;
       const size_t cell = locate(prm, w.dx, w.dy, x0, y0, W, H, tx, ty);
-      const float d = bicubic<false>(p.lut, plane, cell, tx, ty, gx, gy) - c;
+      const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
       sfg = fmaf(sfc[i], d, sfg);
@@ -149,7 +148,7 @@ __global__ void __launch_bounds__(32 * kWarps) adjoint_kernel(const AdjointParam
     for (int i = lane; i < N; i += 32, w.next()) {
       float tx, ty, gx = 0.f, gy = 0.f;
       const size_t cell = locate(prm, w.dx, w.dy, x0, y0, W, H, tx, ty);
-      const float d = bicubic<true>(p.lut, plane, cell, tx, ty, gx, gy) - c;
+      const float d = bicubic<true>(p.gimg, W, cell, tx, ty, gx, gy) - c;
       const float ft = sfc[i] * idf, gt = (d - gm) * idg;
       const float e = ft - gt;
       loss = fmaf(e, e, loss);

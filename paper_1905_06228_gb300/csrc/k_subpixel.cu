@@ -2,8 +2,8 @@
 //
 // One warp per POI; lane l owns subset points i = l, l+32, ...  Per-point
 // reference data (gradients of f, f - fbar, the point's (dx, dy)) lives in
-// shared memory for the whole solve; the deformed image is read through the
-// bicubic coefficient table (4 float4 per cell, from the precompute kernel).
+// shared memory for the whole solve; the deformed image is interpolated from
+// its float copy (Keys weights evaluated per sample).
 //
 // Warp:   W(xi; p) = (x0 + dx + u + ux dx + uy dy, y0 + dy + v + vx dx + vy dy).
 // IC-GN:  SD_i = grad f_i dW/dp, H = sum SD^T SD (once per POI),
@@ -26,7 +26,7 @@
 // Gauss-Newton matrix every iteration.  The final ZNCC is Eq. 1 at
 // the returned shape (one extra pass).
 // resident CTAs per SM requested from the register allocator, and the
-// unroll of the per-point loop (memory-level parallelism of the table loads)
+// unroll of the per-point loop (memory-level parallelism of the sample loads)
 #ifndef DIC_SUB_MINB
 #define DIC_SUB_MINB 1
 #endif
@@ -185,7 +185,6 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
   const int W = p.W, H = p.H;
-  const size_t plane = (size_t)W * H;
 
   const uint8_t st0 = p.st0[poi];
   float prm[6] = {(float)p.u0[poi], 0.f, 0.f, (float)p.v0[poi], 0.f, 0.f};
@@ -295,7 +294,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const int dx = w.dx, dy = w.dy;
       float tx, ty, gx = 0.f, gy = 0.f;
       const size_t cell = locate(prm, dx, dy, x0, y0, W, H, tx, ty);
-      const float g = bicubic<FANR>(p.lut, plane, cell, tx, ty, gx, gy);
+      const float g = bicubic<FANR>(p.gimg, W, cell, tx, ty, gx, gy);
       const float d = g - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
@@ -398,7 +397,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     for (int i = lane; i < N; i += 32, w.next()) {
       float tx, ty, gx, gy;
       const size_t cell = locate(prm, w.dx, w.dy, x0, y0, W, H, tx, ty);
-      const float d = bicubic<false>(p.lut, plane, cell, tx, ty, gx, gy) - c;
+      const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
       sfg = fmaf(sfc[i], d, sfg);
