@@ -28,11 +28,13 @@
 // resident CTAs per SM requested from the register allocator, and the
 // unroll of the per-point loop (memory-level parallelism of the sample loads)
 #ifndef DIC_SUB_MINB
-#define DIC_SUB_MINB 1
+#define DIC_SUB_MINB 4
 #endif
 #ifndef DIC_SUB_UNROLL
 #define DIC_SUB_UNROLL 1
 #endif
+
+#include <cuda_fp16.h>
 
 #include "dic_device.cuh"
 #include "dic_internal.cuh"
@@ -40,7 +42,7 @@
 namespace dic {
 namespace {
 
-constexpr int kWarpsPerCta = 4;
+constexpr int kWarpsPerCta = 8;
 constexpr int kPointUnroll = DIC_SUB_UNROLL;
 
 // 1/sqrt(d): FP32 estimate refined by Newton's iteration for 1/y^2 = d,
@@ -177,14 +179,49 @@ __device__ __forceinline__ const float* ref_ptr<float>(const SubpixelParams& p) 
   return p.ref_f32;
 }
 
-// Refinement of one POI by one warp; sgrad / sfc hold N entries.
+// Reference gradients as kept in shared memory: half2 for 8-bit images
+// (central differences of 8-bit pixels are multiples of 1/2 below 128 in
+// magnitude, exact in FP16), float2 for float images.
+template <typename TP>
+struct GradStore;
+template <>
+struct GradStore<uint8_t> {
+  using T = __half2;
+  static __device__ __forceinline__ T pack(float2 g) { return __floats2half2_rn(g.x, g.y); }
+  static __device__ __forceinline__ float2 unpack(T g) { return __half22float2(g); }
+};
+template <>
+struct GradStore<float> {
+  using T = float2;
+  static __device__ __forceinline__ T pack(float2 g) { return g; }
+  static __device__ __forceinline__ float2 unpack(T g) { return g; }
+};
+
+// Shared memory of one warp: N gradients, then (16-byte aligned) H^-1 as
+// 36 solve-precision values, then the IC-GN constants sum SD and
+// sum SD (f - fbar) (6 floats each).
+__host__ __device__ inline size_t warp_smem_bytes(int N, size_t grad_bytes) {
+  return ((size_t)N * grad_bytes + 15) / 16 * 16 + 36 * sizeof(double) + 12 * sizeof(float);
+}
+
+// Refinement of one POI by one warp; wsm is the warp's shared block.
 template <bool FANR, typename TS, typename TP>
 __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t poi, int lane,
-                                             float2* sgrad, float* sfc) {
+                                             unsigned char* wsm) {
+  using GS = GradStore<TP>;
+  using G = typename GS::T;
   const int S = p.S, M = p.M, N = S * S;
   const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
   const int W = p.W, H = p.H;
+  G* sgrad = reinterpret_cast<G*>(wsm);
+  TS* hinv = reinterpret_cast<TS*>(wsm + ((size_t)N * sizeof(G) + 15) / 16 * 16);
+  float* ssd = reinterpret_cast<float*>(hinv + 36);  // sum SD
+  float* sbf = ssd + 6;                              // sum SD (f - fbar)
+  const TP* fimg = ref_ptr<TP>(p);
+  auto fval = [&](int dx, int dy) {
+    return (float)fimg[(size_t)(y0 + dy) * p.pitch + (x0 + dx)];
+  };
 
   const uint8_t st0 = p.st0[poi];
   float prm[6] = {(float)p.u0[poi], 0.f, 0.f, (float)p.v0[poi], 0.f, 0.f};
@@ -206,19 +243,17 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     return;
   }
 
-  // ---- reference subset: f, its gradients, fbar, df
+  // ---- reference subset: fbar, df, gradients (and for IC-GN the Hessian
+  // and the constant sums of the right-hand side)
   float fsum = 0.f;
   {
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
-      const int x = x0 + w.dx, y = y0 + w.dy;
-      const float f = (float)ref_ptr<TP>(p)[(size_t)y * p.pitch + x];
-      sgrad[i] = p.grad[(size_t)y * W + x];
-      sfc[i] = f;
-      fsum += f;
+      fsum += fval(w.dx, w.dy);
+      sgrad[i] = GS::pack(p.grad[(size_t)(y0 + w.dy) * W + (x0 + w.dx)]);
     }
   }
-  fsum = warp_sum(fsum);  // exact: integer sum below 2^24
+  fsum = warp_sum(fsum);  // exact for 8-bit images: integer sum below 2^24
   const float fbar = fsum / (float)N;
   float q = 0.f;
   float Hs[21], sdsum[6], bfv[6];
@@ -227,25 +262,24 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 #pragma unroll
   for (int k = 0; k < 6; ++k) sdsum[k] = bfv[k] = 0.f;
   {
-   PtWalk w(lane, S, M);
-   for (int i = lane; i < N; i += 32, w.next()) {
-    const float fc = sfc[i] - fbar;
-    sfc[i] = fc;
-    q = fmaf(fc, fc, q);
-    if (!FANR) {
-      const float2 gr = sgrad[i];
-      const float dx = (float)w.dx, dy = (float)w.dy;
-      const float sd[6] = {gr.x, gr.x * dx, gr.x * dy, gr.y, gr.y * dx, gr.y * dy};
-      int k = 0;
+    PtWalk w(lane, S, M);
+    for (int i = lane; i < N; i += 32, w.next()) {
+      const float fc = fval(w.dx, w.dy) - fbar;
+      q = fmaf(fc, fc, q);
+      if (!FANR) {
+        const float2 gr = GS::unpack(sgrad[i]);
+        const float dx = (float)w.dx, dy = (float)w.dy;
+        const float sd[6] = {gr.x, gr.x * dx, gr.x * dy, gr.y, gr.y * dx, gr.y * dy};
+        int k = 0;
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        sdsum[a] += sd[a];
-        bfv[a] = fmaf(sd[a], fc, bfv[a]);
+        for (int a = 0; a < 6; ++a) {
+          sdsum[a] += sd[a];
+          bfv[a] = fmaf(sd[a], fc, bfv[a]);
 #pragma unroll
-        for (int b = 0; b <= a; ++b, ++k) Hs[k] = fmaf(sd[a], sd[b], Hs[k]);
+          for (int b = 0; b <= a; ++b, ++k) Hs[k] = fmaf(sd[a], sd[b], Hs[k]);
+        }
       }
     }
-   }
   }
   q = warp_sum(q);
   const float df = sqrtf(q);
@@ -261,17 +295,27 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       sdsum[k] = warp_sum(sdsum[k]);
       bfv[k] = warp_sum(bfv[k]);
     }
-  }
-  // IC-GN: factor H once (in the solve precision); lane k < 6 keeps row k of
-  // H^-1, so each iteration's solve is six multiply-adds per lane
-  TS hrow[6];
-  if (!FANR) {
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        ssd[k] = sdsum[k];
+        sbf[k] = bfv[k];
+      }
+    }
+    // factor H once (in the solve precision); lane k < 6 stores row k of
+    // H^-1, so each iteration's solve is six multiply-adds per lane
     TS L[6][6], rinv[6];
     if (!chol6_packed<TS>(Hs, L, rinv)) {
       write_out(0.f, 0, kSingular);
       return;
     }
-    chol6_inverse_col<TS>(L, rinv, lane < 6 ? lane : 0, hrow);
+    if (lane < 6) {
+      TS col[6];
+      chol6_inverse_col<TS>(L, rinv, lane, col);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) hinv[lane * 6 + a] = col[a];
+    }
+    __syncwarp();
   }
   if (!corners_in(prm, x0, y0, M, W, H)) {
     write_out(0.f, 0, kOutOfBounds);
@@ -300,7 +344,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       s1 = fmaf(d, d, s1);
       const float fdx = (float)dx, fdy = (float)dy;
       if (!FANR) {
-        const float2 gr = sgrad[i];
+        const float2 gr = GS::unpack(sgrad[i]);
         const float a = gr.x * d, b = gr.y * d;
         acc[0] += a;
         acc[1] = fmaf(a, fdx, acc[1]);
@@ -309,6 +353,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
         acc[4] = fmaf(b, fdx, acc[4]);
         acc[5] = fmaf(b, fdy, acc[5]);
       } else {
+        const float fc = fval(dx, dy) - fbar;
         const float J[6] = {gx, gx * fdx, gx * fdy, gy, gy * fdx, gy * fdy};
         int k = 0;
 #pragma unroll
@@ -317,9 +362,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
           for (int b = 0; b <= a; ++b, ++k) acc[k] = fmaf(J[a], J[b], acc[k]);  // 21 sums
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
-          acc[21 + a] = fmaf(J[a], d, acc[21 + a]);     // sum J (g - c)
-          acc[27 + a] = fmaf(J[a], sfc[i], acc[27 + a]);  // sum J (f - fbar)
-          acc[33 + a] += J[a];                          // sum J
+          acc[21 + a] = fmaf(J[a], d, acc[21 + a]);   // sum J (g - c)
+          acc[27 + a] = fmaf(J[a], fc, acc[27 + a]);  // sum J (f - fbar)
+          acc[33 + a] += J[a];                        // sum J
         }
       }
     }
@@ -339,10 +384,11 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     if (!FANR) {
       const float ratio = df / dg;
 #pragma unroll
-      for (int a = 0; a < 6; ++a) rhs[a] = bfv[a] - ratio * (acc[a] - gm * sdsum[a]);
+      for (int a = 0; a < 6; ++a) rhs[a] = sbf[a] - ratio * (acc[a] - gm * ssd[a]);
       TS acc6 = TS(0);
+      const TS* hr = hinv + (lane < 6 ? lane : 0) * 6;
 #pragma unroll
-      for (int a = 0; a < 6; ++a) acc6 += hrow[a] * (TS)rhs[a];
+      for (int a = 0; a < 6; ++a) acc6 += hr[a] * (TS)rhs[a];
       const float mine = (float)(-acc6);
 #pragma unroll
       for (int a = 0; a < 6; ++a) dp[a] = __shfl_sync(0xffffffffu, mine, a);
@@ -400,7 +446,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
-      sfg = fmaf(sfc[i], d, sfg);
+      sfg = fmaf(fval(w.dx, w.dy) - fbar, d, sfg);
     }
   }
   s0 = warp_sum(s0);
@@ -415,17 +461,14 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 
 // One warp per POI of one pair.
 template <bool FANR, typename TS, typename TP>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, DIC_SUB_MINB)
+__global__ void __launch_bounds__(32 * kWarpsPerCta, FANR ? 1 : DIC_SUB_MINB)
 subpixel_kernel(const SubpixelParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t poi = (int64_t)blockIdx.x * kWarpsPerCta + wid;
   if (poi >= p.n_pois) return;
-  const int N = p.S * p.S;
-  float2* sgrad = reinterpret_cast<float2*>(smem) + (size_t)wid * N;
-  float* sfc = reinterpret_cast<float*>(smem + (size_t)kWarpsPerCta * N * sizeof(float2)) +
-               (size_t)wid * N;
-  subpixel_poi<FANR, TS, TP>(p, poi, lane, sgrad, sfc);
+  const size_t wb = warp_smem_bytes(p.S * p.S, sizeof(typename GradStore<TP>::T));
+  subpixel_poi<FANR, TS, TP>(p, poi, lane, smem + (size_t)wid * wb);
 }
 
 // Persistent form over many pairs: every warp repeatedly takes the next POI
@@ -438,9 +481,8 @@ subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
                       unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float2* sgrad = reinterpret_cast<float2*>(smem) + (size_t)wid * nmax;
-  float* sfc = reinterpret_cast<float*>(smem + (size_t)WPC * nmax * sizeof(float2)) +
-               (size_t)wid * nmax;
+  // room for the larger (float2) gradient store of the two image types
+  unsigned char* wsm = smem + (size_t)wid * warp_smem_bytes(nmax, sizeof(float2));
   const int64_t total = offsets[njobs];
   for (;;) {
     long long item = 0;
@@ -454,16 +496,17 @@ subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
     }
     const SubpixelParams p = jobs[lo];
     if (p.ref_f32)
-      subpixel_poi<FANR, TS, float>(p, item - offsets[lo], lane, sgrad, sfc);
+      subpixel_poi<FANR, TS, float>(p, item - offsets[lo], lane, wsm);
     else
-      subpixel_poi<FANR, TS, uint8_t>(p, item - offsets[lo], lane, sgrad, sfc);
+      subpixel_poi<FANR, TS, uint8_t>(p, item - offsets[lo], lane, wsm);
     __syncwarp();
   }
 }
 
 template <bool FANR, typename TS, typename TP>
 cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
-  const size_t smem = (size_t)kWarpsPerCta * p.S * p.S * (sizeof(float2) + sizeof(float));
+  const size_t smem =
+      (size_t)kWarpsPerCta * warp_smem_bytes(p.S * p.S, sizeof(typename GradStore<TP>::T));
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS, TP>,
@@ -478,7 +521,7 @@ cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
 template <bool FANR, typename TS, int WPC>
 cudaError_t launch_batch_one(const SubpixelParams* jobs, const int64_t* offsets, int njobs,
                              int nmax, unsigned long long* counter, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)WPC * nmax * (sizeof(float2) + sizeof(float));
+  const size_t smem = (size_t)WPC * warp_smem_bytes(nmax, sizeof(float2));
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(subpixel_batch_kernel<FANR, TS, WPC>,
