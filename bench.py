@@ -36,6 +36,32 @@ L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
 FP32_LANES_PER_SM = 128
 
 
+# FP32 operations per interpolated sample of the sub-pixel refinement
+# (IC-GN): warp 8, Keys weights 2 x 17, 4x4 convolution 35, residual and
+# right-hand-side sums 16.
+FLOP_PER_SAMPLE = 93
+# kernels launched per step: precompute, then the integer search (phase
+# images, template bank, two box-sum maps, tile, reduce; or one FP32 search
+# kernel), then the sub-pixel kernel
+LAUNCHES_TC = 1 + 6 + 1
+LAUNCHES_PLAIN = 1 + 1 + 1
+
+
+def traffic_of(name: str):
+    """DRAM bytes per launch from a committed ncu summary, only while every
+    source it was taken on is unchanged (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        meta = json.load(open(path))
+        for rel, digest in meta["sources"].items():
+            if hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest() != digest:
+                return None
+        return meta.get("bytes_per_launch")
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -166,16 +192,20 @@ def run_gpu(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(dd, search_events=None):
+    def step(dd, events=None):
+        # events: (before search, after search, after sub-pixel), on the
+        # stream the kernels are launched on
         dic.dic_set_pair(dd.h, ref_d, def_d)
-        if search_events:
-            search_events[0].record(stream)
+        if events:
+            events[0].record(stream)
         dic.dic_integer_search(dd.h, s_out["u0"], s_out["v0"], s_out["zncc0"], s_out["status0"])
-        if search_events:
-            search_events[1].record(stream)
+        if events:
+            events[1].record(stream)
         dic.dic_subpixel(dd.h, dic.DIC_ICGN, s_out["u0"], s_out["v0"], s_out["status0"],
                          p_out["u"], p_out["v"], p_out["ux"], p_out["uy"], p_out["vx"],
                          p_out["vy"], p_out["zncc"], p_out["iters"], p_out["status"])
+        if events:
+            events[2].record(stream)
 
     def timed_loop(dd, steps, warmup, sampler=None):
         with torch.cuda.stream(stream):
@@ -190,7 +220,7 @@ def run_gpu(args):
             sampler.start()
         starts = [ev() for _ in range(steps)]
         ends = [ev() for _ in range(steps)]
-        sev = [(ev(), ev()) for _ in range(steps)]
+        sev = [(ev(), ev(), ev()) for _ in range(steps)]
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for i in range(steps):
@@ -202,12 +232,14 @@ def run_gpu(args):
         wall = time.perf_counter() - t0
         clocks = sampler.stop() if sampler else None
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        search_ms = [a.elapsed_time(b) for a, b in sev]
+        search_ms = [a.elapsed_time(b) for a, b, _ in sev]
+        sub_ms = [b.elapsed_time(c) for _, b, c in sev]
         conv = int((p_out["status"] == 0).sum().item())
-        return step_ms, search_ms, conv, wall, clocks
+        return step_ms, (search_ms, sub_ms), conv, wall, clocks
 
     sampler = ClockSampler(local)
-    step_ms, search_ms, conv, wall, clocks = timed_loop(d, args.steps, args.warmup, sampler)
+    step_ms, (search_ms, sub_ms), conv, wall, clocks = timed_loop(d, args.steps, args.warmup,
+                                                                   sampler)
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
@@ -227,7 +259,7 @@ def run_gpu(args):
     d32.set_pair(ref_d, def_d)
     st32, se32, conv32, _, _ = timed_loop(d32, max(10, args.steps // 4), 3)
     plain_value = conv32 * len(st32) / (sum(st32) / 1e3)
-    plain_search_ms = statistics.mean(se32)
+    plain_search_ms = statistics.mean(se32[0])
     d32.close()
 
     # e2e through the public call with host buffers: H2D of both images,
@@ -260,44 +292,51 @@ def run_gpu(args):
            "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_out.values())
                                      + sum(v.numel() * v.element_size() for v in h_s.values()))}
 
-    # roofline of the dominant kernel (integer search), algorithmic flops
-    # 2 N (2R+1)^2 per POI (the padded / wasted MACs are not counted)
-    search_avg_s = statistics.mean(search_ms) / 1e3
-    flops = 2.0 * SUBSET * SUBSET * (2 * RADIUS + 1) ** 2 * n
+    # rooflines.  Dominant kernel: the sub-pixel refinement (one launch per
+    # step), bound by FP32 issue; algorithmic work = FLOP_PER_SAMPLE per
+    # interpolated subset sample, N samples per pass, (iterations + 1)
+    # passes per POI (the last pass evaluates Eq. 1 at the returned shape).
     peak_mhz = 2070.0
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
+    fp32_basis = (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                  f"x {peak_mhz:.0f} MHz (nominal max clock)")
+    started = (s_out["status0"] == 0)
+    passes = int((p_out["iters"].to(torch.int64) + 1)[started].sum().item())
+    samples = passes * SUBSET * SUBSET
+    sub_avg_s = statistics.mean(sub_ms) / 1e3
+    sub_achieved = FLOP_PER_SAMPLE * samples / sub_avg_s / 1e12
+    roofline = {"bound": "alu", "achieved": sub_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": sub_achieved / fp32_peak,
+                "traffic": traffic_of("subpixel_affine1024_traffic.json"),
+                "kernel": f"subpixel_kernel<IC-GN, fp{args.solve_bits} solve>",
+                "peak_basis": fp32_basis, "ms": sub_avg_s * 1e3,
+                "work": f"{FLOP_PER_SAMPLE} flop x {samples} interpolated samples per launch"}
+    # the integer search: algorithmic flops 2 N (2R+1)^2 per POI (padded and
+    # wasted MACs not counted)
+    search_avg_s = statistics.mean(search_ms) / 1e3
+    flops = 2.0 * SUBSET * SUBSET * (2 * RADIUS + 1) ** 2 * n
     if args.form == "tc":
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
         peak = float(peaks.get("bf16_tflops", 1900.0))
-        bound, kernel = "tensor", "integer search, tensor-core form (bank + tile + reduce kernels)"
+        bound, kernel = "tensor", ("integer search, tensor-core form (phase + bank + box-map + "
+                                   "tile + reduce kernels)")
         basis = ("measured dense BF16 (cuBLAS burst) " + ("of measured" if peaks else "of fallback"))
-        prof = os.path.join(ROOT, "profiles", "search_tc_affine1024_traffic.json")
+        prof = "search_tc_affine1024_traffic.json"
     else:
         peak = fp32_peak
         bound, kernel = "alu", "search_kernel (FP32 FMA correlation)"
-        basis = (f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz "
-                 "(nominal max clock)")
-        prof = os.path.join(ROOT, "profiles", "search_affine1024_traffic.json")
+        basis = fp32_basis
+        prof = "search_affine1024_traffic.json"
     achieved = flops / search_avg_s / 1e12
-    traffic = None
-    if os.path.exists(prof):
-        # counters apply only while the kernel source is the one they were taken on
-        try:
-            import hashlib
-            meta = json.load(open(prof))
-            src = open(os.path.join(ROOT, meta["source"]), "rb").read()
-            if hashlib.sha256(src).hexdigest() == meta.get("source_sha256"):
-                traffic = meta.get("bytes_per_launch")
-        except (OSError, ValueError, KeyError):
-            traffic = None
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
-                "peak_basis": basis, "search_ms": search_avg_s * 1e3,
-                "plain_fp32_search": {"ms": plain_search_ms,
-                                      "achieved_tflops": flops / (plain_search_ms / 1e3) / 1e12,
-                                      "frac_of_fp32_peak": flops / (plain_search_ms / 1e3) / 1e12
-                                      / fp32_peak}}
+    roofline_search = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                       "frac": achieved / peak, "traffic": traffic_of(prof), "kernel": kernel,
+                       "peak_basis": basis, "ms": search_avg_s * 1e3,
+                       "plain_fp32_search": {"ms": plain_search_ms,
+                                             "achieved_tflops": flops / (plain_search_ms / 1e3)
+                                             / 1e12,
+                                             "frac_of_fp32_peak": flops / (plain_search_ms / 1e3)
+                                             / 1e12 / fp32_peak}}
 
     cpu = None
     if rank == 0:
@@ -311,8 +350,10 @@ def run_gpu(args):
                 "dtype": "bf16+f32" if args.form == "tc" else "f32",
                 "data": "synthetic (seeded speckle renders)",
                 "config": config_dict(world), "e2e": e2e,
-                "gpu_launches": (5 if args.form == "tc" else 3) * args.steps,
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": (LAUNCHES_TC if args.form == "tc" else LAUNCHES_PLAIN)
+                * args.steps,
+                "roofline": roofline, "roofline_search": roofline_search,
+                "cpu_baseline": cpu, "clocks": clocks,
                 "forms": {"chosen": {"search": "bf16-tensor-core-exact" if args.form == "tc"
                                      else "fp32-exact", "solve": f"fp{args.solve_bits}",
                                      "value": value},
