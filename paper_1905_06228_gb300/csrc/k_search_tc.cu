@@ -1,39 +1,44 @@
 // k_search_tc.cu -- brute-force ZNCC integer search (Eq. 1, Section 2.1) as
-// a BF16 tensor-core contraction (tcgen05, TMEM accumulators).
+// a BF16 tensor-core contraction (tcgen05, TMEM accumulators, TMA).
 //
 // Correlation sums as one implicit GEMM across POIs.  Let a "position" be an
 // absolute top-left corner (Y, X) of a subset in the deformed image; POI p
 // (top-left (yp-M, xp-M)) needs every position with |Y-(yp-M)|, |X-(xp-M)|
-// <= R.  For a tile of 128 positions (16 rows x 8 columns) and the N POIs
-// whose windows meet the tile:
+// <= R.  For a tile of 128 positions (16 rows x 8 columns, X0 a multiple of
+// 8) and the block of POIs whose windows meet the tile:
 //
 //   D[m][n] = sum_ty sum_tx  G[Y0+q+ty][X0+r+tx] * T_n[ty][tx],   m = 8q + r
 //
-// A (M = 128 positions x K = taps) is read through a K-major no-swizzle
-// shared-memory descriptor from eight shifted copies of each image row
-// (core matrix = 8 positions x 8 taps), so the step ty -> ty+1 is only a
-// descriptor offset of one image row; B (N POIs x K) is the ty-th template
-// row of every POI, streamed per ty from a template bank with cp.async.
-// Both operands use 128-byte 8-tap blocks (LBO = 128 B) and 8-row groups of
-// one row's blocks (SBO = TWK/8 * 128 B).
-// One tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M=128, N<=256, K=16) per
-// 16 taps; the accumulator lives in TMEM.
+// Operands are K-major with rows of TWK taps (16, 32 or 64; 2*TWK bytes, the
+// swizzle width of both the TMA boxes and the MMA descriptors):
+//  A (M = 128 positions): row (q, r) at image row Y0+q+ty holds
+//    g[Y0+q+ty][X0+r ..] - 128, i.e. row Y0+q+ty of the phase image r (the
+//    copy of g shifted by r columns).  One 3-D TMA box loads all tile rows
+//    once; an 8-row group is one image row, so the step ty -> ty+1 is a
+//    descriptor offset of one group.
+//  B (N = POI block): row n holds template row ty of POI n from the
+//    template bank (every subset of f, POI-major rows); one 4-D TMA box per
+//    template row loads the whole block, streamed through a ring of stages.
+// One thread issues the TMA loads, one thread the MMAs (tcgen05.mma
+// kind::f16, BF16 x BF16 -> FP32, M=128, K=16 per instruction), paired by
+// full/empty mbarriers; the accumulator lives in TMEM.
 //
 // Exactness: a = f-128 and b = g-128 are integers in [-128, 127], exact in
 // BF16; |ab| <= 2^14, so any sum of at most 1024 products is an integer
 // below 2^24 and the FP32 accumulation is exact.  Subsets wider than 32 use
 // several accumulators (blocks of floor(1024/TWK) template rows), added in
-// int32 by the epilogue.  The candidate scores then use the same exact
-// integers as the FP32 form: num = N Sab - Sa Sb, Dg = N Sbb - Sb^2, with
-// Sa, Saa per POI and Sb, Sbb per position (box sums of the tile).
+// int32 by the epilogue.  Candidate scores use the exact integers
+// num = N Sab - Sa Sb, Dg = N Sbb - Sb^2, with Sa, Saa per POI and Sb, Sbb
+// per position (box sums of f and g).
 //
-// Epilogue: TMEM -> registers -> shared memory (transposed), then thread n
-// scans the 128 positions for POI n and keeps the exact best (float
-// pre-filter, exact 128-bit comparison, lowest linear index on ties).  Each
-// (tile, POI) best goes to a slot; a final kernel reduces a POI's slots
-// exactly and re-ranks its top four candidates by recomputing their sums on
-// the CUDA cores from the images, so the integer result is bit-identical to
-// the FP32 form and to the oracle.
+// Epilogue: each warp reads one lane quarter of TMEM (32 positions) x 16
+// POIs, scores sign(num) num^2 / Dg in FP32 (errors bounded, see
+// score_block) and keeps each POI's best two through a warp reduce-scatter;
+// a POI's float winner is its exact tile winner when it clears the second
+// by 5e-4, otherwise one warp compares the near-tied positions exactly.
+// Each (tile, POI) winner goes to a slot; a final kernel reduces a POI's
+// slots exactly (lowest linear index on ties), so the integer result is
+// bit-identical to the FP32 form and to the oracle.
 #include <algorithm>
 
 #include "dic_device.cuh"
