@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--solve-bits", type=int, default=64)
+    ap.add_argument("--solve-bits", type=int, default=32)
     ap.add_argument("--form", default="tc", choices=["tc", "fp32"],
                     help="integer-search form of the chosen configuration")
     ap.add_argument("--cpu-sample", type=int, default=8192,

@@ -154,17 +154,40 @@ __device__ __forceinline__ void compose_inverse(float p[6], const float dp[6]) {
   p[5] = n11 - 1.f;
 }
 
+// Diagonal of a packed symmetric 6x6 scaled to one: Hs = D H D with
+// D_ii = H_ii^-1/2 (1 where H_ii <= 0, which the factorisation then rejects).
+__device__ __forceinline__ void unit_diagonal(const float Hf[21], float Hs[21], float dsc[6]) {
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    k += a;  // index of H[a][a] in the packed lower triangle
+    dsc[a] = Hf[k] > 0.f ? rsqrt_refined<float>(Hf[k]) : 1.f;
+    ++k;
+  }
+  k = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b, ++k) Hs[k] = Hf[k] * (dsc[a] * dsc[b]);
+}
+
+// Solve H x = b through the unit-diagonal form: (D H D) y = D b, x = D y.
 template <typename T>
 __device__ __forceinline__ bool solve6(const float Hf[21], const float bf[6], float out[6],
                                        bool negate) {
+  float Hs[21], dsc[6];
+  unit_diagonal(Hf, Hs, dsc);
   T L[6][6], rinv[6];
-  if (!chol6_packed<T>(Hf, L, rinv)) return false;
+  if (!chol6_packed<T>(Hs, L, rinv)) return false;
   T b[6], x[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) b[i] = (T)bf[i];
+  for (int i = 0; i < 6; ++i) b[i] = (T)bf[i] * (T)dsc[i];
   chol6_solve_r<T>(L, rinv, b, x);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) out[i] = negate ? (float)(-x[i]) : (float)x[i];
+  for (int i = 0; i < 6; ++i) {
+    const float xi = (float)(x[i] * (T)dsc[i]);
+    out[i] = negate ? -xi : xi;
+  }
   return true;
 }
 
@@ -303,7 +326,12 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       }
     }
     // factor H once (in the solve precision); lane k < 6 stores row k of
-    // H^-1, so each iteration's solve is six multiply-adds per lane
+    // H^-1, so each iteration's solve is six multiply-adds per lane.  H is
+    // first scaled symmetrically to a unit diagonal (Hs = D H D, D_ii =
+    // H_ii^-1/2; H^-1 = D Hs^-1 D): the translation and gradient columns
+    // differ in scale by ~M^2, which the factorisation then does not see.
+    float dsc[6];
+    unit_diagonal(Hs, Hs, dsc);
     TS L[6][6], rinv[6];
     if (!chol6_packed<TS>(Hs, L, rinv)) {
       write_out(0.f, 0, kSingular);
@@ -313,7 +341,8 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       TS col[6];
       chol6_inverse_col<TS>(L, rinv, lane, col);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) hinv[lane * 6 + a] = col[a];
+      for (int a = 0; a < 6; ++a)
+        hinv[lane * 6 + a] = col[a] * (TS)dsc[lane] * (TS)dsc[a];
     }
     __syncwarp();
   }

@@ -39,10 +39,11 @@ def test_rigid256_full(rigid256, method, solve_bits):
 
 
 # ------------------------------------------- bench workload, sampled POIs
-@pytest.mark.parametrize("method", [0, 1])
-def test_affine1024_sampled(affine1024, method):
+@pytest.mark.parametrize("method,solve_bits", [(0, 32), (0, 64), (1, 32), (1, 64)])
+def test_affine1024_sampled(affine1024, method, solve_bits):
     p = affine1024
-    gpu = run_gpu(p.ref, p.defm, p.subset, p.step, p.radius, method=method, solve_bits=64)
+    gpu = run_gpu(p.ref, p.defm, p.subset, p.step, p.radius, method=method,
+                  solve_bits=solve_bits)
     assert gpu["n"] == 36100
     rng = np.random.default_rng(11)
     idx = np.sort(rng.choice(gpu["n"], 1500, replace=False))
