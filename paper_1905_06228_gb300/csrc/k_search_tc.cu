@@ -123,6 +123,12 @@ __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
   return a.l < b.l;
 }
 
+// BF16 bits of (byte - 128), exactly: the float 2^23 + byte minus 2^23 + 128
+// (one integer OR and one FP32 add instead of an int-to-float conversion).
+__device__ __forceinline__ uint32_t centred_bf16(uint32_t byte) {
+  return __float_as_uint(__uint_as_float(0x4B000000u | byte) - 8388736.0f) >> 16;
+}
+
 // ------------------------------------------------------------ phase images
 // Eight copies of the deformed image shifted by s = 0..7 pixels, as centred
 // BF16:  ph[s][y][c] = g[y][c + s] - 128  (0 outside the image),
@@ -130,12 +136,12 @@ __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
 // aligned 16-byte chunk: copy s = x mod 8 at column x - s.  One thread per
 // 16-byte chunk.
 __global__ void phase_kernel(const SearchTcParams p) {
-  const int64_t chunk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int cpr = p.phw / 8;  // chunks per row
-  if (chunk >= (int64_t)8 * p.phh * cpr) return;
-  const int sft = (int)(chunk / ((int64_t)p.phh * cpr));
-  const int64_t rem = chunk % ((int64_t)p.phh * cpr);
-  const int y = (int)(rem / cpr), c = (int)(rem % cpr) * 8;
+  const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (chunk >= 8 * p.phh * cpr) return;
+  const int row = chunk / cpr;  // sft * phh + y
+  const int c = (chunk - row * cpr) * 8;
+  const int sft = row / p.phh, y = row - sft * p.phh;
   uint32_t w[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -143,12 +149,12 @@ __global__ void phase_kernel(const SearchTcParams p) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int x = c + sft + 2 * e + k;
-      const int v = (x < p.W && y < p.H) ? (int)p.def[(size_t)y * p.pitch + x] - 128 : 0;
-      h2[k] = __float_as_uint((float)v) >> 16;  // small integers are exact in BF16
+      // small integers are exact in BF16; 0 outside the image
+      h2[k] = (x < p.W && y < p.H) ? centred_bf16(p.def[(size_t)y * p.pitch + x]) : 0u;
     }
     w[e] = h2[0] | (h2[1] << 16);
   }
-  uint16_t* dst = p.gph + ((size_t)sft * p.phh + y) * p.phw + c;
+  uint16_t* dst = p.gph + (size_t)row * p.phw + c;
   *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
@@ -159,14 +165,12 @@ __global__ void phase_kernel(const SearchTcParams p) {
 // is contiguous, so a tile's template rows stream as runs of 16-byte chunks.
 // One thread per 16-byte chunk.
 __global__ void bank_kernel(const SearchTcParams p) {
+  // blockIdx.y = kr * S + ty (one bank row); threads over (kc, kb)
   const int KB = p.twk / 8;
-  const int64_t chunk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (chunk >= (int64_t)p.ny * p.S * p.nx * KB) return;
-  const int kb = (int)(chunk % KB);
-  int64_t rest = chunk / KB;
-  const int kc = (int)(rest % p.nx);
-  rest /= p.nx;
-  const int ty = (int)(rest % p.S), kr = (int)(rest / p.S);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.nx * KB) return;
+  const int kc = t / KB, kb = t - kc * KB;
+  const int kr = blockIdx.y / p.S, ty = blockIdx.y - kr * p.S;
   const int B = p.M + p.R + 2;
   const int xl = B + kc * p.step - p.M, yl = B + kr * p.step - p.M;
   const uint8_t* src = p.ref + (size_t)(yl + ty) * p.pitch + xl;
@@ -177,56 +181,96 @@ __global__ void bank_kernel(const SearchTcParams p) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int tx = 8 * kb + 2 * e + k;
-      const int v = tx < p.S ? (int)src[tx] - 128 : 0;
-      h2[k] = __float_as_uint((float)v) >> 16;
+      h2[k] = tx < p.S ? centred_bf16(src[tx]) : 0u;
     }
     w[e] = h2[0] | (h2[1] << 16);
   }
-  *reinterpret_cast<uint4*>(p.bank + chunk * 8) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(p.bank + ((size_t)blockIdx.y * p.nx * KB + t) * 8) =
+      make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// ------------------------------------------------------------ box-sum map
-// posbox[py*pw + px] = (sum b, sum b^2) over the S x S subset whose top-left
-// is the position (ymin+py, xmin+px); b = g - 128, 0 outside the image.
-// 32 x 32 positions per CTA, separable sums through shared memory.
-constexpr int kBoxT = 32;
-__global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p, int which) {
+// ------------------------------------------------------------ box-sum maps
+// map[py*pw + px] = (sum v, sum v^2) over the S x S subset whose top-left is
+// the position (ymin+py, xmin+px), v = image - 128 (0 outside the image):
+// blockIdx.z = 0 for f (POI sums, fbox), 1 for g (position sums, posbox).
+// A CTA covers kBoxX x kBoxY outputs: the centred pixels go to shared
+// memory, then separable sums, each thread sliding an S-wide window over
+// kBoxSeg consecutive outputs (one add and one subtract per output after the
+// first).  All sums are exact integers.
+constexpr int kBoxX = 64, kBoxY = 32, kBoxSeg = 8;
+
+// Row strides in shared memory: pixels padded to an odd number of words and
+// row sums to kBoxX + 1 int2, so that lanes walking consecutive rows hit
+// distinct banks.
+__host__ __device__ inline int boxmap_vstride(int S) { return (kBoxX + S - 1) | 1; }
+constexpr int kBoxHs = kBoxX + 1;
+
+__host__ __device__ inline size_t boxmap_smem(int S) {
+  return (size_t)(kBoxY + S - 1) * boxmap_vstride(S) * 4 + (size_t)(kBoxY + S - 1) * kBoxHs * 8;
+}
+
+__global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
+  const int which = blockIdx.z;
   const uint8_t* img = which ? p.def : p.ref;
   int2* out = which ? p.posbox : p.fbox;
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int S = p.S, span = kBoxT + S - 1;
-  int* rowb = reinterpret_cast<int*>(smem);          // [span][span] bytes - 128
-  int2* hs = reinterpret_cast<int2*>(rowb + span * span);  // [span][kBoxT]
-  const int px0 = blockIdx.x * kBoxT, py0 = blockIdx.y * kBoxT;
+  const int S = p.S, sw = kBoxX + S - 1, sh = kBoxY + S - 1, vs = boxmap_vstride(S);
+  int* v = reinterpret_cast<int*>(smem);                    // [sh][vs]
+  int2* hs = reinterpret_cast<int2*>(v + (size_t)sh * vs);  // [sh][kBoxHs]
+  const int px0 = blockIdx.x * kBoxX, py0 = blockIdx.y * kBoxY;
   const int X0 = p.xmin + px0, Y0 = p.ymin + py0;
-  for (int i = threadIdx.x; i < span * span; i += blockDim.x) {
-    const int r = i / span, c = i % span, y = Y0 + r, x = X0 + c;
-    rowb[i] = (x >= 0 && x < p.W && y >= 0 && y < p.H)
-                  ? (int)img[(size_t)y * p.pitch + x] - 128 : 0;
+  for (int r = threadIdx.x >> 5; r < sh; r += blockDim.x >> 5) {
+    const int y = Y0 + r;
+    const bool yin = y >= 0 && y < p.H;
+    for (int c = threadIdx.x & 31; c < sw; c += 32) {
+      const int x = X0 + c;
+      v[r * vs + c] = (yin && x >= 0 && x < p.W) ? (int)img[(size_t)y * p.pitch + x] - 128 : 0;
+    }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < span * kBoxT; i += blockDim.x) {
-    const int r = i / kBoxT, c = i % kBoxT;
+  // rows: thread t -> row t % sh, segment t / sh
+  for (int t = threadIdx.x; t < sh * (kBoxX / kBoxSeg); t += blockDim.x) {
+    const int r = t % sh, c0 = (t / sh) * kBoxSeg;
+    const int* row = v + (size_t)r * vs + c0;
     int a = 0, b = 0;
-    for (int t = 0; t < S; ++t) {
-      const int v = rowb[r * span + c + t];
-      a += v;
-      b += v * v;
+    for (int k = 0; k < S; ++k) {
+      const int x = row[k];
+      a += x;
+      b += x * x;
     }
-    hs[i] = make_int2(a, b);
+    int2* o = hs + (size_t)r * kBoxHs + c0;
+    o[0] = make_int2(a, b);
+#pragma unroll
+    for (int j = 1; j < kBoxSeg; ++j) {
+      const int xo = row[j - 1], xi = row[j + S - 1];
+      a += xi - xo;
+      b += xi * xi - xo * xo;
+      o[j] = make_int2(a, b);
+    }
   }
   __syncthreads();
-  const int pw = p.ntx * 8;
-  for (int i = threadIdx.x; i < kBoxT * kBoxT; i += blockDim.x) {
-    const int r = i / kBoxT, c = i % kBoxT;
-    if (py0 + r >= p.nty * 16 || px0 + c >= pw) continue;
+  // columns: thread t -> column t % kBoxX, segment t / kBoxX
+  const int pw = p.ntx * 8, ph = p.nty * 16;
+  for (int t = threadIdx.x; t < kBoxX * (kBoxY / kBoxSeg); t += blockDim.x) {
+    const int c = t % kBoxX, r0 = (t / kBoxX) * kBoxSeg;
+    const int2* col = hs + (size_t)r0 * kBoxHs + c;
     int a = 0, b = 0;
-    for (int t = 0; t < S; ++t) {
-      const int2 v = hs[(r + t) * kBoxT + c];
-      a += v.x;
-      b += v.y;
+    for (int k = 0; k < S; ++k) {
+      const int2 x = col[(size_t)k * kBoxHs];
+      a += x.x;
+      b += x.y;
     }
-    out[(size_t)(py0 + r) * pw + (px0 + c)] = make_int2(a, b);
+    const int px = px0 + c;
+#pragma unroll
+    for (int j = 0; j < kBoxSeg; ++j) {
+      if (j > 0) {
+        const int2 xo = col[(size_t)(j - 1) * kBoxHs], xi = col[(size_t)(j + S - 1) * kBoxHs];
+        a += xi.x - xo.x;
+        b += xi.y - xo.y;
+      }
+      const int py = py0 + r0 + j;
+      if (px < pw && py < ph) out[(size_t)py * pw + px] = make_int2(a, b);
+    }
   }
 }
 
@@ -838,6 +882,10 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   const int hneed = std::max(H, g->ymin + g->nty * kTileQ + S + 1);
   g->phw = (wneed + 7) / 8 * 8;
   g->phh = hneed;
+  // grid rows of the bank launch, 32-bit chunk indices of the phase images
+  if (g->phh > 65535 || (long long)ny * S > 65535 ||
+      (long long)g->phh * g->phw >= (1ll << 31))
+    return false;
   return true;
 }
 
@@ -861,10 +909,10 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   const unsigned wblocks = (unsigned)((p.n_pois + 7) / 8);
   cudaError_t e;
   {
-    const int64_t chunks = (int64_t)8 * p.phh * (p.phw / 8);
-    phase_kernel<<<(unsigned)((chunks + 255) / 256), 256, 0, st>>>(p);
-    const int64_t bchunks = (int64_t)p.ny * p.S * p.nx * (p.twk / 8);
-    bank_kernel<<<(unsigned)((bchunks + 255) / 256), 256, 0, st>>>(p);
+    const int chunks = 8 * p.phh * (p.phw / 8);  // 16-byte chunks of the phase images
+    phase_kernel<<<(chunks + 255) / 256, 256, 0, st>>>(p);
+    const int per_row = p.nx * (p.twk / 8);
+    bank_kernel<<<dim3((per_row + 127) / 128, p.ny * p.S), 128, 0, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -872,16 +920,14 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   e = cudaMemsetAsync(p.slots, 0xff, sizeof(SlotCand) * (size_t)p.n_pois * p.nslots, st);
   if (e != cudaSuccess) return e;
   {
-    const int span = kBoxT + p.S - 1;
-    const size_t bsm = (size_t)span * span * 4 + (size_t)span * kBoxT * 8;
+    const size_t bsm = boxmap_smem(p.S);
     if (bsm > 48 * 1024) {
       e = cudaFuncSetAttribute(boxmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)bsm);
       if (e != cudaSuccess) return e;
     }
-    dim3 grid((p.ntx * 8 + kBoxT - 1) / kBoxT, (p.nty * 16 + kBoxT - 1) / kBoxT);
-    boxmap_kernel<<<grid, 256, bsm, st>>>(p, 1);
-    boxmap_kernel<<<grid, 256, bsm, st>>>(p, 0);
+    dim3 grid((p.ntx * 8 + kBoxX - 1) / kBoxX, (p.nty * 16 + kBoxY - 1) / kBoxY, 2);
+    boxmap_kernel<<<grid, 256, bsm, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
