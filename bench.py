@@ -38,8 +38,8 @@ FP32_LANES_PER_SM = 128
 
 # FP32 operations per interpolated sample of the sub-pixel refinement
 # (IC-GN): warp 8, Keys weights 2 x 17, 4x4 convolution 35, residual and
-# right-hand-side sums 16.
-FLOP_PER_SAMPLE = 93
+# right-hand-side sums 16, the cross sum of Eq. 1 3.
+FLOP_PER_SAMPLE = 96
 # kernels launched per step: precompute, then the integer search (phase
 # images, template bank, two box-sum maps, tile, reduce; or one FP32 search
 # kernel), then the sub-pixel kernel
@@ -294,14 +294,16 @@ def run_gpu(args):
 
     # rooflines.  Dominant kernel: the sub-pixel refinement (one launch per
     # step), bound by FP32 issue; algorithmic work = FLOP_PER_SAMPLE per
-    # interpolated subset sample, N samples per pass, (iterations + 1)
-    # passes per POI (the last pass evaluates Eq. 1 at the returned shape).
+    # interpolated subset sample, N samples per pass.
     peak_mhz = 2070.0
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
     fp32_basis = (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                   f"x {peak_mhz:.0f} MHz (nominal max clock)")
+    # passes per POI: one per iteration, plus one at the returned shape for
+    # POIs that did not converge
     started = (s_out["status0"] == 0)
-    passes = int((p_out["iters"].to(torch.int64) + 1)[started].sum().item())
+    extra = (p_out["status"] != 0).to(torch.int64)
+    passes = int((p_out["iters"].to(torch.int64) + extra)[started].sum().item())
     samples = passes * SUBSET * SUBSET
     sub_avg_s = statistics.mean(sub_ms) / 1e3
     sub_achieved = FLOP_PER_SAMPLE * samples / sub_avg_s / 1e12

@@ -1,9 +1,9 @@
 // k_subpixel.cu -- sub-pixel refinement: IC-GN and FA-NR (Section 2.2, Table 2).
 //
 // One warp per POI; lane l owns subset points i = l, l+32, ...  Per-point
-// reference data (gradients of f, f - fbar, the point's (dx, dy)) lives in
-// shared memory for the whole solve; the deformed image is interpolated from
-// its float copy (Keys weights evaluated per sample).
+// reference data (the gradient of f and f) lives in shared memory for the
+// whole solve; the deformed image is interpolated from its float copy (Keys
+// weights evaluated per sample).
 //
 // Warp:   W(xi; p) = (x0 + dx + u + ux dx + uy dy, y0 + dy + v + vx dx + vy dy).
 // IC-GN:  SD_i = grad f_i dW/dp, H = sum SD^T SD (once per POI),
@@ -23,12 +23,15 @@
 // FP32 or FP64, chosen per launch: a Cholesky factorisation whose diagonal
 // reciprocals come from a refined reciprocal square root (no divisions);
 // IC-GN factors H once and keeps H^-1 (row k on lane k), FA-NR factors its
-// Gauss-Newton matrix every iteration.  The final ZNCC is Eq. 1 at
-// the returned shape (one extra pass).
+// Gauss-Newton matrix every iteration.  Each pass also accumulates
+// sum (f-fbar)(g-c), so a POI that converges reports Eq. 1 at the shape its
+// last pass sampled (the returned shape differs by the final update, below
+// tol, at a stationary point of C: the two values differ by O(|dp|^2));
+// other POIs get one extra pass at the returned shape.
 // resident CTAs per SM requested from the register allocator, and the
 // unroll of the per-point loop (memory-level parallelism of the sample loads)
 #ifndef DIC_SUB_MINB
-#define DIC_SUB_MINB 4
+#define DIC_SUB_MINB 3
 #endif
 #ifndef DIC_SUB_UNROLL
 #define DIC_SUB_UNROLL 1
@@ -202,49 +205,61 @@ __device__ __forceinline__ const float* ref_ptr<float>(const SubpixelParams& p) 
   return p.ref_f32;
 }
 
-// Reference gradients as kept in shared memory: half2 for 8-bit images
-// (central differences of 8-bit pixels are multiples of 1/2 below 128 in
-// magnitude, exact in FP16), float2 for float images.
+// Per-point reference data kept in shared memory: the gradient of f and f.
+// 8-bit images: FP16, 8 bytes per point (central differences of 8-bit
+// pixels are multiples of 1/2 below 128 and the pixels integers below 256,
+// both exact in FP16); float images: FP32, 16 bytes per point.
 template <typename TP>
-struct GradStore;
+struct PointStore;
 template <>
-struct GradStore<uint8_t> {
-  using T = __half2;
-  static __device__ __forceinline__ T pack(float2 g) { return __floats2half2_rn(g.x, g.y); }
-  static __device__ __forceinline__ float2 unpack(T g) { return __half22float2(g); }
+struct PointStore<uint8_t> {
+  struct alignas(8) T {
+    __half2 g;
+    __half2 f;  // (f, 0)
+  };
+  static __device__ __forceinline__ T pack(float2 g, float f) {
+    return T{__floats2half2_rn(g.x, g.y), __floats2half2_rn(f, 0.f)};
+  }
+  static __device__ __forceinline__ void unpack(const T& t, float2& g, float& f) {
+    g = __half22float2(t.g);
+    f = __low2float(t.f);
+  }
 };
 template <>
-struct GradStore<float> {
-  using T = float2;
-  static __device__ __forceinline__ T pack(float2 g) { return g; }
-  static __device__ __forceinline__ float2 unpack(T g) { return g; }
+struct PointStore<float> {
+  struct alignas(16) T {
+    float2 g;
+    float f, pad;
+  };
+  static __device__ __forceinline__ T pack(float2 g, float f) { return T{g, f, 0.f}; }
+  static __device__ __forceinline__ void unpack(const T& t, float2& g, float& f) {
+    g = t.g;
+    f = t.f;
+  }
 };
 
-// Shared memory of one warp: N gradients, then (16-byte aligned) H^-1 as
-// 36 solve-precision values, then the IC-GN constants sum SD and
+// Shared memory of one warp: N point records, then (16-byte aligned) H^-1
+// as 36 solve-precision values, then the IC-GN constants sum SD and
 // sum SD (f - fbar) (6 floats each).
-__host__ __device__ inline size_t warp_smem_bytes(int N, size_t grad_bytes) {
-  return ((size_t)N * grad_bytes + 15) / 16 * 16 + 36 * sizeof(double) + 12 * sizeof(float);
+__host__ __device__ inline size_t warp_smem_bytes(int N, size_t point_bytes) {
+  return ((size_t)N * point_bytes + 15) / 16 * 16 + 36 * sizeof(double) + 12 * sizeof(float);
 }
 
 // Refinement of one POI by one warp; wsm is the warp's shared block.
 template <bool FANR, typename TS, typename TP>
 __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t poi, int lane,
                                              unsigned char* wsm) {
-  using GS = GradStore<TP>;
-  using G = typename GS::T;
+  using PS = PointStore<TP>;
+  using G = typename PS::T;
   const int S = p.S, M = p.M, N = S * S;
   const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
   const int W = p.W, H = p.H;
-  G* sgrad = reinterpret_cast<G*>(wsm);
+  G* spt = reinterpret_cast<G*>(wsm);
   TS* hinv = reinterpret_cast<TS*>(wsm + ((size_t)N * sizeof(G) + 15) / 16 * 16);
   float* ssd = reinterpret_cast<float*>(hinv + 36);  // sum SD
   float* sbf = ssd + 6;                              // sum SD (f - fbar)
   const TP* fimg = ref_ptr<TP>(p);
-  auto fval = [&](int dx, int dy) {
-    return (float)fimg[(size_t)(y0 + dy) * p.pitch + (x0 + dx)];
-  };
 
   const uint8_t st0 = p.st0[poi];
   float prm[6] = {(float)p.u0[poi], 0.f, 0.f, (float)p.v0[poi], 0.f, 0.f};
@@ -272,8 +287,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   {
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
-      fsum += fval(w.dx, w.dy);
-      sgrad[i] = GS::pack(p.grad[(size_t)(y0 + w.dy) * W + (x0 + w.dx)]);
+      const float f = (float)fimg[(size_t)(y0 + w.dy) * p.pitch + (x0 + w.dx)];
+      fsum += f;
+      spt[i] = PS::pack(p.grad[(size_t)(y0 + w.dy) * W + (x0 + w.dx)], f);
     }
   }
   fsum = warp_sum(fsum);  // exact for 8-bit images: integer sum below 2^24
@@ -287,10 +303,12 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   {
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
-      const float fc = fval(w.dx, w.dy) - fbar;
+      float2 gr;
+      float f;
+      PS::unpack(spt[i], gr, f);
+      const float fc = f - fbar;
       q = fmaf(fc, fc, q);
       if (!FANR) {
-        const float2 gr = GS::unpack(sgrad[i]);
         const float dx = (float)w.dx, dy = (float)w.dy;
         const float sd[6] = {gr.x, gr.x * dx, gr.x * dy, gr.y, gr.y * dx, gr.y * dy};
         int k = 0;
@@ -356,8 +374,10 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   const float m2 = (float)M * (float)M;
   uint8_t st = kMaxIter;
   int it_done = 0;
+  float zn = 0.f;
+  bool have_zn = false;  // Eq. 1 already known (converged: at the last sampled shape)
   for (int it = 1; it <= p.max_iter; ++it) {
-    float s0 = 0.f, s1 = 0.f;
+    float s0 = 0.f, s1 = 0.f, sfd = 0.f;
     float acc[FANR ? 39 : 6];
 #pragma unroll
     for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = 0.f;
@@ -371,9 +391,13 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const float d = g - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
+      float2 gr;
+      float f;
+      PS::unpack(spt[i], gr, f);
+      const float fc = f - fbar;
+      sfd = fmaf(fc, d, sfd);
       const float fdx = (float)dx, fdy = (float)dy;
       if (!FANR) {
-        const float2 gr = GS::unpack(sgrad[i]);
         const float a = gr.x * d, b = gr.y * d;
         acc[0] += a;
         acc[1] = fmaf(a, fdx, acc[1]);
@@ -382,7 +406,6 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
         acc[4] = fmaf(b, fdx, acc[4]);
         acc[5] = fmaf(b, fdy, acc[5]);
       } else {
-        const float fc = fval(dx, dy) - fbar;
         const float J[6] = {gx, gx * fdx, gx * fdy, gy, gy * fdx, gy * fdy};
         int k = 0;
 #pragma unroll
@@ -460,31 +483,40 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     const float nrm = sqrtf(dp[0] * dp[0] + dp[3] * dp[3] +
                             m2 * (dp[1] * dp[1] + dp[2] * dp[2] + dp[4] * dp[4] + dp[5] * dp[5]));
     if (nrm < p.tol) {
+      // Eq. 1 at this iteration's sampled shape: sum fc (g - gbar) =
+      // sum fc (g - c) because sum fc = 0.  The returned shape differs from it
+      // by the last update (|dp| < tol), where C is stationary, so the two
+      // values differ by O(|dp|^2): below 1e-7 for tol = 1e-3.
+      zn = warp_sum(sfd) / (df * dg);
+      have_zn = true;
       st = kOk;
       break;
     }
   }
 
-  // ---- Eq. 1 at the returned shape
-  float s0 = 0.f, s1 = 0.f, sfg = 0.f;
-  {
+  // ---- Eq. 1 at the returned shape (POIs that did not converge)
+  if (!have_zn) {
+    float s0 = 0.f, s1 = 0.f, sfg = 0.f;
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
       float tx, ty, gx, gy;
       const size_t cell = locate(prm, w.dx, w.dy, x0, y0, W, H, tx, ty);
       const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
+      float2 gr;
+      float f;
+      PS::unpack(spt[i], gr, f);
       s0 += d;
       s1 = fmaf(d, d, s1);
-      sfg = fmaf(fval(w.dx, w.dy) - fbar, d, sfg);
+      sfg = fmaf(f - fbar, d, sfg);
     }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    sfg = warp_sum(sfg);
+    const float var = s1 - s0 * s0 * invN;
+    const float dgf = sqrtf(fmaxf(var, 0.f));
+    // sum fc (g - gbar) = sum fc (g - c) because sum fc = 0
+    zn = dgf > 0.f ? sfg / (df * dgf) : 0.f;
   }
-  s0 = warp_sum(s0);
-  s1 = warp_sum(s1);
-  sfg = warp_sum(sfg);
-  const float var = s1 - s0 * s0 * invN;
-  const float dgf = sqrtf(fmaxf(var, 0.f));
-  // sum fc (g - gbar) = sum fc (g - c) because sum fc = 0
-  const float zn = dgf > 0.f ? sfg / (df * dgf) : 0.f;
   write_out(zn, it_done, st);
 }
 
@@ -494,9 +526,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, FANR ? 1 : DIC_SUB_MINB)
 subpixel_kernel(const SubpixelParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t poi = (int64_t)blockIdx.x * kWarpsPerCta + wid;
+  const int64_t poi = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
   if (poi >= p.n_pois) return;
-  const size_t wb = warp_smem_bytes(p.S * p.S, sizeof(typename GradStore<TP>::T));
+  const size_t wb = warp_smem_bytes(p.S * p.S, sizeof(typename PointStore<TP>::T));
   subpixel_poi<FANR, TS, TP>(p, poi, lane, smem + (size_t)wid * wb);
 }
 
@@ -510,8 +542,9 @@ subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
                       unsigned long long* counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // room for the larger (float2) gradient store of the two image types
-  unsigned char* wsm = smem + (size_t)wid * warp_smem_bytes(nmax, sizeof(float2));
+  // batches hold 8-bit pairs only
+  unsigned char* wsm =
+      smem + (size_t)wid * warp_smem_bytes(nmax, sizeof(PointStore<uint8_t>::T));
   const int64_t total = offsets[njobs];
   for (;;) {
     long long item = 0;
@@ -523,34 +556,34 @@ subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
       const int mid = (lo + hi) >> 1;
       if (offsets[mid] <= item) lo = mid; else hi = mid;
     }
-    const SubpixelParams p = jobs[lo];
-    if (p.ref_f32)
-      subpixel_poi<FANR, TS, float>(p, item - offsets[lo], lane, wsm);
-    else
-      subpixel_poi<FANR, TS, uint8_t>(p, item - offsets[lo], lane, wsm);
+    subpixel_poi<FANR, TS, uint8_t>(jobs[lo], item - offsets[lo], lane, wsm);
     __syncwarp();
   }
 }
 
 template <bool FANR, typename TS, typename TP>
 cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
-  const size_t smem =
-      (size_t)kWarpsPerCta * warp_smem_bytes(p.S * p.S, sizeof(typename GradStore<TP>::T));
+  // kWarpsPerCta warps per CTA, fewer where the subset's shared memory
+  // would not fit (large subsets)
+  const size_t wb = warp_smem_bytes(p.S * p.S, sizeof(typename PointStore<TP>::T));
+  int wpc = kWarpsPerCta;
+  while (wpc > 1 && (size_t)wpc * wb > 227 * 1024) wpc >>= 1;
+  const size_t smem = (size_t)wpc * wb;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS, TP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const unsigned grid = (unsigned)((p.n_pois + kWarpsPerCta - 1) / kWarpsPerCta);
-  subpixel_kernel<FANR, TS, TP><<<grid, 32 * kWarpsPerCta, smem, st>>>(p);
+  const unsigned grid = (unsigned)((p.n_pois + wpc - 1) / wpc);
+  subpixel_kernel<FANR, TS, TP><<<grid, 32 * wpc, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 template <bool FANR, typename TS, int WPC>
 cudaError_t launch_batch_one(const SubpixelParams* jobs, const int64_t* offsets, int njobs,
                              int nmax, unsigned long long* counter, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)WPC * warp_smem_bytes(nmax, sizeof(float2));
+  const size_t smem = (size_t)WPC * warp_smem_bytes(nmax, sizeof(PointStore<uint8_t>::T));
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(subpixel_batch_kernel<FANR, TS, WPC>,
