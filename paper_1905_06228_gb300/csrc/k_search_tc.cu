@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
 // full[ty]); thread 32 issues the MMAs of row ty once full[ty] completes and
 // commits them to empty[ty], which lets the producer refill that stage.  The
 // other threads wait at the block barrier before the epilogue.
-constexpr int kMaxStages = 6;
+constexpr int kMaxStages = 12;
 constexpr int kWaitLimit = 1 << 17;  // try_wait calls before giving up (~1.3 s)
 
 struct TileLayout {
@@ -565,10 +565,10 @@ __global__ void __launch_bounds__(kThreads, 3)
     // ty % NST with one TMA: the ncols_max x nrows_max patch of the bank
     // lands as operand rows n = bi * ncols_max + bj of TWK taps (swizzled)
     const uint32_t bbase = smem_u32(bbuf);
+    int st = 0;
+    uint32_t eparity = 0;  // parity of the empty phase awaited on this lap
     for (int ty = 0; ty < S; ++ty, ++issued) {
-      const int st = ty % NST;
-      if (ty >= NST &&
-          !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((ty / NST) - 1) & 1), kWaitLimit)) {
+      if (ty >= NST && !mbar_wait(smem_u32(&empty[st]), eparity, kWaitLimit)) {
         failed = 1;
         break;
       }
@@ -576,33 +576,38 @@ __global__ void __launch_bounds__(kThreads, 3)
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                    "r"(row_bytes)
                    : "memory");
-      const uint32_t stage = bbase + (uint32_t)(st * L.stageB);
       asm volatile(
           "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-          "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(stage),
+          "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(bbase + (uint32_t)(st * L.stageB)),
           "l"(&tmB), "r"(0), "r"(kc0), "r"(kr0), "r"(ty), "r"(fb)
           : "memory");
+      if (++st == NST) {
+        st = 0;
+        if (ty >= NST) eparity ^= 1u;  // the first lap waits on nothing
+      }
     }
   } else if (tid == 32) {
-    // ---- MMA issuer
+    // ---- MMA issuer.  Descriptors are built once and advanced by adding
+    // (byte offset >> 4) to their start-address field; stage, phase and
+    // accumulator indices advance incrementally (no divisions in the loop).
     const uint32_t idesc = make_idesc(128, NP);
-    const uint32_t bbase = smem_u32(bbuf);
+    const uint64_t ad0 = make_desc(smem_u32(abuf), L.RB);
+    const uint64_t bd0 = make_desc(smem_u32(bbuf), L.RB);
+    const uint32_t a_step = (uint32_t)L.grp >> 4, b_step = (uint32_t)L.stageB >> 4;
     if (!mbar_wait(smem_u32(abar), 0, kWaitLimit)) failed = 1;
+    int st = 0, rin = 0;
+    uint32_t fparity = 0, dcol = tmem;
+    uint64_t ad_row = ad0, bd_st = bd0;
     for (int ty = 0; ty < S && !failed; ++ty) {
-      const int st = ty % NST;
-      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((ty / NST) & 1), kWaitLimit)) {
+      if (!mbar_wait(smem_u32(&full[st]), fparity, kWaitLimit)) {
         failed = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int acc = ty / rows_per_acc;
-      const uint32_t dcol = tmem + (uint32_t)(acc * NP);
-      const uint32_t a_base = smem_u32(abuf) + (uint32_t)(ty * L.grp);
-      const uint32_t b_base = bbase + (uint32_t)(st * L.stageB);
+#pragma unroll 4
       for (int j = 0; j < TWK / 16; ++j) {  // 16 taps (32 bytes) per MMA
-        const uint64_t ad = make_desc(a_base + j * 32, L.RB);
-        const uint64_t bd = make_desc(b_base + j * 32, L.RB);
-        const uint32_t accum = (ty % rows_per_acc == 0 && j == 0) ? 0u : 1u;
+        const uint64_t ad = ad_row + (uint64_t)(2 * j), bd = bd_st + (uint64_t)(2 * j);
+        const uint32_t accum = (rin == 0 && j == 0) ? 0u : 1u;
         asm volatile(
             "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(dcol),
@@ -613,6 +618,18 @@ __global__ void __launch_bounds__(kThreads, 3)
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&empty[st]))
           : "memory");
+      ad_row += a_step;
+      if (++st == NST) {
+        st = 0;
+        fparity ^= 1u;
+        bd_st = bd0;
+      } else {
+        bd_st += b_step;
+      }
+      if (++rin == rows_per_acc) {
+        rin = 0;
+        dcol += (uint32_t)NP;
+      }
     }
     // every MMA issued so far (all of them, or those before a failure)
     asm volatile(
