@@ -506,22 +506,9 @@ def run_batch_workload(args):
         print(json.dumps(line))
         dic.dic_destroy(h)
         return
-    try:
-        dic.dic_set_pairs(h, tens)
-    except dic.DICError:
-        # pairs whose search window exceeds shared memory are left out (named)
-        keep = []
-        for k, t in enumerate(tens):
-            hh = dic.dic_create(21, 5, 10)
-            try:
-                dic.dic_set_pairs(hh, [t])
-                keep.append(t)
-            except dic.DICError:
-                skipped.append(k)
-            finally:
-                dic.dic_destroy(hh)
-        tens = keep
-        dic.dic_set_pairs(h, tens)
+    form = 1 if args.form == "tc" else 0
+    dic.dic_set_form(h, form)
+    dic.dic_set_pairs(h, tens)
     total, offs = dic.dic_batch_pois(h, len(tens))
     out = dic.batch_outputs(total, dev)
     with torch.cuda.stream(stream):
@@ -547,6 +534,7 @@ def run_batch_workload(args):
     for (f8, g8, s_, st_, r_) in tens:
         hh = dic.dic_create(s_, st_, r_, 1, TOL, MAX_ITER)
         dic.dic_set_solve_precision(hh, args.solve_bits)
+        dic.dic_set_form(hh, form)
         dic.dic_set_stream(hh, stream)
         singles.append(hh)
     n_each = []
@@ -575,17 +563,61 @@ def run_batch_workload(args):
     ms_single = a.elapsed_time(e) / max(1, args.steps // 2)
     for hh in singles:
         dic.dic_destroy(hh)
+    # the plain form of the same batch: FP32 integer search (persistent
+    # kernels per template width); pairs whose FP32 window does not fit
+    # shared memory are left out of this comparison and named
+    plain = None
+    if form == 1:
+        keep = list(range(len(tens)))
+        hp = None
+        while keep:
+            hp = dic.dic_create(21, 5, 10, 1, TOL, MAX_ITER)
+            dic.dic_set_solve_precision(hp, args.solve_bits)
+            dic.dic_set_stream(hp, stream)
+            dic.dic_set_pairs(hp, [tens[k] for k in keep])
+            tp, _ = dic.dic_batch_pois(hp, len(keep))
+            op = dic.batch_outputs(tp, dev)
+            try:
+                with torch.cuda.stream(stream):
+                    dic.dic_run_batch(hp, dic.DIC_ICGN, op)
+                break
+            except dic.DICError:
+                msg = dic.dic_last_error(hp)
+                dic.dic_destroy(hp)
+                hp = None
+                bad = int(msg.split("pair ")[1].split(":")[0])
+                skipped.append(keep.pop(bad))
+        if hp is not None:
+            torch.cuda.synchronize(dev)
+            n_plain = max(1, args.steps // 20)
+            with torch.cuda.stream(stream):
+                a, e = ev(), ev()
+                a.record(stream)
+                for _ in range(n_plain):
+                    dic.dic_run_batch(hp, dic.DIC_ICGN, op)
+                e.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_plain = a.elapsed_time(e) / n_plain
+            conv_plain = int((op["status"] == 0).sum())
+            plain = {"search": "fp32-exact", "pairs": len(keep), "pairs_left_out": skipped,
+                     "ms_per_step": ms_plain, "value": conv_plain / (ms_plain / 1e3)}
+            dic.dic_destroy(hp)
     line = {"metric": METRIC, "value": conv / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16+f32" if form == 1 else "f32",
             "data": "synthetic (seeded speckle renders)",
-            "config": {"workload": args.workload, "pairs": len(tens), "pairs_left_out": skipped,
-                       "pois": int(total), "form": "one CUDA graph, persistent kernels",
+            "config": {"workload": args.workload, "pairs": len(tens), "pois": int(total),
+                       "form": ("one CUDA graph: tensor-core search pair by pair, one "
+                                "persistent sub-pixel kernel" if form == 1 else
+                                "one CUDA graph: persistent FP32 search per template width, "
+                                "one persistent sub-pixel kernel"),
                        "autotuned": {"warps_per_cta": chosen[0], "grid_mult": chosen[1]},
                        "l2": "inputs and tables larger than L2"},
             "pairs_per_s": len(tens) / (ms / 1e3),
             "per_pair_launches": {"ms_per_step": ms_single,
                                   "value": conv / (ms_single / 1e3)},
+            "plain_fp32_batch": plain,
             "converged_fraction": conv / max(1, int(total)), "clocks": clocks}
     print(json.dumps(line))
     dic.dic_destroy(h)

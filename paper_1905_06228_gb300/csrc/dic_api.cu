@@ -150,6 +150,10 @@ void free_batch(dic::BatchState* b) {
   if (b->d_pjobs) cudaFree(b->d_pjobs);
   if (b->d_offsets) cudaFree(b->d_offsets);
   if (b->d_counters) cudaFree(b->d_counters);
+  if (b->tc_phase) cudaFree(b->tc_phase);
+  if (b->tc_fbox) cudaFree(b->tc_fbox);
+  if (b->tc_posbox) cudaFree(b->tc_posbox);
+  if (b->tc_slots) cudaFree(b->tc_slots);
   for (auto& c : b->classes) {
     if (c.d_jobs) cudaFree(c.d_jobs);
     if (c.d_offsets) cudaFree(c.d_offsets);
@@ -357,8 +361,8 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
                                  &t) ||
         dic::search_tc_smem(t) > 227 * 1024)
       return fail(h, DIC_ERR_UNSUPPORTED,
-                  "tensor-core search: POI block of a tile exceeds 256 (grid step too small "
-                  "for this radius) or shared memory");
+                  "tensor-core search: one row of a tile's POI block exceeds N = 256 (grid "
+                  "step too small for this radius), or the geometry exceeds shared memory");
     const size_t phase = dic::search_tc_phase_elems(t);
     const size_t slots = (size_t)h->g.n_pois * t.nslots;
     if (phase > h->tc_phase_elems || (size_t)h->g.n_pois > h->tc_pois ||
@@ -565,10 +569,74 @@ dic_status write_jobs(dic_t h, const dic_batch_out& o, int solve_bits) {
   return DIC_OK;
 }
 
+// Scratch of the tensor-core search for the largest pair of the batch
+// (allocated once; the pairs' searches run one after another and share it).
+dic_status batch_tc_scratch(dic_t h) {
+  dic::BatchState* b = h->batch;
+  if (b->tc_phase) return DIC_OK;
+  size_t phase = 0, pbe = 0, slots = 0;
+  for (const dic::BatchPair& bp : b->pairs) {
+    if (!bp.tc_ok) continue;  // no POI (checked by build_graph)
+    phase = std::max(phase, dic::search_tc_phase_elems(bp.tc));
+    pbe = std::max(pbe, dic::search_tc_posbox_elems(bp.tc));
+    slots = std::max(slots, (size_t)bp.n * bp.tc.nslots);
+  }
+  if (cudaMalloc(&b->tc_phase, phase * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMalloc(&b->tc_fbox, pbe * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&b->tc_posbox, pbe * sizeof(int2)) != cudaSuccess ||
+      cudaMalloc(&b->tc_slots, std::max<size_t>(slots, 1) * sizeof(dic::SlotCand)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, DIC_ERR_OOM, "cannot allocate tensor-core search scratch for the batch");
+  }
+  return DIC_OK;
+}
+
 dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
   dic::BatchState* b = h->batch;
+  const bool tc = h->form == DIC_FORM_BF16TC;
+  for (size_t k = 0; k < b->pairs.size(); ++k) {
+    const dic::BatchPair& bp = b->pairs[k];
+    if (bp.n > 0 && !(tc ? bp.tc_ok : bp.fp32_ok))
+      return fail(h, DIC_ERR_UNSUPPORTED,
+                  "pair %zu: subset %d, step %d, radius %d not supported by the %s search", k,
+                  bp.S, bp.step, bp.R, tc ? "tensor-core" : "FP32");
+  }
   dic_status st = write_jobs(h, o, h->solve_bits);
   if (st != DIC_OK) return st;
+  if (tc && (st = batch_tc_scratch(h)) != DIC_OK) return st;
+  // per-pair tensor-core search parameters and tensor maps (by value in the
+  // graph's kernel nodes)
+  std::vector<dic::SearchTcParams> tcp;
+  std::vector<CUtensorMap> tma, tmb;
+  if (tc) {
+    tcp.resize(b->pairs.size());
+    tma.resize(b->pairs.size());
+    tmb.resize(b->pairs.size());
+    for (size_t k = 0; k < b->pairs.size(); ++k) {
+      const dic::BatchPair& bp = b->pairs[k];
+      dic::SearchTcParams& t = tcp[k];
+      t = bp.tc;
+      t.ref = bp.d.ref_dev;
+      t.def = bp.d.def_dev;
+      t.W = bp.d.width;
+      t.H = bp.d.height;
+      t.pitch = bp.d.pitch_bytes;
+      t.n_pois = bp.n;
+      t.gph = b->tc_phase;
+      t.bank = b->tc_phase + dic::search_tc_gph_elems(t);
+      t.fbox = b->tc_fbox;
+      t.posbox = b->tc_posbox;
+      t.slots = b->tc_slots;
+      t.u0 = o.u0 + bp.off;
+      t.v0 = o.v0 + bp.off;
+      t.zncc0 = o.zncc0 + bp.off;
+      t.status = o.status0 + bp.off;
+      t.err_flag = h->err_flag;
+      if (bp.n > 0 && !encode_tc(&tma[k], &tmb[k], t))
+        return fail(h, DIC_ERR_UNSUPPORTED, "pair %zu: tensor map encoding failed", k);
+    }
+  }
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
@@ -587,7 +655,12 @@ dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
                                 bp.d.pitch_bytes, b->grad + bp.px_off, b->gimg + bp.px_off,
                                 cs);
   }
-  for (size_t c = 0; c < b->classes.size() && le == cudaSuccess; ++c) {
+  // integer search: the tensor-core form pair by pair (each launch fills
+  // the GPU: tens of thousands of tile CTAs per 2048^2 pair), or one
+  // persistent FP32 kernel per template-width class over a work counter
+  for (size_t k = 0; tc && k < b->pairs.size() && le == cudaSuccess; ++k)
+    if (b->pairs[k].n > 0) le = dic::launch_search_tc(tcp[k], &tma[k], &tmb[k], cs);
+  for (size_t c = 0; !tc && c < b->classes.size() && le == cudaSuccess; ++c) {
     dic::BatchClass& cl = b->classes[c];
     int occ = dic::search_batch_occupancy(cl.tw, cl.smem);
     int64_t items = 0;
@@ -619,6 +692,7 @@ dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
   b->last_wpc = b->wpc;
   b->last_mult = b->grid_mult;
   b->last_bits = h->solve_bits;
+  b->last_form = h->form;
   return DIC_OK;
 }
 
@@ -652,13 +726,18 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
       delete b;
       return fail(h, DIC_ERR_ARG, "bad descriptor for pair %d", k);
     }
-    if (dic::search_smem_bytes(bp.S, bp.R) > 227 * 1024) {
+    grid_of(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, &bp.nx, &bp.ny);
+    bp.fp32_ok = dic::search_smem_bytes(bp.S, bp.R) <= 227 * 1024;
+    bp.tc_ok = dic::search_tc_geometry(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, bp.nx,
+                                       bp.ny, &bp.tc) &&
+               dic::search_tc_smem(bp.tc) <= 227 * 1024;
+    if (!bp.fp32_ok && !bp.tc_ok && bp.nx > 0 && bp.ny > 0) {
       delete b;
       return fail(h, DIC_ERR_UNSUPPORTED,
-                  "pair %d: search window (subset %d, radius %d) exceeds shared memory", k, bp.S,
-                  bp.R);
+                  "pair %d: search window (subset %d, step %d, radius %d) fits neither search "
+                  "form",
+                  k, bp.S, bp.step, bp.R);
     }
-    grid_of(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, &bp.nx, &bp.ny);
     bp.n = (int64_t)bp.nx * bp.ny;
     bp.off = off;
     bp.px_off = px;
@@ -667,6 +746,7 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
     px += (size_t)bp.d.width * bp.d.height;
     if (bp.S * bp.S > b->nmax) b->nmax = bp.S * bp.S;
     b->pairs.push_back(bp);
+    if (!bp.fp32_ok) continue;  // tensor-core search only
     bool placed = false;
     for (auto& c : b->classes)
       if (c.tw == bp.tw) {
@@ -741,7 +821,8 @@ dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out* out) {
       !o.vy || !o.zncc || !o.iters || !o.status)
     return fail(h, DIC_ERR_ARG, "null output array");
   if (!b->exec || !same_out(b->last_out, o) || b->last_method != (int)method ||
-      b->last_wpc != b->wpc || b->last_mult != b->grid_mult || b->last_bits != h->solve_bits) {
+      b->last_wpc != b->wpc || b->last_mult != b->grid_mult || b->last_bits != h->solve_bits ||
+      b->last_form != h->form) {
     dic_status st = build_graph(h, method, o);
     if (st != DIC_OK) return st;
   }

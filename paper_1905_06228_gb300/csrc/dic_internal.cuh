@@ -63,7 +63,8 @@ struct SearchTcParams {
   int64_t n_pois;
   int twk;           // template row width padded to 16 taps
   int npad;          // N of the MMA (POIs per tile block, padded to 16)
-  int ncols_max, nrows_max;  // POI block of a tile (columns, rows)
+  int ncols_max, nrows_max;  // POI block of a tile's CTA (columns, rows of one chunk)
+  int nchunk;                // CTAs per tile, each taking nrows_max rows of POIs
   int arows;                 // image rows of a tile's A buffer
   int rows_per_acc;  // template rows per exact FP32 accumulator
   int tmem_cols;
@@ -169,6 +170,9 @@ struct BatchPair {
   int S, M, R, step, nx, ny, tw;
   int64_t n, off;
   size_t px_off;
+  bool fp32_ok = false;     // the FP32 search window fits shared memory
+  bool tc_ok = false;       // the tensor-core search geometry exists
+  SearchTcParams tc{};      // its geometry (scratch pointers filled per graph)
 };
 struct BatchClass {  // pairs sharing the search template width
   int tw;
@@ -191,7 +195,13 @@ struct BatchState {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   dic_batch_out last_out{};
-  int last_method = -1, last_wpc = 0, last_mult = 0, last_bits = 0;
+  int last_method = -1, last_wpc = 0, last_mult = 0, last_bits = 0, last_form = -1;
+  // tensor-core search scratch, shared by the pairs' searches (they run one
+  // after another on the graph's stream), sized for the largest pair
+  uint16_t* tc_phase = nullptr;
+  int2* tc_fbox = nullptr;
+  int2* tc_posbox = nullptr;
+  SlotCand* tc_slots = nullptr;
   int wpc = 4, grid_mult = 1;
 };
 }  // namespace dic

@@ -48,6 +48,7 @@ namespace dic {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kMaxSlots = 1024;  // tiles met by one POI window (10-bit index)
 constexpr int kTileQ = 16;  // position rows per tile
 constexpr int kTileR = 8;   // position columns per tile
 
@@ -487,11 +488,16 @@ __global__ void __launch_bounds__(kThreads, 3)
   // POI column k is met iff x_k - M - R <= X0 + 7 and x_k - M + R >= X0
   auto ceil_div = [](int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); };
   auto floor_div = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+  // blockIdx.y selects a chunk of nrows_max POI rows of the block (several
+  // chunks when the whole block would exceed N = 256 or the TMEM columns)
   const int kc0 = max(0, ceil_div(X0 + M - R - B, p.step));
-  const int kr0 = max(0, ceil_div(Y0 + M - R - B, p.step));
+  const int kr0 = max(0, ceil_div(Y0 + M - R - B, p.step)) + (int)blockIdx.y * p.nrows_max;
   const int kc1 = min(p.nx - 1, floor_div(X0 + kTileR - 1 + M + R - B, p.step));
   const int kr1 = min(p.ny - 1, floor_div(Y0 + kTileQ - 1 + M + R - B, p.step));
   const int nbr = kr1 - kr0 + 1, nbc = kc1 - kc0 + 1;
+  // a chunk past the block's last row, or a tile in a gap between windows
+  // (grid step > 2R + 8): no POI, nothing to compute (uniform over the CTA)
+  if (nbr <= 0 || nbc <= 0) return;
   const long long N = (long long)S * S;
   const int nblock = p.ncols_max * p.nrows_max;  // POIs (operand rows) loaded per row
   const uint32_t row_bytes = (uint32_t)(nblock * L.RB);
@@ -761,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 // ------------------------------------------------------------ final reduce
 // One warp per POI.  Each slot holds the exact winner of one tile (or no
 // candidate).  Lanes score their slots in float from the exact sums (error
-// below 1e-6 plus 2^-15 from the slot index packed into the key) and the
+// below 1e-6 plus 2^-13 from the slot index packed into the key) and the
 // warp keeps the best two; if the best is positive above 1e-8 and clears the
 // second by 1e-3 it is the POI's winner, otherwise the slots within 2e-3
 // (+1e-8) of the best are compared exactly, lowest linear index on ties.
@@ -795,7 +801,8 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   int mx = INT_MIN, sc = INT_MIN;
   for (int s = lane; s < p.nslots; s += 32) {
     const SlotCand c = sl[s];
-    if (valid(c.l)) merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~255) | s, INT_MIN);
+    if (valid(c.l))
+      merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~(kMaxSlots - 1)) | s, INT_MIN);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -807,7 +814,7 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   if (mx != INT_MIN) {
     const float fm = key2f(mx);
     if (fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm)) {
-      const SlotCand w = sl[mx & 255];
+      const SlotCand w = sl[mx & (kMaxSlots - 1)];
       best = Cand{w.num, w.dg, w.l};
     } else {
       const float thr = fm - 2e-3f * fabsf(fm) - 1e-8f;
@@ -857,13 +864,23 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->ny = ny;
   if (S > 64) return false;
   g->twk = S <= 16 ? 16 : S <= 32 ? 32 : 64;  // one swizzle width per operand row
-  g->ncols_max = (2 * R + kTileR - 1) / step + 1;
-  g->nrows_max = (2 * R + kTileQ - 1) / step + 1;
-  g->npad = (g->ncols_max * g->nrows_max + 15) / 16 * 16;
-  if (g->npad > 256 || nx == 0 || ny == 0) return false;
+  if (nx == 0 || ny == 0) return false;
   g->rows_per_acc = 1024 / g->twk;
   if (g->rows_per_acc > S) g->rows_per_acc = S;
   const int nacc = (S + g->rows_per_acc - 1) / g->rows_per_acc;
+  // POI block of a tile: ncols x nrows_all POIs.  One CTA takes nrows_max
+  // rows of it (a chunk), as many as keep the MMA's N <= 256 and the nacc
+  // accumulators within 512 TMEM columns; chunks are balanced.
+  g->ncols_max = (2 * R + kTileR - 1) / step + 1;
+  const int nrows_all = (2 * R + kTileQ - 1) / step + 1;
+  auto npad_of = [&](int r) { return (g->ncols_max * r + 15) / 16 * 16; };
+  int rmax = 0;
+  for (int r = 1; r <= nrows_all; ++r)
+    if (npad_of(r) <= 256 && nacc * npad_of(r) <= 512) rmax = r;
+  if (rmax == 0) return false;  // one row of POIs already exceeds N = 256
+  g->nchunk = (nrows_all + rmax - 1) / rmax;
+  g->nrows_max = (nrows_all + g->nchunk - 1) / g->nchunk;
+  g->npad = npad_of(g->nrows_max);
   int cols = 32;
   while (cols < nacc * g->npad) cols *= 2;
   if (cols > 512) return false;
@@ -890,7 +907,7 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->slots_x = (2 * R + kTileR - 1) / kTileR + 1;
   g->slots_y = (2 * R + kTileQ - 1) / kTileQ + 1;
   g->nslots = g->slots_x * g->slots_y;
-  if (g->nslots > 256) return false;  // slot index packed in 8 bits by the reduce
+  if (g->nslots > kMaxSlots) return false;  // slot index packed in 10 bits by the reduce
   // template bank offsets are 32-bit element counts
   if ((double)nx * ny * S * g->twk >= 4294967296.0) return false;
   // phase images cover every A row / column a tile touches and every
@@ -938,11 +955,10 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   if (e != cudaSuccess) return e;
   {
     const size_t bsm = boxmap_smem(p.S);
-    if (bsm > 48 * 1024) {
-      e = cudaFuncSetAttribute(boxmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)bsm);
-      if (e != cudaSuccess) return e;
-    }
+    if (bsm > 227 * 1024) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(boxmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+    if (e != cudaSuccess) return e;
     dim3 grid((p.ntx * 8 + kBoxX - 1) / kBoxX, (p.nty * 16 + kBoxY - 1) / kBoxY, 2);
     boxmap_kernel<<<grid, 256, bsm, st>>>(p);
     e = cudaGetLastError();
@@ -950,9 +966,12 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   }
   const size_t smem = search_tc_smem(p);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the limit, not this launch's size: a graph may hold launches of several
+  // geometries, each checked against the attribute when the graph runs
+  e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
-  tile_kernel<<<(unsigned)(p.ntx * p.nty), kThreads, smem, st>>>(p, *tmA, *tmB);
+  tile_kernel<<<dim3((unsigned)(p.ntx * p.nty), (unsigned)p.nchunk), kThreads, smem, st>>>(
+      p, *tmA, *tmB);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_kernel<<<wblocks, 256, 0, st>>>(p);

@@ -24,8 +24,9 @@ def _built():
     __graft_entry__.build()
 
 
-def _run_batch(pairs, method=0, solve_bits=32, autotune=False, repeat=1):
-    """pairs: list of (f, g, subset, step, radius) numpy uint8 pairs."""
+def _run_batch(pairs, method=0, solve_bits=32, autotune=False, repeat=1, form=0):
+    """pairs: list of (f, g, subset, step, radius) numpy uint8 pairs; form 1
+    runs the tensor-core integer search."""
     import torch
 
     import paper_1905_06228_gb300 as dic
@@ -37,6 +38,8 @@ def _run_batch(pairs, method=0, solve_bits=32, autotune=False, repeat=1):
     try:
         if solve_bits != 32:
             dic.dic_set_solve_precision(h, solve_bits)
+        if form:
+            dic.dic_set_form(h, form)
         dic.dic_set_pairs(h, tens)
         total, offs = dic.dic_batch_pois(h, len(pairs))
         out = dic.batch_outputs(total, dev)
@@ -141,6 +144,41 @@ def test_sine2048_pairs():
         assert (b["status"] == 0).mean() > 0.95
 
 
+def test_batch_tensor_core_search_equals_fp32_batch():
+    """The batch graph with the tensor-core search (one search per pair, shared
+    scratch) gives bitwise the results of the FP32 batch form: same exact
+    integer winners, hence the same sub-pixel starts and iterates."""
+    pairs = _mixed_small_pairs()
+    a, offs_a, _ = _run_batch(pairs, method=0)
+    b, offs_b, _ = _run_batch(pairs, method=0, form=1, repeat=2)
+    np.testing.assert_array_equal(offs_a, offs_b)
+    for key in KEYS:
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+def test_mixed32_large_window_pairs_tensor_core():
+    """The 4096x4096 pairs of the mixed-size batch with the largest search
+    windows (radius 85 with subset 41; radius 63 with subset 31; radius 43
+    with subset 15 and 638401 POIs), which the FP32 form's shared-memory
+    window cannot hold or holds only in part, in one tensor-core batch,
+    sampled against the oracle."""
+    pairs = []
+    for k in (25, 28, 29):
+        p = configs.mixed(k)
+        pairs.append((p.ref, p.defm, p.subset, p.step, p.radius))
+    res, offs, _ = _run_batch(pairs, method=0, solve_bits=32, form=1)
+    rng = np.random.default_rng(5)
+    for k, (f, g, s, st, r) in enumerate(pairs):
+        b = _slice(res, offs, k)
+        n = offs[k + 1] - offs[k]
+        idx = np.sort(rng.choice(n, 24, replace=False))
+        ref = oracle.integer_search(f, g, s, st, r, poi_idx=idx)
+        compare_search(b, ref, idx)
+        b["p"] = np.stack([b[n_] for n_ in ("u", "ux", "uy", "v", "vx", "vy")], 1).astype(
+            np.float64)
+        compare_subpixel(b, f, g, s, st, r, ref, 0, idx=idx, min_iter_agreement=0.8)
+
+
 def test_set_pairs_rejects_oversized_window():
     import torch
 
@@ -148,9 +186,34 @@ def test_set_pairs_rejects_oversized_window():
     img = torch.zeros((600, 600), dtype=torch.uint8, device="cuda:0")
     h = dic.dic_create(21, 5, 10)
     try:
+        # step 1, radius 120: neither the FP32 window nor one row of the
+        # tensor-core POI block (4 accumulators x 256 POIs) fits
         with pytest.raises(dic.DICError) as e:
-            dic.dic_set_pairs(h, [(img, img, 51, 10, 120)])
+            dic.dic_set_pairs(h, [(img, img, 51, 1, 120)])
         assert e.value.code == dic.DIC_ERR_UNSUPPORTED
         assert "pair 0" in dic.dic_last_error(h)
+    finally:
+        dic.dic_destroy(h)
+
+
+def test_fp32_batch_rejects_tensor_core_only_pair():
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    f, g = configs.tiny(77, 600, 600, 12000)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    h = dic.dic_create(21, 5, 10)
+    try:
+        dic.dic_set_pairs(h, [(tf, tg, 21, 7, 10), (tf, tg, 51, 10, 120)])
+        total, _ = dic.dic_batch_pois(h, 2)
+        out = dic.batch_outputs(total, torch.device("cuda:0"))
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_run_batch(h, 0, out)
+        assert e.value.code == dic.DIC_ERR_UNSUPPORTED
+        assert "pair 1" in dic.dic_last_error(h)
+        dic.dic_set_form(h, 1)
+        dic.dic_run_batch(h, 0, out)
+        torch.cuda.synchronize()
+        assert (out["status0"][:total].cpu().numpy() <= 6).all()
     finally:
         dic.dic_destroy(h)

@@ -83,12 +83,38 @@ def test_ties_flat_and_planted():
     assert (b["u0"] == 7).all() and (b["v0"] == -5).all()
 
 
+@pytest.mark.parametrize("subset,step,radius,size", [
+    (9, 2, 20, 120),     # 24 x 28 POIs meet a tile: 3 chunks of 10 rows (N = 240 -> 256)
+    (15, 3, 30, 200),    # 23 x 26 POIs: 3 chunks
+])
+def test_chunked_poi_blocks(subset, step, radius, size):
+    """A tile's POI block larger than one MMA's N = 256 is split into row
+    chunks, one CTA each; every chunk's POIs get their slots."""
+    f, g = configs.tiny(3000 + subset, size, size, int(0.03 * size * size),
+                        Affine(0.004, -0.003, 0.6, 2.2, -1.4, size / 2, size / 2), noise=1.5)
+    b = _both(f, g, subset, step, radius)
+    compare_search(b, oracle.integer_search(f, g, subset, step, radius))
+
+
+def test_large_radius_many_slots():
+    """Subset 41, step 13, radius 85 (the largest window of the mixed-size
+    batch): 276 tiles per POI window (slot index beyond 8 bits), three
+    accumulators x 112 POIs = 512 TMEM columns, two chunks.  The FP32 form's
+    window does not fit shared memory, so the oracle is the only reference."""
+    size = 256
+    f, g = configs.tiny(3100, size, size, int(0.035 * size * size),
+                        Affine(0.01, -0.008, 1.5, 31.0, -57.0, size / 2, size / 2), noise=1.0)
+    b = run_gpu(f, g, 41, 13, 85, subpixel=False, form=TC)
+    assert b["n"] == 16
+    compare_search(b, oracle.integer_search(f, g, 41, 13, 85))
+
+
 def test_unsupported_geometry_is_reported():
     import torch
 
     import paper_1905_06228_gb300 as dic
-    f, g = configs.tiny(8, 120, 120, 300)
-    h = dic.dic_create(9, 1, 10)   # step 1: 35 x 27 POIs would meet one tile
+    f, g = configs.tiny(8, 300, 300, 2000)
+    h = dic.dic_create(9, 1, 125)   # step 1: 257 POI columns meet one tile (N > 256)
     try:
         dic.dic_set_form(h, TC)
         tf = torch.from_numpy(f).cuda()
