@@ -41,9 +41,9 @@ FP32_LANES_PER_SM = 128
 # right-hand-side sums 16, the cross sum of Eq. 1 3.
 FLOP_PER_SAMPLE = 96
 # kernels launched per step: precompute, then the integer search (phase
-# images, template bank, two box-sum maps, tile, reduce; or one FP32 search
-# kernel), then the sub-pixel kernel
-LAUNCHES_TC = 1 + 6 + 1
+# images, template bank, box-sum maps of f and g in one launch, tile,
+# reduce; or one FP32 search kernel), then the sub-pixel kernel
+LAUNCHES_TC = 1 + 5 + 1
 LAUNCHES_PLAIN = 1 + 1 + 1
 
 
@@ -65,14 +65,15 @@ def traffic_of(name: str):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--solve-bits", type=int, default=32)
+    ap.add_argument("--solve-bits", type=int, default=64,
+                    help="6x6 solve precision of the chosen form (the precision form: FP64)")
     ap.add_argument("--form", default="tc", choices=["tc", "fp32"],
                     help="integer-search form of the chosen configuration")
-    ap.add_argument("--cpu-sample", type=int, default=8192,
-                    help="POIs in the oracle's CPU sample")
+    ap.add_argument("--cpu-sample", type=int, default=36100,
+                    help="POIs in the oracle's CPU sample (default: the whole pair)")
     ap.add_argument("--workload", default="affine1024",
                     choices=["affine1024", "sine2048x64", "mixed32", "affine1024x8"],
                     help="affine1024 is the headline; the others measure the batched form "
@@ -261,6 +262,14 @@ def run_gpu(args):
     plain_value = conv32 * len(st32) / (sum(st32) / 1e3)
     plain_search_ms = statistics.mean(se32[0])
     d32.close()
+    # the chosen search with the other 6x6 solve precision
+    other_bits = 32 if args.solve_bits == 64 else 64
+    dob = make(other_bits, args.form)
+    dob.set_pair(ref_d, def_d)
+    sto, seo, convo, _, _ = timed_loop(dob, max(10, args.steps // 4), 3)
+    other_value = convo * len(sto) / (sum(sto) / 1e3)
+    other_sub_ms = statistics.mean(seo[1])
+    dob.close()
 
     # e2e through the public call with host buffers: H2D of both images,
     # the three kernels, D2H of every per-POI output, all inside the events
@@ -359,6 +368,10 @@ def run_gpu(args):
                 "forms": {"chosen": {"search": "bf16-tensor-core-exact" if args.form == "tc"
                                      else "fp32-exact", "solve": f"fp{args.solve_bits}",
                                      "value": value},
+                          "chosen_fp%d_solve" % other_bits: {
+                              "search": "bf16-tensor-core-exact" if args.form == "tc"
+                              else "fp32-exact", "solve": f"fp{other_bits}",
+                              "value": other_value, "subpixel_ms": other_sub_ms},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
                                          "value": plain_value}},
                 "converged_fraction": conv / n, "wall_s_timed": wall}

@@ -235,7 +235,7 @@ dic_status dic_backward(dic_t h, const float *p6, const float *grad_loss, float 
  *
  * Same arithmetic as dic_set_pair (precompute) followed by dic_subpixel, but
  * without a handle: the float deformed image and the gradient field go to one
- * fixed array inside the library (a static device symbol of 768 KiB, held by
+ * fixed array inside the library (a static device symbol of 1.25 MiB, held by
  * every GPU that loads the library until the process exits).
  *   - width * height must be <= 65536 pixels (e.g. 256 x 256); larger
  *     images, and every other invalid argument, return DIC_ERR_ARG before any

@@ -147,6 +147,7 @@ void free_batch(dic::BatchState* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->gimg) cudaFree(b->gimg);
   if (b->grad) cudaFree(b->grad);
+  if (b->gq) cudaFree(b->gq);
   if (b->d_pjobs) cudaFree(b->d_pjobs);
   if (b->d_offsets) cudaFree(b->d_offsets);
   if (b->d_counters) cudaFree(b->d_counters);
@@ -171,6 +172,7 @@ void dic_destroy(dic_t h) {
   free_batch(h->batch);
   if (h->gimg) cudaFree(h->gimg);
   if (h->grad) cudaFree(h->grad);
+  if (h->gq) cudaFree(h->gq);
   if (h->err_flag) cudaFree(h->err_flag);
   if (h->tc_phase) cudaFree(h->tc_phase);
   if (h->tc_fbox) cudaFree(h->tc_fbox);
@@ -226,15 +228,20 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
   if (px > h->scratch_px) {
     if (h->gimg) cudaFree(h->gimg);
     if (h->grad) cudaFree(h->grad);
+    if (h->gq) cudaFree(h->gq);
     h->gimg = nullptr;
     h->grad = nullptr;
+    h->gq = nullptr;
     h->scratch_px = 0;
     if (cudaMalloc(&h->gimg, px * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&h->grad, px * sizeof(float2)) != cudaSuccess) {
+        cudaMalloc(&h->grad, px * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&h->gq, px * sizeof(uint2)) != cudaSuccess) {
       cudaGetLastError();
       if (h->gimg) cudaFree(h->gimg);
+      if (h->grad) cudaFree(h->grad);
       h->gimg = nullptr;
-      return fail(h, DIC_ERR_OOM, "cannot allocate %zu bytes of scratch", px * 12);
+      h->grad = nullptr;
+      return fail(h, DIC_ERR_OOM, "cannot allocate %zu bytes of scratch", px * 20);
     }
     h->scratch_px = px;
   }
@@ -270,7 +277,8 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
                 bwg <= 256 && span <= 256 &&
                 encode_u8(&h->tm_def, h->def, width, height, pitch, bwg, span) &&
                 encode_u8(&h->tm_ref, h->ref, width, height, pitch, bwf, h->subset);
-    e = dic::launch_precompute(h->ref, h->def, width, height, pitch, h->grad, h->gimg, h->stream);
+    e = dic::launch_precompute(h->ref, h->def, width, height, pitch, h->grad, h->gimg, h->gq,
+                               h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "precompute launch");
   h->have_pair = true;
@@ -458,6 +466,7 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int
   p.ref_f32 = h->ref_f32;
   p.grad = h->grad;
   p.gimg = h->gimg;
+  p.gq = h->ref ? h->gq : nullptr;
   p.W = h->g.W;
   p.H = h->g.H;
   p.pitch = h->g.pitch;
@@ -510,6 +519,7 @@ dic_status write_jobs(dic_t h, const dic_batch_out& o, int solve_bits) {
     p.ref = bp.d.ref_dev;
     p.grad = b->grad + bp.px_off;
     p.gimg = b->gimg + bp.px_off;
+    p.gq = b->gq + bp.px_off;
     p.W = bp.d.width;
     p.H = bp.d.height;
     p.pitch = bp.d.pitch_bytes;
@@ -653,7 +663,7 @@ dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
     if (le != cudaSuccess) break;
     le = dic::launch_precompute(bp.d.ref_dev, bp.d.def_dev, bp.d.width, bp.d.height,
                                 bp.d.pitch_bytes, b->grad + bp.px_off, b->gimg + bp.px_off,
-                                cs);
+                                b->gq + bp.px_off, cs);
   }
   // integer search: the tensor-core form pair by pair (each launch fills
   // the GPU: tens of thousands of tile CTAs per 2048^2 pair), or one
@@ -777,6 +787,7 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
   offs.push_back(off);
   cudaError_t e = cudaMalloc(&b->gimg, px * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&b->grad, px * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&b->gq, px * sizeof(uint2));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_pjobs, sizeof(dic::SubpixelParams) * n_pairs);
   if (e == cudaSuccess) e = upload(&b->d_offsets, offs);
   if (e == cudaSuccess)

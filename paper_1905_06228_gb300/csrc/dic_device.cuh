@@ -65,6 +65,120 @@ __device__ __forceinline__ float bicubic(const float* __restrict__ img, int W, s
   return fmaf(wy[3], row[3], fmaf(wy[2], row[2], fmaf(wy[1], row[1], wy[0] * row[0])));
 }
 
+// ---- packed FP32 (Blackwell f32x2: two FP32 operations per instruction).
+// Each packed operation rounds every half exactly like its scalar form, so
+// the helpers below give bitwise the results of keys_weights / bicubic /
+// locate while issuing about half the FP32 instructions.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// Keys weights of both axes at once: w[k] = (weight of tap k-1 along x at
+// t.x, the same along y at t.y); same operation order as keys_weights.
+__device__ __forceinline__ void keys_weights2(float2 t, float2 w[4]) {
+  const float2 t2 = __fmul2_rn(t, t), t3 = __fmul2_rn(t2, t);
+  w[0] = __ffma2_rn(dup2(-0.5f), t3, __ffma2_rn(dup2(-0.5f), t, t2));
+  w[1] = __ffma2_rn(dup2(1.5f), t3, __ffma2_rn(dup2(-2.5f), t2, dup2(1.f)));
+  w[2] = __ffma2_rn(dup2(-1.5f), t3, __ffma2_rn(dup2(2.f), t2, __fmul2_rn(dup2(0.5f), t)));
+  w[3] = __fmul2_rn(dup2(0.5f), __ffma2_rn(t2, dup2(-1.f), t3));  // 0.5 (t3 - t2)
+}
+
+// Bicubic value at fractional offsets t of cell (as bicubic<false>): the
+// four horizontal 4-tap sums run as two packed pairs of rows.
+__device__ __forceinline__ float bicubic2(const float* __restrict__ img, int W, size_t cell,
+                                          float2 t) {
+  float2 w[4];
+  keys_weights2(t, w);
+  const float* r = img + cell - W - 1;
+  float2 rr[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float* a = r + (size_t)(2 * h) * W;
+    const float* b = a + W;
+    float2 acc = __fmul2_rn(dup2(w[0].x), make_float2(__ldg(a), __ldg(b)));
+    acc = __ffma2_rn(dup2(w[1].x), make_float2(__ldg(a + 1), __ldg(b + 1)), acc);
+    acc = __ffma2_rn(dup2(w[2].x), make_float2(__ldg(a + 2), __ldg(b + 2)), acc);
+    rr[h] = __ffma2_rn(dup2(w[3].x), make_float2(__ldg(a + 3), __ldg(b + 3)), acc);
+  }
+  return fmaf(w[3].y, rr[1].y, fmaf(w[2].y, rr[1].x, fmaf(w[1].y, rr[0].y, w[0].y * rr[0].x)));
+}
+
+// The same value from the tap quads of an 8-bit image: gq[y*W + x] holds
+// the BF16 of g[y][x-1 .. x+2] (exact), so each stencil row is one 8-byte
+// load; a BF16 becomes its float by a shift or a mask (integer ALU, no
+// conversion).  Bitwise equal to bicubic2 on the float copy.
+__device__ __forceinline__ float bicubic_q(const uint2* __restrict__ gq, int W, size_t cell,
+                                           float2 t) {
+  float2 w[4];
+  keys_weights2(t, w);
+  const uint2* r = gq + cell - W;
+  float2 rr[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint2 qa = __ldg(r + (size_t)(2 * h) * W), qb = __ldg(r + (size_t)(2 * h + 1) * W);
+    const float2 p0 = make_float2(__uint_as_float(qa.x << 16), __uint_as_float(qb.x << 16));
+    const float2 p1 =
+        make_float2(__uint_as_float(qa.x & 0xFFFF0000u), __uint_as_float(qb.x & 0xFFFF0000u));
+    const float2 p2 = make_float2(__uint_as_float(qa.y << 16), __uint_as_float(qb.y << 16));
+    const float2 p3 =
+        make_float2(__uint_as_float(qa.y & 0xFFFF0000u), __uint_as_float(qb.y & 0xFFFF0000u));
+    float2 acc = __fmul2_rn(dup2(w[0].x), p0);
+    acc = __ffma2_rn(dup2(w[1].x), p1, acc);
+    acc = __ffma2_rn(dup2(w[2].x), p2, acc);
+    rr[h] = __ffma2_rn(dup2(w[3].x), p3, acc);
+  }
+  return fmaf(w[3].y, rr[1].y, fmaf(w[2].y, rr[1].x, fmaf(w[1].y, rr[0].y, w[0].y * rr[0].x)));
+}
+
+// The warp W(xi; p) of one shape, for packed point offsets (dx, dx), (dy, dy):
+// local position l = (u + (1+ux) dx + uy dy, v + vx dx + (1+vy) dy), with
+// the operation order of locate.  floor(l) comes from one round-down add of
+// 1.5 * 2^23 (exact for |l| < 2^22: the sum's unit is 1), whose bits minus
+// those of 1.5 * 2^23 are the integer floor, so no conversion instruction
+// is issued.
+struct WarpAffine {
+  static constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+  static constexpr int kMagicBits = 0x4B400000;
+  float2 a, b, o;
+  int xm, ym;
+  __device__ __forceinline__ WarpAffine(const float p[6], int x0, int y0)
+      : a(make_float2(1.f + p[1], p[4])),
+        b(make_float2(p[2], 1.f + p[5])),
+        o(make_float2(p[0], p[3])),
+        xm(x0 - kMagicBits),
+        ym(y0 - kMagicBits) {}
+  __device__ __forceinline__ size_t locate(float2 DX, float2 DY, int W, int H, float2& t) const {
+    const float2 l = __ffma2_rn(b, DY, __ffma2_rn(a, DX, o));
+    const float2 r = __fadd2_rd(l, dup2(kMagic));
+    const float2 fl = __fadd2_rn(r, dup2(-kMagic));
+    t = __ffma2_rn(fl, dup2(-1.f), l);  // l - floor(l), one rounding as in locate
+    int ix = __float_as_int(r.x) + xm, iy = __float_as_int(r.y) + ym;
+    ix = min(max(ix, 1), W - 3);  // memory safety only; bounds are checked on p
+    iy = min(max(iy, 1), H - 3);
+    return (size_t)iy * W + ix;
+  }
+};
+
+// Subset point walk with float offsets held as packed duplicates (dx, dx),
+// (dy, dy) (small integers, exact), for the packed warp and sums.
+struct PtWalk2 {
+  float2 DX, DY;
+  float ddx, ddy, fM, fS;
+  __device__ __forceinline__ PtWalk2(int lane, int S, int M)
+      : DX(dup2((float)(lane % S - M))),
+        DY(dup2((float)(lane / S - M))),
+        ddx((float)(32 % S)),
+        ddy((float)(32 / S)),
+        fM((float)M),
+        fS((float)S) {}
+  __device__ __forceinline__ void next() {
+    DX = __fadd2_rn(DX, dup2(ddx));
+    DY = __fadd2_rn(DY, dup2(ddy));
+    if (DX.x > fM) {
+      DX = __fadd2_rn(DX, dup2(-fS));
+      DY = __fadd2_rn(DY, dup2(1.f));
+    }
+  }
+};
+
 // Subset point walk of one lane: points i = lane, lane+32, ... in row-major
 // (dy outer) order, with (dx, dy) advanced incrementally.
 struct PtWalk {

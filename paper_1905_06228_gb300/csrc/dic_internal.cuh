@@ -91,6 +91,7 @@ struct SubpixelParams {
   const float* ref_f32 = nullptr;
   const float2* grad;  // central-difference gradients of f, W*H
   const float* gimg;   // deformed image as float, W*H
+  const uint2* gq = nullptr;  // 8-bit pairs: BF16 tap quads of g, W*H (required)
   int W, H, pitch;
   int S, M, R, step, nx;
   int64_t n_pois;
@@ -130,7 +131,7 @@ struct AdjointParams {
 
 // Launchers (each returns the cudaError_t of its launch).
 cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int H,
-                              int pitch, float2* grad, float* gimg, cudaStream_t st);
+                              int pitch, float2* grad, float* gimg, uint2* gq, cudaStream_t st);
 cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int H,
                                   int pitch, float2* grad, float* gimg, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjointParams& p, cudaStream_t st);
@@ -189,6 +190,7 @@ struct BatchState {
   size_t px_total = 0;
   float* gimg = nullptr;
   float2* grad = nullptr;
+  uint2* gq = nullptr;
   SubpixelParams* d_pjobs = nullptr;
   int64_t* d_offsets = nullptr;
   unsigned long long* d_counters = nullptr;
@@ -222,6 +224,7 @@ struct dic_s {
 
   float* gimg = nullptr;
   float2* grad = nullptr;
+  uint2* gq = nullptr;    // tap quads of an 8-bit deformed image
   size_t scratch_px = 0;  // capacity in pixels
   unsigned int* err_flag = nullptr;
 

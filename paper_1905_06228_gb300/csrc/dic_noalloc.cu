@@ -6,8 +6,9 @@
 // inside a host application whose own allocator owns the device memory
 // budget, where a stray allocation breaks its accounting.
 //
-// The regular path keeps the float deformed image and the reference
-// gradient field in scratch that dic_set_pair allocates.  Here the same two
+// The regular path keeps the float deformed image, its BF16 tap quads and
+// the reference gradient field in scratch that dic_set_pair allocates.  Here
+// the same two
 // kernels (precompute, then sub-pixel refinement) run on a fixed scratch
 // array that lives in this file as a static __device__ symbol.  Every GPU
 // that loads the library holds kNoAllocScratchBytes of it until the process
@@ -20,10 +21,12 @@ namespace {
 
 // Largest image (width * height, pixels) this entry point accepts.
 constexpr size_t kNoAllocMaxPixels = 256 * 256;
-// Float deformed image (one float per pixel) followed by the gradient
-// field (one float2 per pixel): 768 KiB.
+// Float deformed image (one float per pixel), the gradient field (one
+// float2 per pixel), then the tap quads of the deformed image (one uint2 per
+// pixel): 1.25 MiB.
 constexpr size_t kGimgBytes = kNoAllocMaxPixels * sizeof(float);
-constexpr size_t kNoAllocScratchBytes = kGimgBytes + kNoAllocMaxPixels * sizeof(float2);
+constexpr size_t kGradBytes = kNoAllocMaxPixels * sizeof(float2);
+constexpr size_t kNoAllocScratchBytes = kGimgBytes + kGradBytes + kNoAllocMaxPixels * sizeof(uint2);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -79,19 +82,21 @@ extern "C" dic_status dic_subpixel_noalloc(
   if (scratch_on_current_device(&scratch) != cudaSuccess) return DIC_ERR_CUDA;
   float* gimg = reinterpret_cast<float*>(scratch);
   float2* grad = reinterpret_cast<float2*>(scratch + kGimgBytes);
+  uint2* gq = reinterpret_cast<uint2*>(scratch + kGimgBytes + kGradBytes);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
 
-  // The precompute kernel writes every float pixel and gradient of the
-  // width x height image (zeros on the border), so nothing left over from an
-  // earlier call is ever read and no clearing is needed.
-  if (dic::launch_precompute(ref_dev, def_dev, width, height, pitch_bytes, grad, gimg, st) !=
-      cudaSuccess)
+  // The precompute kernel writes every float pixel, gradient and tap quad of
+  // the width x height image (zeros on the border), so nothing left over
+  // from an earlier call is ever read and no clearing is needed.
+  if (dic::launch_precompute(ref_dev, def_dev, width, height, pitch_bytes, grad, gimg, gq,
+                             st) != cudaSuccess)
     return DIC_ERR_CUDA;
 
   dic::SubpixelParams p;
   p.ref = ref_dev;
   p.grad = grad;
   p.gimg = gimg;
+  p.gq = gq;
   p.W = width;
   p.H = height;
   p.pitch = pitch_bytes;

@@ -11,6 +11,11 @@
 //                  consistent with the interpolation used for g.
 //  gimg[y*W + x] = g[y][x] as float (dense, unpadded), the samples the
 //                  bicubic evaluation reads.
+//  gq[y*W + x]   = (8-bit pairs, if gq is given) the four horizontal taps
+//                  g[y][x-1 .. x+2] of a bicubic stencil whose cell starts
+//                  at column x, as BF16 (exact for 8-bit values; 0 outside
+//                  the image), 8 bytes: one load per stencil row instead of
+//                  four.
 //
 // The paper keeps interpolation results in look-up tables; here the bicubic
 // weights are evaluated per sample instead (a table of 16 coefficients per
@@ -19,7 +24,8 @@
 //
 // Pixels are 8-bit or float (the float form serves differentiation with
 // respect to real-valued deformed-image pixels); pitch is in elements.
-// Bytes per pixel: 1 (f) + 1 (g) read, 8 (grad) + 4 (gimg) written.
+// Bytes per pixel: 1 (f) + 1 (g) read, 8 (grad) + 4 (gimg) (+ 8 (gq))
+// written.
 #include "dic_internal.cuh"
 
 namespace dic {
@@ -29,10 +35,16 @@ constexpr int TX = 32;  // tile width (pixels) = threads in x
 constexpr int TY = 16;  // tile height (pixels)
 constexpr int BY = 8;   // threads in y; each thread does TY/BY rows
 
+// BF16 bits of an 8-bit value (its FP32 encoding has 16 trailing zero bits).
+__device__ __forceinline__ uint32_t bf16_of_byte(uint32_t b) {
+  return __float_as_uint((float)b) >> 16;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TX* BY)
 precompute_kernel(const T* __restrict__ ref, const T* __restrict__ def, int W,
-                  int H, int pitch, float2* __restrict__ grad, float* __restrict__ gimg) {
+                  int H, int pitch, float2* __restrict__ grad, float* __restrict__ gimg,
+                  uint2* __restrict__ gq) {
   __shared__ float sf[TY + 2][TX + 3];  // f rows y0-1 .. y0+TY,   cols x0-1 .. x0+TX
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int tid = threadIdx.y * TX + threadIdx.x;
@@ -57,16 +69,26 @@ precompute_kernel(const T* __restrict__ ref, const T* __restrict__ def, int W,
     }
     grad[(size_t)y * W + x] = gr;
     gimg[(size_t)y * W + x] = (float)def[(size_t)y * pitch + x];
+    if (gq) {
+      const T* row = def + (size_t)y * pitch;
+      uint32_t h[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int xx = x - 1 + k;
+        h[k] = (xx >= 0 && xx < W) ? bf16_of_byte((uint32_t)row[xx]) : 0u;
+      }
+      gq[(size_t)y * W + x] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    }
   }
 }
 
 }  // namespace
 
 cudaError_t launch_precompute(const uint8_t* ref, const uint8_t* def, int W, int H, int pitch,
-                              float2* grad, float* gimg, cudaStream_t st) {
+                              float2* grad, float* gimg, uint2* gq, cudaStream_t st) {
   dim3 block(TX, BY);
   dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
-  precompute_kernel<uint8_t><<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, gimg);
+  precompute_kernel<uint8_t><<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, gimg, gq);
   return cudaGetLastError();
 }
 
@@ -74,7 +96,7 @@ cudaError_t launch_precompute_f32(const float* ref, const float* def, int W, int
                                   float2* grad, float* gimg, cudaStream_t st) {
   dim3 block(TX, BY);
   dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
-  precompute_kernel<float><<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, gimg);
+  precompute_kernel<float><<<grid, block, 0, st>>>(ref, def, W, H, pitch, grad, gimg, nullptr);
   return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@
 // resident CTAs per SM requested from the register allocator, and the
 // unroll of the per-point loop (memory-level parallelism of the sample loads)
 #ifndef DIC_SUB_MINB
-#define DIC_SUB_MINB 3
+#define DIC_SUB_MINB 4
 #endif
 #ifndef DIC_SUB_UNROLL
 #define DIC_SUB_UNROLL 1
@@ -45,7 +45,12 @@
 namespace dic {
 namespace {
 
-constexpr int kWarpsPerCta = 8;
+// warps per CTA: 5 x 4 CTAs = 20 warps per SM at 96 registers per thread
+// (no spills; 8 x 3 at 80 registers spilled and ran 5 % slower)
+#ifndef DIC_SUB_WPC
+#define DIC_SUB_WPC 5
+#endif
+constexpr int kWarpsPerCta = DIC_SUB_WPC;
 constexpr int kPointUnroll = DIC_SUB_UNROLL;
 
 // 1/sqrt(d): FP32 estimate refined by Newton's iteration for 1/y^2 = d,
@@ -91,6 +96,66 @@ __device__ __forceinline__ bool chol6_packed(const float Hp[21], T L[6][6], T ri
       L[i][j] = sacc * r;
     }
   }
+  return ok;
+}
+
+// 1/d: FP32 reciprocal refined by Newton's iteration y <- y + y (1 - d y)
+// in the solve precision (each step doubles the correct bits).
+template <typename T>
+__device__ __forceinline__ T rcp_refined(T d);
+template <>
+__device__ __forceinline__ float rcp_refined<float>(float d) {
+  return __frcp_rn(d);
+}
+template <>
+__device__ __forceinline__ double rcp_refined<double>(double d) {
+  double y = (double)__frcp_rn((float)d);
+  y = fma(y, fma(-d, y, 1.0), y);
+  return fma(y, fma(-d, y, 1.0), y);
+}
+
+__device__ __forceinline__ int packed_index(int r, int c) {  // entry (r, c) of a packed lower triangle
+  return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r;
+}
+
+// Inverse of a symmetric positive definite 6x6 (21 packed lower entries,
+// identical on every lane) by the symmetric sweep operator, one lane per
+// entry: lane l < 21 holds entry (i, j), i >= j, l = i (i+1)/2 + j.  Pivot
+// k (k = 0..5) replaces a_kk by -1/a_kk, every other entry of row / column
+// k by a_ik / a_kk, and the remaining entries by a_ij - a_ik a_jk / a_kk;
+// after the six pivots the entries hold -A^-1 (Gauss-Jordan elimination in
+// symmetric form; the pivots are the successive Schur complements, positive
+// for a positive definite A, so no pivoting is needed).  Each step costs a
+// few instructions for the whole warp, instead of a full factorisation
+// repeated on every lane.  Returns false on every lane if a pivot is not
+// positive and finite; lanes >= 21 return no entry.
+template <typename T>
+__device__ __forceinline__ bool sweep_inverse6(const float A[21], int lane, T& out, int& oi,
+                                               int& oj) {
+  int i = 0;
+#pragma unroll
+  for (int r = 1; r < 6; ++r) i += lane >= r * (r + 1) / 2 ? 1 : 0;
+  const int j = min(lane - i * (i + 1) / 2, i);
+  float h = A[0];
+#pragma unroll
+  for (int k = 1; k < 21; ++k) h = lane == k ? A[k] : h;
+  T a = (T)h;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const T akk = __shfl_sync(0xffffffffu, a, k * (k + 1) / 2 + k);
+    const T aik = __shfl_sync(0xffffffffu, a, packed_index(i, k));
+    const T ajk = __shfl_sync(0xffffffffu, a, packed_index(j, k));
+    ok = ok && akk > T(0) && akk < T(3e38);
+    const T d = rcp_refined<T>(ok ? akk : T(1));
+    T r = fma(-(aik * d), ajk, a);
+    if (i == k || j == k) r = a * d;
+    if (i == k && j == k) r = -d;
+    a = r;
+  }
+  out = -a;
+  oi = i;
+  oj = j;
   return ok;
 }
 
@@ -206,23 +271,26 @@ __device__ __forceinline__ const float* ref_ptr<float>(const SubpixelParams& p) 
 }
 
 // Per-point reference data kept in shared memory: the gradient of f and f.
-// 8-bit images: FP16, 8 bytes per point (central differences of 8-bit
-// pixels are multiples of 1/2 below 128 and the pixels integers below 256,
-// both exact in FP16); float images: FP32, 16 bytes per point.
+// 8-bit images: BF16, 8 bytes per point.  Central differences of 8-bit
+// pixels are k/2 with |k| <= 255 and the pixels integers below 256: at most
+// 8 significant bits, so their FP32 encodings end in 16 zero bits and the
+// upper halves (BF16) are exact; unpacking is a shift and a mask (integer
+// ALU), f is stored as its full FP32 bits.  Float images: FP32, 16 bytes.
 template <typename TP>
 struct PointStore;
 template <>
 struct PointStore<uint8_t> {
   struct alignas(8) T {
-    __half2 g;
-    __half2 f;  // (f, 0)
+    uint32_t g;  // BF16 of df/dx (low half), df/dy (high half)
+    uint32_t f;  // FP32 bits of f (low half zero)
   };
   static __device__ __forceinline__ T pack(float2 g, float f) {
-    return T{__floats2half2_rn(g.x, g.y), __floats2half2_rn(f, 0.f)};
+    return T{(__float_as_uint(g.x) >> 16) | (__float_as_uint(g.y) & 0xFFFF0000u),
+             __float_as_uint(f)};
   }
   static __device__ __forceinline__ void unpack(const T& t, float2& g, float& f) {
-    g = __half22float2(t.g);
-    f = __low2float(t.f);
+    g = make_float2(__uint_as_float(t.g << 16), __uint_as_float(t.g & 0xFFFF0000u));
+    f = __uint_as_float(t.f);
   }
 };
 template <>
@@ -260,6 +328,8 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   float* ssd = reinterpret_cast<float*>(hinv + 36);  // sum SD
   float* sbf = ssd + 6;                              // sum SD (f - fbar)
   const TP* fimg = ref_ptr<TP>(p);
+  // 8-bit pairs sample IC-GN's g from the BF16 tap quads (exact)
+  constexpr bool kQuads = sizeof(TP) == 1;
 
   const uint8_t st0 = p.st0[poi];
   float prm[6] = {(float)p.u0[poi], 0.f, 0.f, (float)p.v0[poi], 0.f, 0.f};
@@ -343,24 +413,32 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
         sbf[k] = bfv[k];
       }
     }
-    // factor H once (in the solve precision); lane k < 6 stores row k of
-    // H^-1, so each iteration's solve is six multiply-adds per lane.  H is
-    // first scaled symmetrically to a unit diagonal (Hs = D H D, D_ii =
-    // H_ii^-1/2; H^-1 = D Hs^-1 D): the translation and gradient columns
-    // differ in scale by ~M^2, which the factorisation then does not see.
+    // invert H once (in the solve precision), one lane per entry of its
+    // lower triangle; H^-1 goes to shared memory and lane k < 6 reads row k
+    // in every iteration, so an iteration's solve is six multiply-adds per
+    // lane.  H is first scaled symmetrically to a unit diagonal (Hs = D H D,
+    // D_ii = H_ii^-1/2; H^-1 = D Hs^-1 D): the translation and gradient
+    // columns differ in scale by ~M^2, which the elimination then does not
+    // see.  D_ii D_jj is rounded to FP32 before the solve-precision product
+    // (relative 6e-8: below the FP32 sums that form H).
     float dsc[6];
     unit_diagonal(Hs, Hs, dsc);
-    TS L[6][6], rinv[6];
-    if (!chol6_packed<TS>(Hs, L, rinv)) {
+    int ei, ej;
+    TS hij;
+    if (!sweep_inverse6<TS>(Hs, lane, hij, ei, ej)) {
       write_out(0.f, 0, kSingular);
       return;
     }
-    if (lane < 6) {
-      TS col[6];
-      chol6_inverse_col<TS>(L, rinv, lane, col);
+    if (lane < 21) {
+      float di = dsc[0], dj = dsc[0];
 #pragma unroll
-      for (int a = 0; a < 6; ++a)
-        hinv[lane * 6 + a] = col[a] * (TS)dsc[lane] * (TS)dsc[a];
+      for (int a = 1; a < 6; ++a) {
+        di = ei == a ? dsc[a] : di;
+        dj = ej == a ? dsc[a] : dj;
+      }
+      const TS v = hij * (TS)(di * dj);  // H^-1 = D Hs^-1 D
+      hinv[ei * 6 + ej] = v;
+      hinv[ej * 6 + ei] = v;
     }
     __syncwarp();
   }
@@ -381,13 +459,22 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     float acc[FANR ? 39 : 6];
 #pragma unroll
     for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = 0.f;
-    PtWalk w(lane, S, M);
+    // IC-GN sums in packed pairs: (SD0, SD3), (SD1, SD4), (SD2, SD5) . (g - c)
+    float2 a03 = dup2(0.f), a14 = dup2(0.f), a25 = dup2(0.f);
+    const WarpAffine wa(prm, x0, y0);
+    PtWalk2 w(lane, S, M);
 #pragma unroll kPointUnroll
     for (int i = lane; i < N; i += 32, w.next()) {
-      const int dx = w.dx, dy = w.dy;
-      float tx, ty, gx = 0.f, gy = 0.f;
-      const size_t cell = locate(prm, dx, dy, x0, y0, W, H, tx, ty);
-      const float g = bicubic<FANR>(p.gimg, W, cell, tx, ty, gx, gy);
+      float2 t;
+      float gx = 0.f, gy = 0.f;
+      const size_t cell = wa.locate(w.DX, w.DY, W, H, t);
+      float g;
+      if (FANR)
+        g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
+      else if (kQuads)
+        g = bicubic_q(p.gq, W, cell, t);
+      else
+        g = bicubic2(p.gimg, W, cell, t);
       const float d = g - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
@@ -396,16 +483,13 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       PS::unpack(spt[i], gr, f);
       const float fc = f - fbar;
       sfd = fmaf(fc, d, sfd);
-      const float fdx = (float)dx, fdy = (float)dy;
       if (!FANR) {
-        const float a = gr.x * d, b = gr.y * d;
-        acc[0] += a;
-        acc[1] = fmaf(a, fdx, acc[1]);
-        acc[2] = fmaf(a, fdy, acc[2]);
-        acc[3] += b;
-        acc[4] = fmaf(b, fdx, acc[4]);
-        acc[5] = fmaf(b, fdy, acc[5]);
+        const float2 ab = __fmul2_rn(gr, dup2(d));  // (SD0, SD3) (g - c)
+        a03 = __fadd2_rn(a03, ab);
+        a14 = __ffma2_rn(ab, w.DX, a14);
+        a25 = __ffma2_rn(ab, w.DY, a25);
       } else {
+        const float fdx = w.DX.x, fdy = w.DY.x;
         const float J[6] = {gx, gx * fdx, gx * fdy, gy, gy * fdx, gy * fdy};
         int k = 0;
 #pragma unroll
@@ -419,6 +503,14 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
           acc[33 + a] += J[a];                        // sum J
         }
       }
+    }
+    if (!FANR) {
+      acc[0] = a03.x;
+      acc[1] = a14.x;
+      acc[2] = a25.x;
+      acc[3] = a03.y;
+      acc[4] = a14.y;
+      acc[5] = a25.y;
     }
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
@@ -634,6 +726,7 @@ cudaError_t launch_subpixel_batch(const SubpixelParams* jobs, const int64_t* off
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
                             cudaStream_t st) {
   if (p.n_pois == 0) return cudaSuccess;
+  if (!p.ref_f32 && !p.gq) return cudaErrorInvalidValue;  // 8-bit pairs need the tap quads
   if (p.ref_f32) {
     if (method == DIC_ICGN)
       return solve_fp64 ? launch_one<false, double, float>(p, st)
