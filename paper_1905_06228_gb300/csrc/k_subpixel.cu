@@ -118,27 +118,28 @@ __device__ __forceinline__ int packed_index(int r, int c) {  // entry (r, c) of 
   return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r;
 }
 
-// Inverse of a symmetric positive definite 6x6 (21 packed lower entries,
-// identical on every lane) by the symmetric sweep operator, one lane per
-// entry: lane l < 21 holds entry (i, j), i >= j, l = i (i+1)/2 + j.  Pivot
-// k (k = 0..5) replaces a_kk by -1/a_kk, every other entry of row / column
-// k by a_ik / a_kk, and the remaining entries by a_ij - a_ik a_jk / a_kk;
-// after the six pivots the entries hold -A^-1 (Gauss-Jordan elimination in
+// Entry (i, j), i >= j, of a packed lower-triangular 6x6 held by lane
+// l = i (i+1)/2 + j (lanes >= 21 get (5, 5) and hold no entry).
+__device__ __forceinline__ void packed_entry(int lane, int& i, int& j) {
+  i = 0;
+#pragma unroll
+  for (int r = 1; r < 6; ++r) i += lane >= r * (r + 1) / 2 ? 1 : 0;
+  j = min(lane - i * (i + 1) / 2, i);
+}
+
+// Inverse of a symmetric positive definite 6x6 by the symmetric sweep
+// operator, one lane per entry of the lower triangle (lane l < 21 passes
+// its entry h = A_ij, (i, j) from packed_entry).  Pivot k (k = 0..5)
+// replaces a_kk by -1/a_kk, every other entry of row / column k by
+// a_ik / a_kk, and the remaining entries by a_ij - a_ik a_jk / a_kk; after
+// the six pivots the entries hold -A^-1 (Gauss-Jordan elimination in
 // symmetric form; the pivots are the successive Schur complements, positive
 // for a positive definite A, so no pivoting is needed).  Each step costs a
 // few instructions for the whole warp, instead of a full factorisation
 // repeated on every lane.  Returns false on every lane if a pivot is not
-// positive and finite; lanes >= 21 return no entry.
+// positive and finite; out = (A^-1)_ij on lanes < 21.
 template <typename T>
-__device__ __forceinline__ bool sweep_inverse6(const float A[21], int lane, T& out, int& oi,
-                                               int& oj) {
-  int i = 0;
-#pragma unroll
-  for (int r = 1; r < 6; ++r) i += lane >= r * (r + 1) / 2 ? 1 : 0;
-  const int j = min(lane - i * (i + 1) / 2, i);
-  float h = A[0];
-#pragma unroll
-  for (int k = 1; k < 21; ++k) h = lane == k ? A[k] : h;
+__device__ __forceinline__ bool sweep_inverse6(float h, int i, int j, T& out) {
   T a = (T)h;
   bool ok = true;
 #pragma unroll
@@ -154,10 +155,31 @@ __device__ __forceinline__ bool sweep_inverse6(const float A[21], int lane, T& o
     a = r;
   }
   out = -a;
-  oi = i;
-  oj = j;
   return ok;
 }
+
+// Sum over the warp of 32 values per lane, scattered: lane l returns the
+// sum of every lane's v[l] (five halving exchanges, 31 shuffles in all).
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = lane & h;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = up ? v[k] : v[k + h];
+      const float keep = up ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
+}
+
+// 8-bit pixel as float without a conversion instruction: its bits OR'd into
+// the mantissa of 2^23, minus 2^23 (exact).
+__device__ __forceinline__ float pixel_value(uint8_t b) {
+  return __uint_as_float(0x4B000000u | (uint32_t)b) - 8388608.0f;
+}
+__device__ __forceinline__ float pixel_value(float f) { return f; }
 
 // Column k of (L L^T)^-1 (forward then backward substitution of e_k).
 template <typename T>
@@ -205,7 +227,8 @@ __device__ __forceinline__ void chol6_solve_r(const T L[6][6], const T rinv[6], 
 __device__ __forceinline__ void compose_inverse(float p[6], const float dp[6]) {
   const float a = 1.f + dp[1], b = dp[2], c = dp[4], d = 1.f + dp[5];
   const float det = a * d - b * c;
-  const float ia = d / det, ib = -b / det, ic = -c / det, id = a / det;
+  const float rdet = __frcp_rn(det);
+  const float ia = d * rdet, ib = -b * rdet, ic = -c * rdet, id = a * rdet;
   const float itx = -(ia * dp[0] + ib * dp[3]);
   const float ity = -(ic * dp[0] + id * dp[3]);
   const float P00 = 1.f + p[1], P01 = p[2], P02 = p[0];
@@ -357,7 +380,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   {
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
-      const float f = (float)fimg[(size_t)(y0 + w.dy) * p.pitch + (x0 + w.dx)];
+      const float f = pixel_value(fimg[(size_t)(y0 + w.dy) * p.pitch + (x0 + w.dx)]);
       fsum += f;
       spt[i] = PS::pack(p.grad[(size_t)(y0 + w.dy) * W + (x0 + w.dx)], f);
     }
@@ -365,13 +388,22 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   fsum = warp_sum(fsum);  // exact for 8-bit images: integer sum below 2^24
   const float fbar = fsum / (float)N;
   float q = 0.f;
-  float Hs[21], sdsum[6], bfv[6];
+  // IC-GN: SD = (gx, gx dx, gx dy, gy, gy dx, gy dy) = (gx e, gy e) with
+  // e = (1, dx, dy).  Packed pairs: sp[a] = (gx e_a, gy e_a); the xx and yy
+  // blocks of H as pairs hp[ab] = (sum gx e_a gx e_b, sum gy e_a gy e_b),
+  // a >= b; the xy block as scalars hxy[3a+b] = sum gy e_a gx e_b; the sums
+  // of SD and of SD (f - fbar) as pairs.  Every entry is accumulated with
+  // the same products and order as sd_a sd_b point by point.
+  float2 hp[6], ssum[3], sfc[3];
+  float hxy[9];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) Hs[k] = 0.f;
+  for (int k = 0; k < 6; ++k) hp[k] = dup2(0.f);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) sdsum[k] = bfv[k] = 0.f;
+  for (int k = 0; k < 3; ++k) ssum[k] = sfc[k] = dup2(0.f);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) hxy[k] = 0.f;
   {
-    PtWalk w(lane, S, M);
+    PtWalk2 w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
       float2 gr;
       float f;
@@ -379,40 +411,59 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const float fc = f - fbar;
       q = fmaf(fc, fc, q);
       if (!FANR) {
-        const float dx = (float)w.dx, dy = (float)w.dy;
-        const float sd[6] = {gr.x, gr.x * dx, gr.x * dy, gr.y, gr.y * dx, gr.y * dy};
+        const float2 sp[3] = {gr, __fmul2_rn(gr, w.DX), __fmul2_rn(gr, w.DY)};
+        const float2 fcc = dup2(fc);
         int k = 0;
 #pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          sdsum[a] += sd[a];
-          bfv[a] = fmaf(sd[a], fc, bfv[a]);
+        for (int a = 0; a < 3; ++a) {
+          ssum[a] = __fadd2_rn(ssum[a], sp[a]);
+          sfc[a] = __ffma2_rn(sp[a], fcc, sfc[a]);
 #pragma unroll
-          for (int b = 0; b <= a; ++b, ++k) Hs[k] = fmaf(sd[a], sd[b], Hs[k]);
+          for (int b = 0; b <= a; ++b, ++k) hp[k] = __ffma2_rn(sp[a], sp[b], hp[k]);
+#pragma unroll
+          for (int b = 0; b < 3; ++b) hxy[3 * a + b] = fmaf(sp[a].y, sp[b].x, hxy[3 * a + b]);
         }
       }
     }
   }
-  q = warp_sum(q);
-  const float df = sqrtf(q);
-  if (!(df > 0.f)) {
-    write_out(0.f, 0, kZeroVarRef);
-    return;
-  }
   if (!FANR) {
+    // the 33 sums: H (21, packed lower, SD order), sum SD (6), sum SD (f -
+    // fbar) (6).  A reduce-scatter over the warp leaves sum k on lane k for
+    // the first 32; the last one and q are reduced whole.
+    float v[32];
+    {
+      int k = 0;
+      // rows 0..2 (xx block)
 #pragma unroll
-    for (int k = 0; k < 21; ++k) Hs[k] = warp_sum(Hs[k]);
+      for (int a = 0, t = 0; a < 3; ++a)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      sdsum[k] = warp_sum(sdsum[k]);
-      bfv[k] = warp_sum(bfv[k]);
-    }
-    if (lane == 0) {
+        for (int b = 0; b <= a; ++b, ++t) v[k++] = hp[t].x;
+      // rows 3..5: xy block, then yy block
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        ssd[k] = sdsum[k];
-        sbf[k] = bfv[k];
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) v[k++] = hxy[3 * a + b];
+#pragma unroll
+        for (int b = 0; b <= a; ++b) v[k++] = hp[a * (a + 1) / 2 + b].y;
       }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[21 + a] = ssum[a].x, v[24 + a] = ssum[a].y;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[27 + a] = sfc[a].x;
+      v[30] = sfc[0].y;
+      v[31] = sfc[1].y;
     }
+    const float last = warp_sum(sfc[2].y);  // sum SD_5 (f - fbar)
+    const float mine = reduce_scatter32(v, lane);
+    q = warp_sum(q);
+    const float df = sqrtf(q);
+    if (!(df > 0.f)) {
+      write_out(0.f, 0, kZeroVarRef);
+      return;
+    }
+    if (lane >= 21 && lane < 27) ssd[lane - 21] = mine;
+    if (lane >= 27) sbf[lane - 27] = mine;
+    if (lane == 0) sbf[5] = last;
     // invert H once (in the solve precision), one lane per entry of its
     // lower triangle; H^-1 goes to shared memory and lane k < 6 reads row k
     // in every iteration, so an iteration's solve is six multiply-adds per
@@ -422,25 +473,37 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     // see.  D_ii D_jj is rounded to FP32 before the solve-precision product
     // (relative 6e-8: below the FP32 sums that form H).
     float dsc[6];
-    unit_diagonal(Hs, Hs, dsc);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const float hd = __shfl_sync(0xffffffffu, mine, a * (a + 1) / 2 + a);
+      dsc[a] = hd > 0.f ? rsqrt_refined<float>(hd) : 1.f;
+    }
     int ei, ej;
+    packed_entry(lane, ei, ej);
+    float di = dsc[0], dj = dsc[0];
+#pragma unroll
+    for (int a = 1; a < 6; ++a) {
+      di = ei == a ? dsc[a] : di;
+      dj = ej == a ? dsc[a] : dj;
+    }
     TS hij;
-    if (!sweep_inverse6<TS>(Hs, lane, hij, ei, ej)) {
+    if (!sweep_inverse6<TS>(mine * (di * dj), ei, ej, hij)) {
       write_out(0.f, 0, kSingular);
       return;
     }
     if (lane < 21) {
-      float di = dsc[0], dj = dsc[0];
-#pragma unroll
-      for (int a = 1; a < 6; ++a) {
-        di = ei == a ? dsc[a] : di;
-        dj = ej == a ? dsc[a] : dj;
-      }
-      const TS v = hij * (TS)(di * dj);  // H^-1 = D Hs^-1 D
-      hinv[ei * 6 + ej] = v;
-      hinv[ej * 6 + ei] = v;
+      const TS hv = hij * (TS)(di * dj);  // H^-1 = D Hs^-1 D
+      hinv[ei * 6 + ej] = hv;
+      hinv[ej * 6 + ei] = hv;
     }
     __syncwarp();
+  } else {
+    q = warp_sum(q);
+  }
+  const float df = sqrtf(q);
+  if (!(df > 0.f)) {
+    write_out(0.f, 0, kZeroVarRef);
+    return;
   }
   if (!corners_in(prm, x0, y0, M, W, H)) {
     write_out(0.f, 0, kOutOfBounds);
