@@ -621,10 +621,13 @@ def run_batch_workload(args):
             "dtype": "bf16+f32" if form == 1 else "f32",
             "data": "synthetic (seeded speckle renders)",
             "config": {"workload": args.workload, "pairs": len(tens), "pois": int(total),
-                       "form": ("one CUDA graph: tensor-core search pair by pair, one "
-                                "persistent sub-pixel kernel" if form == 1 else
-                                "one CUDA graph: persistent FP32 search per template width, "
-                                "one persistent sub-pixel kernel"),
+                       "form": ("one CUDA graph: " +
+                                ("tensor-core search pair by pair, " if form == 1 else
+                                 "persistent FP32 search per template width, ") +
+                                ("per-pair sub-pixel launches on a second stream, each "
+                                 "overlapping the next pairs' searches"
+                                 if tuple(chosen) == (0, 0) else
+                                 "one persistent sub-pixel kernel")),
                        "autotuned": {"warps_per_cta": chosen[0], "grid_mult": chosen[1]},
                        "l2": "inputs and tables larger than L2"},
             "pairs_per_s": len(tens) / (ms / 1e3),

@@ -201,10 +201,22 @@ dic_status dic_batch_pois(dic_t h, int64_t *total, int64_t *offsets);
  * tuning change; later calls only launch it.  Requires dic_set_pairs. */
 dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out *out);
 
+/* Sub-pixel launch shape of later dic_run_batch calls: warps_per_cta 2, 4
+ * or 8 with grid_mult 1 or 2 (one persistent kernel over all pairs, grid =
+ * grid_mult x resident CTAs), or {0, 0}: per-pair launches on a second
+ * stream, each overlapping the searches of the pairs after it (tensor-core
+ * form only; dic_run_batch returns DIC_ERR_ARG otherwise).  Use it to
+ * re-apply a shape dic_autotune chose earlier.  DIC_ERR_STATE without a
+ * batch, DIC_ERR_ARG for any other shape. */
+dic_status dic_set_batch_shape(dic_t h, int warps_per_cta, int grid_mult);
+
 /* Time the batch under each candidate launch shape (sub-pixel warps per CTA
- * 2/4/8 x persistent grid 1x/2x the resident CTAs) and keep the fastest for
- * later dic_run_batch calls.  Runs the batch several times (outputs are
- * overwritten).  chosen (may be NULL) receives {warps_per_cta, grid_mult}. */
+ * 2/4/8 x persistent grid 1x/2x the resident CTAs; with the tensor-core
+ * search form also per-pair sub-pixel launches, each overlapping the next
+ * pairs' searches on a second stream) and keep the fastest for later
+ * dic_run_batch calls.  Runs the batch several times (outputs are
+ * overwritten).  chosen (may be NULL) receives {warps_per_cta, grid_mult},
+ * {0, 0} for the overlapped per-pair launches. */
 dic_status dic_autotune(dic_t h, dic_method method, const dic_batch_out *out, int *chosen);
 
 /* Summed ZNSSD of the subsets at given shapes: for POI k,

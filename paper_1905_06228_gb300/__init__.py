@@ -64,6 +64,7 @@ SIGNATURES = {
     "dic_batch_pois": (i32, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "dic_run_batch": (i32, [P, i32, C.POINTER(dic_batch_out)]),
     "dic_autotune": (i32, [P, i32, C.POINTER(dic_batch_out), C.POINTER(i32)]),
+    "dic_set_batch_shape": (i32, [P, i32, i32]),
     "dic_backward": (i32, [P, P, P, f32, P, P]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -215,6 +216,10 @@ def dic_autotune(h, method: int, out: dict) -> tuple[int, int]:
     chosen = (i32 * 2)()
     _check(lib().dic_autotune(h, method, C.byref(o), chosen), h)
     return chosen[0], chosen[1]
+
+
+def dic_set_batch_shape(h, warps_per_cta: int, grid_mult: int) -> None:
+    _check(lib().dic_set_batch_shape(h, warps_per_cta, grid_mult), h)
 
 
 def batch_outputs(total: int, device):

@@ -160,6 +160,8 @@ void free_batch(dic::BatchState* b) {
     if (c.d_offsets) cudaFree(c.d_offsets);
   }
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  for (cudaEvent_t ev : b->evs) cudaEventDestroy(ev);
   delete b;
 }
 
@@ -547,6 +549,7 @@ dic_status write_jobs(dic_t h, const dic_batch_out& o, int solve_bits) {
   if (cudaMemcpy(b->d_pjobs, pj.data(), sizeof(dic::SubpixelParams) * pj.size(),
                  cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(h, DIC_ERR_CUDA, "job upload failed");
+  b->pj = pj;
   for (auto& c : b->classes) {
     std::vector<dic::SearchParams> sj;
     for (int k : c.pairs) {
@@ -605,6 +608,9 @@ dic_status batch_tc_scratch(dic_t h) {
 dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
   dic::BatchState* b = h->batch;
   const bool tc = h->form == DIC_FORM_BF16TC;
+  const bool overlap = b->grid_mult == 0;
+  if (overlap && !tc)
+    return fail(h, DIC_ERR_ARG, "overlapped per-pair sub-pixel launches need the tensor-core form");
   for (size_t k = 0; k < b->pairs.size(); ++k) {
     const dic::BatchPair& bp = b->pairs[k];
     if (bp.n > 0 && !(tc ? bp.tc_ok : bp.fp32_ok))
@@ -667,9 +673,29 @@ dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
   }
   // integer search: the tensor-core form pair by pair (each launch fills
   // the GPU: tens of thousands of tile CTAs per 2048^2 pair), or one
-  // persistent FP32 kernel per template-width class over a work counter
-  for (size_t k = 0; tc && k < b->pairs.size() && le == cudaSuccess; ++k)
-    if (b->pairs[k].n > 0) le = dic::launch_search_tc(tcp[k], &tma[k], &tmb[k], cs);
+  // persistent FP32 kernel per template-width class over a work counter.
+  // Overlapped mode: pair k's sub-pixel kernel runs on the side stream as
+  // soon as its search is done, beside the searches of the pairs after it
+  // (tensor pipe and FP32 pipes in use at once); the side stream forks from
+  // and joins back into the capture stream.
+  if (overlap && le == cudaSuccess) {
+    le = cudaEventRecord(b->evs[0], cs);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(b->side, b->evs[0], 0);
+  }
+  for (size_t k = 0; tc && k < b->pairs.size() && le == cudaSuccess; ++k) {
+    if (b->pairs[k].n == 0) continue;
+    le = dic::launch_search_tc(tcp[k], &tma[k], &tmb[k], cs);
+    if (overlap && le == cudaSuccess) {
+      le = cudaEventRecord(b->evs[1 + k], cs);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(b->side, b->evs[1 + k], 0);
+      if (le == cudaSuccess)
+        le = dic::launch_subpixel(b->pj[k], (int)method, h->solve_bits == 64, b->side);
+    }
+  }
+  if (overlap && le == cudaSuccess) {
+    le = cudaEventRecord(b->evs[b->pairs.size() + 1], b->side);
+    if (le == cudaSuccess) le = cudaStreamWaitEvent(cs, b->evs[b->pairs.size() + 1], 0);
+  }
   for (size_t c = 0; !tc && c < b->classes.size() && le == cudaSuccess; ++c) {
     dic::BatchClass& cl = b->classes[c];
     int occ = dic::search_batch_occupancy(cl.tw, cl.smem);
@@ -681,7 +707,7 @@ dic_status build_graph(dic_t h, dic_method method, const dic_batch_out& o) {
     le = dic::launch_search_batch(cl.tw, cl.d_jobs, cl.d_offsets, (int)cl.pairs.size(),
                                   b->d_counters + c, cl.smem, (int)grid, cs);
   }
-  if (le == cudaSuccess) {
+  if (le == cudaSuccess && !overlap) {
     // grid <= 0 asks the launcher for (resident CTAs x SMs) x -grid
     le = dic::launch_subpixel_batch(b->d_pjobs, b->d_offsets, (int)b->pairs.size(), b->nmax,
                                     (int)method, h->solve_bits == 64, b->wpc,
@@ -800,6 +826,16 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
     if (e == cudaSuccess) e = upload(&c.d_offsets, co);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    int lo = 0, hi = 0;  // the side stream at the highest priority
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    e = cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi);
+  }
+  for (int k = 0; e == cudaSuccess && k < n_pairs + 2; ++k) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->evs.push_back(ev);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_batch(b);
@@ -842,34 +878,52 @@ dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out* out) {
   return DIC_OK;
 }
 
+dic_status dic_set_batch_shape(dic_t h, int warps_per_cta, int grid_mult) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->batch) return fail(h, DIC_ERR_STATE, "no batch set");
+  const bool persistent = (warps_per_cta == 2 || warps_per_cta == 4 || warps_per_cta == 8) &&
+                          (grid_mult == 1 || grid_mult == 2);
+  if (!persistent && !(warps_per_cta == 0 && grid_mult == 0))
+    return fail(h, DIC_ERR_ARG, "batch shape {%d, %d}: want {2|4|8, 1|2} or {0, 0}",
+                warps_per_cta, grid_mult);
+  h->batch->wpc = warps_per_cta;
+  h->batch->grid_mult = grid_mult;
+  return DIC_OK;
+}
+
 dic_status dic_autotune(dic_t h, dic_method method, const dic_batch_out* out, int* chosen) {
   if (!h) return DIC_ERR_ARG;
   if (!h->batch) return fail(h, DIC_ERR_STATE, "no batch set");
   dic::BatchState* b = h->batch;
-  const int wpcs[3] = {2, 4, 8}, mults[2] = {1, 2};
+  // persistent sub-pixel kernel: warps per CTA x grid multiple; with the
+  // tensor-core search also per-pair launches overlapped with the searches
+  // (encoded {0, 0})
+  std::vector<std::pair<int, int>> cands;
+  for (int w : {2, 4, 8})
+    for (int m : {1, 2}) cands.push_back({w, m});
+  if (h->form == DIC_FORM_BF16TC) cands.push_back({0, 0});
   float best = 1e30f;
   int bw = b->wpc, bm = b->grid_mult;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int w : wpcs)
-    for (int m : mults) {
-      b->wpc = w;
-      b->grid_mult = m;
-      dic_status st = dic_run_batch(h, method, out);  // builds and warms up
-      if (st != DIC_OK) continue;
-      cudaEventRecord(e0, h->stream);
-      for (int r = 0; r < 3; ++r) dic_run_batch(h, method, out);
-      cudaEventRecord(e1, h->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) continue;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        bw = w;
-        bm = m;
-      }
+  for (const auto& c : cands) {
+    b->wpc = c.first;
+    b->grid_mult = c.second;
+    dic_status st = dic_run_batch(h, method, out);  // builds and warms up
+    if (st != DIC_OK) continue;
+    cudaEventRecord(e0, h->stream);
+    for (int r = 0; r < 3; ++r) dic_run_batch(h, method, out);
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bw = c.first;
+      bm = c.second;
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->wpc = bw;

@@ -195,6 +195,9 @@ struct BatchState {
   int64_t* d_offsets = nullptr;
   unsigned long long* d_counters = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;     // sub-pixel launches overlapped with searches
+  std::vector<cudaEvent_t> evs;    // fork / per-pair / join events of the capture
+  std::vector<SubpixelParams> pj;  // host copy of the per-pair sub-pixel jobs
   cudaGraphExec_t exec = nullptr;
   dic_batch_out last_out{};
   int last_method = -1, last_wpc = 0, last_mult = 0, last_bits = 0, last_form = -1;
@@ -204,6 +207,9 @@ struct BatchState {
   int2* tc_fbox = nullptr;
   int2* tc_posbox = nullptr;
   SlotCand* tc_slots = nullptr;
+  // sub-pixel launch shape: warps per CTA x persistent grid multiple, or
+  // wpc = grid_mult = 0 for per-pair launches on the side stream, each
+  // overlapping the next pair's tensor-core search
   int wpc = 4, grid_mult = 1;
 };
 }  // namespace dic

@@ -726,8 +726,10 @@ cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
   const size_t smem = (size_t)wpc * wb;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
+    // the limit, not this launch's size: a graph may hold launches of
+    // several subset sizes, each checked against the attribute when it runs
     cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS, TP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
   const unsigned grid = (unsigned)((p.n_pois + wpc - 1) / wpc);

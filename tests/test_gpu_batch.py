@@ -24,9 +24,10 @@ def _built():
     __graft_entry__.build()
 
 
-def _run_batch(pairs, method=0, solve_bits=32, autotune=False, repeat=1, form=0):
+def _run_batch(pairs, method=0, solve_bits=32, autotune=False, repeat=1, form=0, shape=None):
     """pairs: list of (f, g, subset, step, radius) numpy uint8 pairs; form 1
-    runs the tensor-core integer search."""
+    runs the tensor-core integer search; shape = (warps_per_cta, grid_mult)
+    of the sub-pixel launches."""
     import torch
 
     import paper_1905_06228_gb300 as dic
@@ -41,6 +42,8 @@ def _run_batch(pairs, method=0, solve_bits=32, autotune=False, repeat=1, form=0)
         if form:
             dic.dic_set_form(h, form)
         dic.dic_set_pairs(h, tens)
+        if shape is not None:
+            dic.dic_set_batch_shape(h, *shape)
         total, offs = dic.dic_batch_pois(h, len(pairs))
         out = dic.batch_outputs(total, dev)
         chosen = None
@@ -154,6 +157,49 @@ def test_batch_tensor_core_search_equals_fp32_batch():
     np.testing.assert_array_equal(offs_a, offs_b)
     for key in KEYS:
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_overlapped_subpixel_launches_equal_persistent(method):
+    """Per-pair sub-pixel launches on a second stream, overlapping the next
+    pairs' tensor-core searches ({0, 0}), give bitwise the persistent
+    kernel's results (same per-POI arithmetic), on replay too; the
+    autotuner may choose either shape."""
+    pairs = _mixed_small_pairs()
+    a, _, _ = _run_batch(pairs, method=method, form=1, shape=(8, 2))
+    b, _, _ = _run_batch(pairs, method=method, form=1, shape=(0, 0), repeat=3)
+    for key in KEYS:
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+    c, _, chosen = _run_batch(pairs[:3], method=method, form=1, autotune=True, repeat=2)
+    assert tuple(chosen) in {(2, 1), (2, 2), (4, 1), (4, 2), (8, 1), (8, 2), (0, 0)}
+    for key in KEYS:
+        np.testing.assert_array_equal(c[key], a[key][:len(c[key])], err_msg=key)
+
+
+def test_batch_shape_arguments():
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    f, g = configs.tiny(78, 128, 128, 600)
+    tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+    h = dic.dic_create(15, 5, 5)
+    try:
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_set_batch_shape(h, 4, 1)
+        assert e.value.code == dic.DIC_ERR_STATE
+        dic.dic_set_pairs(h, [(tf, tg)])
+        for bad in ((3, 1), (4, 3), (0, 1), (-1, 0)):
+            with pytest.raises(dic.DICError) as e:
+                dic.dic_set_batch_shape(h, *bad)
+            assert e.value.code == dic.DIC_ERR_ARG
+        dic.dic_set_batch_shape(h, 0, 0)     # needs the tensor-core form
+        total, _ = dic.dic_batch_pois(h, 1)
+        out = dic.batch_outputs(total, torch.device("cuda:0"))
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_run_batch(h, 0, out)
+        assert e.value.code == dic.DIC_ERR_ARG
+    finally:
+        dic.dic_destroy(h)
 
 
 def test_mixed32_large_window_pairs_tensor_core():
