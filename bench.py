@@ -94,6 +94,21 @@ def shard(n_units: int, rank: int, world: int) -> list[int]:
     return list(range(rank, n_units, world))
 
 
+def reduce_over_ranks(ms: float, units: float, device) -> tuple[float, float]:
+    """Whole-job timing of the replicas: the largest timed milliseconds and
+    the summed units (converged POIs) over all ranks.  Only these two
+    numbers cross ranks; the data path exchanges nothing."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(ms), float(units)
+    t_ms = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_units = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t_ms, op=tdist.ReduceOp.MAX)
+    tdist.all_reduce(t_units, op=tdist.ReduceOp.SUM)
+    return float(t_ms.item()), float(t_units.item())
+
+
 def config_dict(world: int) -> dict:
     return {"workload": WORKLOAD, "image": "1024x1024 u8", "pairs_per_gpu": 1,
             "subset": SUBSET, "grid_step": STEP, "search_radius": RADIUS, "pois_per_pair": 36100,
@@ -241,17 +256,7 @@ def run_gpu(args):
     sampler = ClockSampler(local)
     step_ms, (search_ms, sub_ms), conv, wall, clocks = timed_loop(d, args.steps, args.warmup,
                                                                    sampler)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms, float(conv)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum[1:], op=torch.distributed.ReduceOp.SUM)
-        total_ms = float(tmax[0])
-        conv_all = float(tsum[1])
-    else:
-        conv_all = float(conv)
+    total_ms, conv_all = reduce_over_ranks(sum(step_ms), conv, dev)
     ms_per_step = total_ms / args.steps
     value = conv_all * args.steps / (total_ms / 1e3)
 
@@ -294,9 +299,9 @@ def run_gpu(args):
                 h_s[k].copy_(s_out[k], non_blocking=True)
             e_ends[i].record(stream)
     torch.cuda.synchronize(dev)
-    e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)) / ek
-    e_conv = int((h_out["status"] == 0).sum().item())
-    e2e = {"value": e_conv / (e_ms / 1e3) * world, "unit": UNIT,
+    e_ms, e_conv = reduce_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)) / ek,
+                                     int((h_out["status"] == 0).sum().item()), dev)
+    e2e = {"value": e_conv / (e_ms / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(h_ref.numel() + h_def.numel()),
            "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_out.values())
                                      + sum(v.numel() * v.element_size() for v in h_s.values()))}
