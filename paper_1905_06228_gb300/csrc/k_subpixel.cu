@@ -37,6 +37,7 @@
 #define DIC_SUB_UNROLL 1
 #endif
 
+
 #include <cuda_fp16.h>
 
 #include "dic_device.cuh"
