@@ -208,7 +208,7 @@ def run_gpu(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(dd, events=None):
+    def step(dd, events=None, method=dic.DIC_ICGN):
         # events: (before search, after search, after sub-pixel), on the
         # stream the kernels are launched on
         dic.dic_set_pair(dd.h, ref_d, def_d)
@@ -217,17 +217,17 @@ def run_gpu(args):
         dic.dic_integer_search(dd.h, s_out["u0"], s_out["v0"], s_out["zncc0"], s_out["status0"])
         if events:
             events[1].record(stream)
-        dic.dic_subpixel(dd.h, dic.DIC_ICGN, s_out["u0"], s_out["v0"], s_out["status0"],
+        dic.dic_subpixel(dd.h, method, s_out["u0"], s_out["v0"], s_out["status0"],
                          p_out["u"], p_out["v"], p_out["ux"], p_out["uy"], p_out["vx"],
                          p_out["vy"], p_out["zncc"], p_out["iters"], p_out["status"])
         if events:
             events[2].record(stream)
 
-    def timed_loop(dd, steps, warmup, sampler=None):
+    def timed_loop(dd, steps, warmup, sampler=None, method=dic.DIC_ICGN):
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 flush.zero_()
-                step(dd)
+                step(dd, method=method)
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
@@ -242,7 +242,7 @@ def run_gpu(args):
             for i in range(steps):
                 flush.zero_()
                 starts[i].record(stream)
-                step(dd, sev[i])
+                step(dd, sev[i], method=method)
                 ends[i].record(stream)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
@@ -275,6 +275,14 @@ def run_gpu(args):
     other_value = convo * len(sto) / (sum(sto) / 1e3)
     other_sub_ms = statistics.mean(seo[1])
     dob.close()
+    # the chosen form with forward-additive Newton-Raphson (Gauss-Newton
+    # form) in place of IC-GN
+    dnr = make(args.solve_bits, args.form)
+    dnr.set_pair(ref_d, def_d)
+    stn, sen, convn, _, _ = timed_loop(dnr, max(10, args.steps // 4), 3, method=dic.DIC_FANR)
+    fanr_value = convn * len(stn) / (sum(stn) / 1e3)
+    fanr_sub_ms = statistics.mean(sen[1])
+    dnr.close()
 
     # e2e through the public call with host buffers: H2D of both images,
     # the three kernels, D2H of every per-POI output, all inside the events
@@ -377,6 +385,9 @@ def run_gpu(args):
                               "search": "bf16-tensor-core-exact" if args.form == "tc"
                               else "fp32-exact", "solve": f"fp{other_bits}",
                               "value": other_value, "subpixel_ms": other_sub_ms},
+                          "chosen_fanr": {"method": "FA-NR (Gauss-Newton form)",
+                                          "solve": f"fp{args.solve_bits}",
+                                          "value": fanr_value, "subpixel_ms": fanr_sub_ms},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
                                          "value": plain_value}},
                 "converged_fraction": conv / n, "wall_s_timed": wall}

@@ -2,8 +2,9 @@
 //
 // One warp per POI; lane l owns subset points i = l, l+32, ...  Per-point
 // reference data (the gradient of f and f) lives in shared memory for the
-// whole solve; the deformed image is interpolated from its float copy (Keys
-// weights evaluated per sample).
+// whole solve; the deformed image is interpolated with Keys weights
+// evaluated per sample, from its BF16 tap quads (IC-GN, 8-bit pairs) or its
+// float copy.
 //
 // Warp:   W(xi; p) = (x0 + dx + u + ux dx + uy dy, y0 + dy + v + vx dx + vy dy).
 // IC-GN:  SD_i = grad f_i dW/dp, H = sum SD^T SD (once per POI),
@@ -20,10 +21,12 @@
 // lane accumulates S0 = sum (g-c), S1 = sum (g-c)^2 and sum SD_k (g-c) (or
 // the FA-NR sums); then gbar = c + S0/N, dg^2 = S1 - S0^2/N and the
 // right-hand side follow exactly as in the formulas above.  The 6x6 solve is
-// FP32 or FP64, chosen per launch: a Cholesky factorisation whose diagonal
-// reciprocals come from a refined reciprocal square root (no divisions);
-// IC-GN factors H once and keeps H^-1 (row k on lane k), FA-NR factors its
-// Gauss-Newton matrix every iteration.  Each pass also accumulates
+// FP32 or FP64, chosen per launch: the matrix, scaled to a unit diagonal,
+// is inverted by the symmetric sweep operator with one lane per entry of
+// its lower triangle (pivot reciprocals refined by Newton's iteration, no
+// divisions) into shared memory, and lane k < 6 forms row k of H^-1 times
+// the right-hand side; IC-GN inverts H once per POI, FA-NR its Gauss-Newton
+// matrix every iteration.  Each pass also accumulates
 // sum (f-fbar)(g-c), so a POI that converges reports Eq. 1 at the shape its
 // last pass sampled (the returned shape differs by the final update, below
 // tol, at a stationary point of C: the two values differ by O(|dp|^2));
@@ -62,42 +65,6 @@ template <>
 __device__ __forceinline__ float rsqrt_refined<float>(float d) {
   float y = rsqrtf(d);
   return y * (1.5f - 0.5f * d * y * y);
-}
-template <>
-__device__ __forceinline__ double rsqrt_refined<double>(double d) {
-  double y = (double)rsqrtf((float)d);
-  y = y * (1.5 - 0.5 * d * y * y);
-  return y * (1.5 - 0.5 * d * y * y);
-}
-
-// Cholesky factor L (lower) of the symmetric 6x6 given as 21 packed lower
-// entries (row-major), with the reciprocals of its diagonal; no divisions.
-template <typename T>
-__device__ __forceinline__ bool chol6_packed(const float Hp[21], T L[6][6], T rinv[6]) {
-  int k0 = 0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) L[i][j] = (T)Hp[k0++];
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    T d = L[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    ok = ok && (d > T(0)) && (d < T(3e38));
-    const T r = rsqrt_refined<T>(ok ? d : T(1));
-    L[j][j] = d * r;
-    rinv[j] = r;
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      T sacc = L[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) sacc -= L[i][k] * L[j][k];
-      L[i][j] = sacc * r;
-    }
-  }
-  return ok;
 }
 
 // 1/d: FP32 reciprocal refined by Newton's iteration y <- y + y (1 - d y)
@@ -175,54 +142,48 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
   return v[0];
 }
 
+// H^-1 into shared memory (36 solve-precision values, row-major) from the 21
+// entries of a symmetric positive definite H held one per lane (lane l < 21:
+// packed entry l, see packed_entry): H is first scaled symmetrically to a
+// unit diagonal (Hs = D H D, D_ii = H_ii^-1/2; H^-1 = D Hs^-1 D) -- the
+// translation and gradient columns differ in scale by ~M^2, which the
+// elimination then does not see -- then inverted by the sweep.  D_ii D_jj is
+// rounded to FP32 before the solve-precision product (relative 6e-8, below
+// the FP32 sums that form H).  Returns false (every lane) if H is not
+// positive definite.
+template <typename TS>
+__device__ __forceinline__ bool invert_to_smem(float mine, int lane, TS* hinv) {
+  float dsc[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float hd = __shfl_sync(0xffffffffu, mine, a * (a + 1) / 2 + a);
+    dsc[a] = hd > 0.f ? rsqrt_refined<float>(hd) : 1.f;
+  }
+  int ei, ej;
+  packed_entry(lane, ei, ej);
+  float di = dsc[0], dj = dsc[0];
+#pragma unroll
+  for (int a = 1; a < 6; ++a) {
+    di = ei == a ? dsc[a] : di;
+    dj = ej == a ? dsc[a] : dj;
+  }
+  TS hij;
+  if (!sweep_inverse6<TS>(mine * (di * dj), ei, ej, hij)) return false;
+  if (lane < 21) {
+    const TS hv = hij * (TS)(di * dj);
+    hinv[ei * 6 + ej] = hv;
+    hinv[ej * 6 + ei] = hv;
+  }
+  __syncwarp();
+  return true;
+}
+
 // 8-bit pixel as float without a conversion instruction: its bits OR'd into
 // the mantissa of 2^23, minus 2^23 (exact).
 __device__ __forceinline__ float pixel_value(uint8_t b) {
   return __uint_as_float(0x4B000000u | (uint32_t)b) - 8388608.0f;
 }
 __device__ __forceinline__ float pixel_value(float f) { return f; }
-
-// Column k of (L L^T)^-1 (forward then backward substitution of e_k).
-template <typename T>
-__device__ __forceinline__ void chol6_inverse_col(const T L[6][6], const T rinv[6], int k,
-                                                  T x[6]) {
-  T y[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    T sacc = (i == k) ? T(1) : T(0);
-#pragma unroll
-    for (int j = 0; j < i; ++j) sacc -= L[i][j] * y[j];
-    y[i] = sacc * rinv[i];
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    T sacc = y[i];
-#pragma unroll
-    for (int j = i + 1; j < 6; ++j) sacc -= L[j][i] * x[j];
-    x[i] = sacc * rinv[i];
-  }
-}
-
-// Solve (L L^T) x = b with the stored reciprocals.
-template <typename T>
-__device__ __forceinline__ void chol6_solve_r(const T L[6][6], const T rinv[6], const T b[6],
-                                              T x[6]) {
-  T y[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    T sacc = b[i];
-#pragma unroll
-    for (int j = 0; j < i; ++j) sacc -= L[i][j] * y[j];
-    y[i] = sacc * rinv[i];
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    T sacc = y[i];
-#pragma unroll
-    for (int j = i + 1; j < 6; ++j) sacc -= L[j][i] * x[j];
-    x[i] = sacc * rinv[i];
-  }
-}
 
 // W(p) <- W(p) W(dp)^-1 for the first-order warp.
 __device__ __forceinline__ void compose_inverse(float p[6], const float dp[6]) {
@@ -244,43 +205,6 @@ __device__ __forceinline__ void compose_inverse(float p[6], const float dp[6]) {
   p[3] = n12;
   p[4] = n10;
   p[5] = n11 - 1.f;
-}
-
-// Diagonal of a packed symmetric 6x6 scaled to one: Hs = D H D with
-// D_ii = H_ii^-1/2 (1 where H_ii <= 0, which the factorisation then rejects).
-__device__ __forceinline__ void unit_diagonal(const float Hf[21], float Hs[21], float dsc[6]) {
-  int k = 0;
-#pragma unroll
-  for (int a = 0; a < 6; ++a) {
-    k += a;  // index of H[a][a] in the packed lower triangle
-    dsc[a] = Hf[k] > 0.f ? rsqrt_refined<float>(Hf[k]) : 1.f;
-    ++k;
-  }
-  k = 0;
-#pragma unroll
-  for (int a = 0; a < 6; ++a)
-#pragma unroll
-    for (int b = 0; b <= a; ++b, ++k) Hs[k] = Hf[k] * (dsc[a] * dsc[b]);
-}
-
-// Solve H x = b through the unit-diagonal form: (D H D) y = D b, x = D y.
-template <typename T>
-__device__ __forceinline__ bool solve6(const float Hf[21], const float bf[6], float out[6],
-                                       bool negate) {
-  float Hs[21], dsc[6];
-  unit_diagonal(Hf, Hs, dsc);
-  T L[6][6], rinv[6];
-  if (!chol6_packed<T>(Hs, L, rinv)) return false;
-  T b[6], x[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) b[i] = (T)bf[i] * (T)dsc[i];
-  chol6_solve_r<T>(L, rinv, b, x);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const float xi = (float)(x[i] * (T)dsc[i]);
-    out[i] = negate ? -xi : xi;
-  }
-  return true;
 }
 
 template <typename T>
@@ -468,36 +392,11 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     // invert H once (in the solve precision), one lane per entry of its
     // lower triangle; H^-1 goes to shared memory and lane k < 6 reads row k
     // in every iteration, so an iteration's solve is six multiply-adds per
-    // lane.  H is first scaled symmetrically to a unit diagonal (Hs = D H D,
-    // D_ii = H_ii^-1/2; H^-1 = D Hs^-1 D): the translation and gradient
-    // columns differ in scale by ~M^2, which the elimination then does not
-    // see.  D_ii D_jj is rounded to FP32 before the solve-precision product
-    // (relative 6e-8: below the FP32 sums that form H).
-    float dsc[6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a) {
-      const float hd = __shfl_sync(0xffffffffu, mine, a * (a + 1) / 2 + a);
-      dsc[a] = hd > 0.f ? rsqrt_refined<float>(hd) : 1.f;
-    }
-    int ei, ej;
-    packed_entry(lane, ei, ej);
-    float di = dsc[0], dj = dsc[0];
-#pragma unroll
-    for (int a = 1; a < 6; ++a) {
-      di = ei == a ? dsc[a] : di;
-      dj = ej == a ? dsc[a] : dj;
-    }
-    TS hij;
-    if (!sweep_inverse6<TS>(mine * (di * dj), ei, ej, hij)) {
+    // lane.
+    if (!invert_to_smem<TS>(mine, lane, hinv)) {
       write_out(0.f, 0, kSingular);
       return;
     }
-    if (lane < 21) {
-      const TS hv = hij * (TS)(di * dj);  // H^-1 = D Hs^-1 D
-      hinv[ei * 6 + ej] = hv;
-      hinv[ej * 6 + ei] = hv;
-    }
-    __syncwarp();
   } else {
     q = warp_sum(q);
   }
@@ -578,8 +477,21 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     }
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
+    // FA-NR: the first 32 of its 39 sums by a reduce-scatter (sum k on lane
+    // k: J^T J on lanes 0..20, sum J (g - c) on 21..26, sum J (f - fbar) of
+    // J_0..J_4 on 27..31), the other 7 whole
+    float fa_mine = 0.f;
+    if (!FANR) {
 #pragma unroll
-    for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = warp_sum(acc[k]);
+      for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
+    } else {
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = acc[k];
+      fa_mine = reduce_scatter32(v, lane);
+#pragma unroll
+      for (int k = 32; k < (FANR ? 39 : 6); ++k) acc[k] = warp_sum(acc[k]);
+    }
     const float gm = s0 * invN;  // gbar - c
     const float var = s1 - s0 * gm;
     const float dg = sqrtf(fmaxf(var, 0.f));
@@ -602,16 +514,35 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       for (int a = 0; a < 6; ++a) dp[a] = __shfl_sync(0xffffffffu, mine, a);
       ok = true;
     } else {
+      // rhs_a = ratio sum J_a (f - fbar) - (sum J_a (g - c) - gm sum J_a),
+      // formed on lane 21 + a, then broadcast
       const float ratio = dg / df;
+      const float jf = __shfl_sync(0xffffffffu, fa_mine, min(lane + 6, 31));
+      float r = 0.f;
+      if (lane >= 21 && lane < 27) {
+        const int a = lane - 21;
+        float sj = acc[33];
 #pragma unroll
-      for (int a = 0; a < 6; ++a)
-        rhs[a] = ratio * acc[27 + a] - (acc[21 + a] - gm * acc[33 + a]);
-      ok = solve6<TS>(acc, rhs, dp, false);
+        for (int b = 1; b < 6; ++b) sj = a == b ? acc[33 + b] : sj;
+        r = ratio * (a < 5 ? jf : acc[32]) - (fa_mine - gm * sj);
+      }
+#pragma unroll
+      for (int a = 0; a < 6; ++a) rhs[a] = __shfl_sync(0xffffffffu, r, 21 + a);
+      // dp = (J^T J)^-1 rhs: the sweep inverse (solve precision) into shared
+      // memory, lane k < 6 forms row k . rhs
+      ok = invert_to_smem<TS>(fa_mine, lane, hinv);
       if (!ok) {
         it_done = it;
         st = kSingular;
         break;
       }
+      TS acc6 = TS(0);
+      const TS* hr = hinv + (lane < 6 ? lane : 0) * 6;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) acc6 += hr[a] * (TS)rhs[a];
+      const float mine = (float)acc6;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) dp[a] = __shfl_sync(0xffffffffu, mine, a);
     }
     it_done = it;
     bool fin = true;
