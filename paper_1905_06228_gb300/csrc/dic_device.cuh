@@ -68,9 +68,7 @@ __device__ __forceinline__ float bicubic(const float* __restrict__ img, int W, s
 // ---- packed FP32 (Blackwell f32x2: two FP32 operations per instruction).
 // Each packed operation rounds every half exactly like its scalar form, so
 // the helpers below give bitwise the results of keys_weights / bicubic /
-// locate.  (The compiler pairs the equivalent scalar code into the same
-// f32x2 instructions by itself -- identical instruction counts measured --
-// so the explicit form documents the pairing rather than adding to it.)
+// locate.
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 // Keys weights of both axes at once: w[k] = (weight of tap k-1 along x at
@@ -128,6 +126,31 @@ __device__ __forceinline__ float bicubic_q(const uint2* __restrict__ gq, int W, 
     rr[h] = __ffma2_rn(dup2(w[3].x), p3, acc);
   }
   return fmaf(w[3].y, rr[1].y, fmaf(w[2].y, rr[1].x, fmaf(w[1].y, rr[0].y, w[0].y * rr[0].x)));
+}
+
+// Value and gradient of the bicubic patch from the tap quads (as
+// bicubic<true> on the float copy, same operations and order: bitwise
+// equal), for FA-NR's Jacobian.
+__device__ __forceinline__ float bicubic_q_grad(const uint2* __restrict__ gq, int W, size_t cell,
+                                                float tx, float ty, float& gx, float& gy) {
+  float wx[4], wy[4], dx[4], dy[4];
+  keys_weights(tx, wx);
+  keys_weights(ty, wy);
+  keys_dweights(tx, dx);
+  keys_dweights(ty, dy);
+  const uint2* r = gq + cell - W;
+  float row[4], drow[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) {
+    const uint2 q = __ldg(r + (size_t)l * W);
+    const float p0 = __uint_as_float(q.x << 16), p1 = __uint_as_float(q.x & 0xFFFF0000u);
+    const float p2 = __uint_as_float(q.y << 16), p3 = __uint_as_float(q.y & 0xFFFF0000u);
+    row[l] = fmaf(wx[3], p3, fmaf(wx[2], p2, fmaf(wx[1], p1, wx[0] * p0)));
+    drow[l] = fmaf(dx[3], p3, fmaf(dx[2], p2, fmaf(dx[1], p1, dx[0] * p0)));
+  }
+  gx = fmaf(wy[3], drow[3], fmaf(wy[2], drow[2], fmaf(wy[1], drow[1], wy[0] * drow[0])));
+  gy = fmaf(dy[3], row[3], fmaf(dy[2], row[2], fmaf(dy[1], row[1], dy[0] * row[0])));
+  return fmaf(wy[3], row[3], fmaf(wy[2], row[2], fmaf(wy[1], row[1], wy[0] * row[0])));
 }
 
 // The warp W(xi; p) of one shape, for packed point offsets (dx, dx), (dy, dy):

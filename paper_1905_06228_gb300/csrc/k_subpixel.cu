@@ -36,6 +36,9 @@
 #ifndef DIC_SUB_MINB
 #define DIC_SUB_MINB 4
 #endif
+#ifndef DIC_SUB_MINB_NR
+#define DIC_SUB_MINB_NR 1
+#endif
 #ifndef DIC_SUB_UNROLL
 #define DIC_SUB_UNROLL 1
 #endif
@@ -276,7 +279,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
   float* ssd = reinterpret_cast<float*>(hinv + 36);  // sum SD
   float* sbf = ssd + 6;                              // sum SD (f - fbar)
   const TP* fimg = ref_ptr<TP>(p);
-  // 8-bit pairs sample IC-GN's g from the BF16 tap quads (exact)
+  // 8-bit pairs sample g from the BF16 tap quads (exact)
   constexpr bool kQuads = sizeof(TP) == 1;
 
   const uint8_t st0 = p.st0[poi];
@@ -432,7 +435,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       float gx = 0.f, gy = 0.f;
       const size_t cell = wa.locate(w.DX, w.DY, W, H, t);
       float g;
-      if (FANR)
+      if (FANR && kQuads)
+        g = bicubic_q_grad(p.gq, W, cell, t.x, t.y, gx, gy);
+      else if (FANR)
         g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
       else if (kQuads)
         g = bicubic_q(p.gq, W, cell, t);
@@ -609,7 +614,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 
 // One warp per POI of one pair.
 template <bool FANR, typename TS, typename TP>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, FANR ? 1 : DIC_SUB_MINB)
+__global__ void __launch_bounds__(32 * kWarpsPerCta, FANR ? DIC_SUB_MINB_NR : DIC_SUB_MINB)
 subpixel_kernel(const SubpixelParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
