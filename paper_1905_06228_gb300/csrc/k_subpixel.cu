@@ -36,8 +36,11 @@
 #ifndef DIC_SUB_MINB
 #define DIC_SUB_MINB 4
 #endif
+// FA-NR (39 sums per sample): 4 CTAs/SM, 96 registers without spills
+// (1.05 ms on affine1024 against 1.13 ms at 3 CTAs/SM and 1.39 ms at 146
+// registers and 2 CTAs/SM)
 #ifndef DIC_SUB_MINB_NR
-#define DIC_SUB_MINB_NR 1
+#define DIC_SUB_MINB_NR 4
 #endif
 #ifndef DIC_SUB_UNROLL
 #define DIC_SUB_UNROLL 1
@@ -627,8 +630,15 @@ subpixel_kernel(const SubpixelParams p) {
 // Persistent form over many pairs: every warp repeatedly takes the next POI
 // of the batch from a global counter, so POIs with many iterations do not
 // hold back a whole CTA.  nmax = largest subset size N of the batch.
+// resident warps per SM the persistent kernel asks the register allocator
+// for (as the single-pair kernel: 20 for IC-GN, 15 for FA-NR)
+template <bool FANR, int WPC>
+constexpr int batch_min_blocks() {
+  return (FANR ? 15 : 20) / WPC > 1 ? (FANR ? 15 : 20) / WPC : 1;
+}
+
 template <bool FANR, typename TS, int WPC>
-__global__ void __launch_bounds__(32 * WPC)
+__global__ void __launch_bounds__(32 * WPC, batch_min_blocks<FANR, WPC>())
 subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
                       const int64_t* __restrict__ offsets, int njobs, int nmax,
                       unsigned long long* counter) {
