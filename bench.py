@@ -40,6 +40,9 @@ FP32_LANES_PER_SM = 128
 # (IC-GN): warp 8, Keys weights 2 x 17, 4x4 convolution 35, residual and
 # right-hand-side sums 16, the cross sum of Eq. 1 3.
 FLOP_PER_SAMPLE = 96
+# algorithmic bytes per pixel of the precompute kernel: f and g read (1 + 1),
+# gradient (8), float g (4) and BF16 tap quads (8) written
+PRECOMPUTE_BYTES_PER_PX = 22
 # kernels launched per step: precompute, then the integer search (phase
 # images, template bank, box-sum maps of f and g in one launch, tile,
 # reduce; or one FP32 search kernel), then the sub-pixel kernel
@@ -362,6 +365,21 @@ def run_gpu(args):
                                              "frac_of_fp32_peak": flops / (plain_search_ms / 1e3)
                                              / 1e12 / fp32_peak}}
 
+    # whole-path roofline: each step at its own bound (search flops at the
+    # search's peak, sub-pixel flops at the FP32 peak, precompute bytes at
+    # HBM), summed, against the measured step time
+    peaks_all = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = float(peaks_all.get("hbm_gbs", 6800.0)) * 1e9
+    pre_bytes = PRECOMPUTE_BYTES_PER_PX * pair.ref.size
+    t_roof = flops / (peak * 1e12) + FLOP_PER_SAMPLE * samples / (fp32_peak * 1e12) + pre_bytes / hbm
+    roofline_path = {"roofline_ms": t_roof * 1e3, "measured_ms": ms_per_step,
+                     "frac": t_roof * 1e3 / ms_per_step,
+                     "terms": {"search_ms": flops / (peak * 1e12) * 1e3,
+                               "subpixel_ms": FLOP_PER_SAMPLE * samples / (fp32_peak * 1e12) * 1e3,
+                               "precompute_ms": pre_bytes / hbm * 1e3},
+                     "hbm_basis": "measured" if peaks_all else "fallback"}
+
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(pair, args.cpu_sample)
@@ -377,6 +395,7 @@ def run_gpu(args):
                 "gpu_launches": (LAUNCHES_TC if args.form == "tc" else LAUNCHES_PLAIN)
                 * args.steps,
                 "roofline": roofline, "roofline_search": roofline_search,
+                "roofline_path": roofline_path,
                 "cpu_baseline": cpu, "clocks": clocks,
                 "forms": {"chosen": {"search": "bf16-tensor-core-exact" if args.form == "tc"
                                      else "fp32-exact", "solve": f"fp{args.solve_bits}",
