@@ -449,9 +449,12 @@ def run_reference(args):
         return
     from workloads import configs
     pair = configs.affine1024(pair=0)
-    sample = max(64, args.cpu_sample // 8)
     for _ in range(args.warmup):
         cpu_baseline(pair, 64)
+    # POIs per step: sized from a calibration sample so that all timed steps
+    # together take about 90 s of host time (at least 64 POIs per step)
+    rate = cpu_baseline(pair, 512)["value"]
+    sample = int(min(args.cpu_sample, max(64, 90.0 / max(1, args.steps) * rate)))
     vals, secs = [], []
     for _ in range(args.steps):
         t0 = time.perf_counter()
