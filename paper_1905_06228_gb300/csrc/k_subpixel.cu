@@ -31,8 +31,9 @@
 // last pass sampled (the returned shape differs by the final update, below
 // tol, at a stationary point of C: the two values differ by O(|dp|^2));
 // other POIs get one extra pass at the returned shape.
-// resident CTAs per SM requested from the register allocator, and the
-// unroll of the per-point loop (memory-level parallelism of the sample loads)
+
+// Build options: resident CTAs per SM requested from the register allocator
+// (IC-GN, FA-NR), warps per CTA, and the unroll of the per-point loop.
 #ifndef DIC_SUB_MINB
 #define DIC_SUB_MINB 4
 #endif
@@ -45,9 +46,6 @@
 #ifndef DIC_SUB_UNROLL
 #define DIC_SUB_UNROLL 1
 #endif
-
-
-#include <cuda_fp16.h>
 
 #include "dic_device.cuh"
 #include "dic_internal.cuh"
