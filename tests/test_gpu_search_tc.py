@@ -109,6 +109,19 @@ def test_large_radius_many_slots():
     compare_search(b, oracle.integer_search(f, g, 41, 13, 85))
 
 
+def test_odd_pitch_images():
+    """Images inside wider buffers with an odd row pitch (not 16-byte aligned):
+    the tensor-core form reads them with plain loads into its own phase
+    images and template bank, so the results equal the unpadded case."""
+    f, g = configs.tiny(79, 150, 110, 520, Affine(0.004, 0.002, -0.5, -3.2, 2.1, 75, 55),
+                        noise=1.0)
+    a = run_gpu(f, g, 15, 5, 6, subpixel=False, form=TC)
+    b = run_gpu(f, g, 15, 5, 6, subpixel=False, form=TC, pitch_pad=3)
+    for k in INT_KEYS:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    compare_search(b, oracle.integer_search(f, g, 15, 5, 6))
+
+
 def test_unsupported_geometry_is_reported():
     import torch
 
