@@ -24,10 +24,11 @@
 // full/empty mbarriers; the accumulator lives in TMEM.
 //
 // Exactness: a = f-128 and b = g-128 are integers in [-128, 127], exact in
-// BF16; |ab| <= 2^14, so any sum of at most 1024 products is an integer
-// below 2^24 and the FP32 accumulation is exact.  Subsets wider than 32 use
-// several accumulators (blocks of floor(1024/TWK) template rows), added in
-// int32 by the epilogue.  Candidate scores use the exact integers
+// BF16; |ab| <= 2^14, so any sum of at most 1024 products is an integer of
+// magnitude at most 2^24 and the FP32 accumulation is exact.  Subsets wider
+// than 32 use several accumulators (blocks of floor(1024/S) template rows:
+// the taps at or beyond S are zero, so a block holds at most 1024 nonzero
+// products), added in int32 by the epilogue.  Candidate scores use the exact integers
 // num = N Sab - Sa Sb, Dg = N Sbb - Sb^2, with Sa, Saa per POI and Sb, Sbb
 // per position (box sums of f and g).
 //
@@ -865,7 +866,9 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   if (S > 64) return false;
   g->twk = S <= 16 ? 16 : S <= 32 ? 32 : 64;  // one swizzle width per operand row
   if (nx == 0 || ny == 0) return false;
-  g->rows_per_acc = 1024 / g->twk;
+  // exact FP32 sums: at most 1024 nonzero products of |ab| <= 2^14 per
+  // accumulator (taps at or beyond S are zero in the bank)
+  g->rows_per_acc = 1024 / S;
   if (g->rows_per_acc > S) g->rows_per_acc = S;
   const int nacc = (S + g->rows_per_acc - 1) / g->rows_per_acc;
   // POI block of a tile: ncols x nrows_all POIs.  One CTA takes nrows_max
