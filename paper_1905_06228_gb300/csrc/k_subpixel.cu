@@ -428,22 +428,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     for (int k = 0; k < (FANR ? 39 : 6); ++k) acc[k] = 0.f;
     // IC-GN sums in packed pairs: (SD0, SD3), (SD1, SD4), (SD2, SD5) . (g - c)
     float2 a03 = dup2(0.f), a14 = dup2(0.f), a25 = dup2(0.f);
-    const WarpAffine wa(prm, x0, y0);
-    PtWalk2 w(lane, S, M);
-#pragma unroll kPointUnroll
-    for (int i = lane; i < N; i += 32, w.next()) {
-      float2 t;
-      float gx = 0.f, gy = 0.f;
-      const size_t cell = wa.locate(w.DX, w.DY, W, H, t);
-      float g;
-      if (FANR && kQuads)
-        g = bicubic_q_grad(p.gq, W, cell, t.x, t.y, gx, gy);
-      else if (FANR)
-        g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
-      else if (kQuads)
-        g = bicubic_q(p.gq, W, cell, t);
-      else
-        g = bicubic2(p.gimg, W, cell, t);
+    // one sample: g (and, for FA-NR, its gradient) at point i with packed
+    // offsets (dx, dx), (dy, dy)
+    auto absorb = [&](int i, float g, float gx, float gy, float2 DX, float2 DY) {
       const float d = g - c;
       s0 += d;
       s1 = fmaf(d, d, s1);
@@ -455,10 +442,10 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       if (!FANR) {
         const float2 ab = __fmul2_rn(gr, dup2(d));  // (SD0, SD3) (g - c)
         a03 = __fadd2_rn(a03, ab);
-        a14 = __ffma2_rn(ab, w.DX, a14);
-        a25 = __ffma2_rn(ab, w.DY, a25);
+        a14 = __ffma2_rn(ab, DX, a14);
+        a25 = __ffma2_rn(ab, DY, a25);
       } else {
-        const float fdx = w.DX.x, fdy = w.DY.x;
+        const float fdx = DX.x, fdy = DY.x;
         const float J[6] = {gx, gx * fdx, gx * fdy, gy, gy * fdx, gy * fdy};
         int k = 0;
 #pragma unroll
@@ -471,6 +458,55 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
           acc[27 + a] = fmaf(J[a], fc, acc[27 + a]);  // sum J (f - fbar)
           acc[33 + a] += J[a];                        // sum J
         }
+      }
+    };
+    if (it == 1) {
+      // The first iteration samples at the integer start (u0, v0) with zero
+      // gradients: every sample lies on a pixel, where the Keys weights are
+      // exactly (0, 1, 0, 0) and their derivatives (-1/2, 0, 1/2, 0), so the
+      // interpolant is the pixel and its gradient the central differences --
+      // bitwise what the interpolating path below computes, from one load
+      // per sample (three for FA-NR).  The walk matches PtWalk2's.
+      const float* gb = p.gimg + (size_t)(y0 + (int)prm[3]) * W + (x0 + (int)prm[0]);
+      float2 DX = dup2((float)(lane % S - M)), DY = dup2((float)(lane / S - M));
+      const float ddx = (float)(32 % S), ddy = (float)(32 / S), fM = (float)M, fS = (float)S;
+      int off = (lane / S - M) * W + (lane % S - M);
+      const int doff = (32 / S) * W + 32 % S, dwrap = W - S;
+      for (int i = lane; i < N; i += 32) {
+        const float* gp = gb + off;
+        float gx = 0.f, gy = 0.f;
+        if (FANR) {
+          gx = fmaf(0.5f, __ldg(gp + 1), -0.5f * __ldg(gp - 1));
+          gy = fmaf(0.5f, __ldg(gp + W), -0.5f * __ldg(gp - W));
+        }
+        absorb(i, __ldg(gp), gx, gy, DX, DY);
+        DX = __fadd2_rn(DX, dup2(ddx));
+        DY = __fadd2_rn(DY, dup2(ddy));
+        off += doff;
+        if (DX.x > fM) {
+          DX = __fadd2_rn(DX, dup2(-fS));
+          DY = __fadd2_rn(DY, dup2(1.f));
+          off += dwrap;
+        }
+      }
+    } else {
+      const WarpAffine wa(prm, x0, y0);
+      PtWalk2 w(lane, S, M);
+#pragma unroll kPointUnroll
+      for (int i = lane; i < N; i += 32, w.next()) {
+        float2 t;
+        float gx = 0.f, gy = 0.f;
+        const size_t cell = wa.locate(w.DX, w.DY, W, H, t);
+        float g;
+        if (FANR && kQuads)
+          g = bicubic_q_grad(p.gq, W, cell, t.x, t.y, gx, gy);
+        else if (FANR)
+          g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
+        else if (kQuads)
+          g = bicubic_q(p.gq, W, cell, t);
+        else
+          g = bicubic2(p.gimg, W, cell, t);
+        absorb(i, g, gx, gy, w.DX, w.DY);
       }
     }
     if (!FANR) {
