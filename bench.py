@@ -40,6 +40,9 @@ FP32_LANES_PER_SM = 128
 # (IC-GN): warp 8, Keys weights 2 x 17, 4x4 convolution 35, residual and
 # right-hand-side sums 16, the cross sum of Eq. 1 3.
 FLOP_PER_SAMPLE = 96
+# per sample of a POI's first pass, at the integer start: the samples are
+# pixels (no warp, weights or convolution), only the sums remain
+FLOP_PER_PIXEL_SAMPLE = 19
 # algorithmic bytes per pixel of the precompute kernel: f and g read (1 + 1),
 # gradient (8), float g (4) and BF16 tap quads (8) written
 PRECOMPUTE_BYTES_PER_PX = 22
@@ -324,20 +327,25 @@ def run_gpu(args):
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12
     fp32_basis = (f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                   f"x {peak_mhz:.0f} MHz (nominal max clock)")
-    # passes per POI: one per iteration, plus one at the returned shape for
-    # POIs that did not converge
-    started = (s_out["status0"] == 0)
+    # passes per POI: one per iteration (the first at the integer start reads
+    # pixels), plus one interpolating pass at the returned shape for POIs
+    # that did not converge
+    its = p_out["iters"].to(torch.int64)
+    ran = (s_out["status0"] == 0) & (its >= 1)
     extra = (p_out["status"] != 0).to(torch.int64)
-    passes = int((p_out["iters"].to(torch.int64) + extra)[started].sum().item())
-    samples = passes * SUBSET * SUBSET
+    pixel_samples = int(ran.sum().item()) * SUBSET * SUBSET
+    samples = int(((its - 1) + extra)[ran].sum().item()) * SUBSET * SUBSET
+    sub_flop = FLOP_PER_SAMPLE * samples + FLOP_PER_PIXEL_SAMPLE * pixel_samples
     sub_avg_s = statistics.mean(sub_ms) / 1e3
-    sub_achieved = FLOP_PER_SAMPLE * samples / sub_avg_s / 1e12
+    sub_achieved = sub_flop / sub_avg_s / 1e12
     roofline = {"bound": "alu", "achieved": sub_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": sub_achieved / fp32_peak,
                 "traffic": traffic_of("subpixel_affine1024_traffic.json"),
                 "kernel": f"subpixel_kernel<IC-GN, fp{args.solve_bits} solve>",
                 "peak_basis": fp32_basis, "ms": sub_avg_s * 1e3,
-                "work": f"{FLOP_PER_SAMPLE} flop x {samples} interpolated samples per launch"}
+                "work": (f"{FLOP_PER_SAMPLE} flop x {samples} interpolated samples + "
+                         f"{FLOP_PER_PIXEL_SAMPLE} flop x {pixel_samples} first-pass pixel "
+                         f"samples per launch")}
     # the integer search: algorithmic flops 2 N (2R+1)^2 per POI (padded and
     # wasted MACs not counted)
     search_avg_s = statistics.mean(search_ms) / 1e3
@@ -372,11 +380,11 @@ def run_gpu(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = float(peaks_all.get("hbm_gbs", 6800.0)) * 1e9
     pre_bytes = PRECOMPUTE_BYTES_PER_PX * pair.ref.size
-    t_roof = flops / (peak * 1e12) + FLOP_PER_SAMPLE * samples / (fp32_peak * 1e12) + pre_bytes / hbm
+    t_roof = flops / (peak * 1e12) + sub_flop / (fp32_peak * 1e12) + pre_bytes / hbm
     roofline_path = {"roofline_ms": t_roof * 1e3, "measured_ms": ms_per_step,
                      "frac": t_roof * 1e3 / ms_per_step,
                      "terms": {"search_ms": flops / (peak * 1e12) * 1e3,
-                               "subpixel_ms": FLOP_PER_SAMPLE * samples / (fp32_peak * 1e12) * 1e3,
+                               "subpixel_ms": sub_flop / (fp32_peak * 1e12) * 1e3,
                                "precompute_ms": pre_bytes / hbm * 1e3},
                      "hbm_basis": "measured" if peaks_all else "fallback"}
 
