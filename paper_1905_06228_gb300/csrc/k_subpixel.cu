@@ -472,6 +472,10 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const float ddx = (float)(32 % S), ddy = (float)(32 / S), fM = (float)M, fS = (float)S;
       int off = (lane / S - M) * W + (lane % S - M);
       const int doff = (32 / S) * W + 32 % S, dwrap = W - S;
+      // unrolled so that several samples' loads are in flight (measured:
+      // IC-GN 4 -> 0.627 ms against 0.660 ms not unrolled, FA-NR 2)
+      constexpr int kPixUnroll = FANR ? 2 : 4;
+#pragma unroll kPixUnroll
       for (int i = lane; i < N; i += 32) {
         const float* gp = gb + off;
         float gx = 0.f, gy = 0.f;
