@@ -94,3 +94,34 @@ def test_set_pair_rejects_null_and_bad_sizes():
 
 def test_destroy_null_is_harmless():
     dic.lib().dic_destroy(None)
+
+
+def test_batch_calls_without_a_batch():
+    """Batch entry points check their state on the host: no batch bound ->
+    DIC_ERR_STATE, null handle -> DIC_ERR_ARG (no device work is issued)."""
+    lib = dic.lib()
+    assert lib.dic_set_batch_shape(None, 4, 1) == dic.DIC_ERR_ARG
+    assert lib.dic_run_batch(None, 0, None) == dic.DIC_ERR_ARG
+    assert lib.dic_autotune(None, 0, None, None) == dic.DIC_ERR_ARG
+    h = dic.dic_create(21, 5, 10)
+    try:
+        assert lib.dic_set_batch_shape(h, 4, 1) == dic.DIC_ERR_STATE
+        assert lib.dic_run_batch(h, 0, None) == dic.DIC_ERR_STATE
+        assert lib.dic_autotune(h, 0, None, None) == dic.DIC_ERR_STATE
+        assert lib.dic_batch_pois(h, None, None) == dic.DIC_ERR_STATE
+        assert lib.dic_set_pairs(h, 0, None) == dic.DIC_ERR_ARG
+    finally:
+        dic.dic_destroy(h)
+
+
+def test_form_and_noalloc_argument_checks():
+    lib = dic.lib()
+    h = dic.dic_create(21, 5, 10)
+    try:
+        assert lib.dic_set_form(h, 7) == dic.DIC_ERR_ARG
+        assert lib.dic_set_form(h, dic.DIC_FORM_BF16TC) == dic.DIC_OK
+    finally:
+        dic.dic_destroy(h)
+    # images beyond the static array's limit are refused before any device work
+    args = [16, 16, 1024, 1024, 1024, 21, 5, 10, 0, 1e-3, 50, 32] + [None] * 13
+    assert lib.dic_subpixel_noalloc(*args) == dic.DIC_ERR_ARG
