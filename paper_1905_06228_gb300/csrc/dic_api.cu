@@ -600,6 +600,14 @@ dic_status batch_tc_scratch(dic_t h) {
       cudaMalloc(&b->tc_slots, std::max<size_t>(slots, 1) * sizeof(dic::SlotCand)) !=
           cudaSuccess) {
     cudaGetLastError();
+    // all or nothing: a later call must not find part of the scratch
+    if (b->tc_phase) cudaFree(b->tc_phase);
+    if (b->tc_fbox) cudaFree(b->tc_fbox);
+    if (b->tc_posbox) cudaFree(b->tc_posbox);
+    if (b->tc_slots) cudaFree(b->tc_slots);
+    b->tc_phase = nullptr;
+    b->tc_fbox = b->tc_posbox = nullptr;
+    b->tc_slots = nullptr;
     return fail(h, DIC_ERR_OOM, "cannot allocate tensor-core search scratch for the batch");
   }
   return DIC_OK;
