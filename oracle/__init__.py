@@ -31,6 +31,7 @@ _lib = None
 ST_OK, ST_ZERO_VAR_REF, ST_OUT_OF_BOUNDS, ST_MAX_ITER, ST_NONFINITE, ST_SINGULAR, \
     ST_ZERO_VAR_DEF = range(7)
 ICGN, FANR = 0, 1
+BICUBIC, BILINEAR = 0, 1  # interpolation of g: Keys cubic convolution, or Eq. 5
 
 
 def build(force: bool = False) -> str:
@@ -58,6 +59,12 @@ def _load():
             lib.dico_subpixel.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, dbl, i32,
                                           P, i64, P, P, P, i32, P, P, P, P, P]
             lib.dico_subpixel.restype = i32
+            lib.dico_subpixel_interp.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, i32,
+                                                 dbl, i32, P, i64, P, P, P, i32, P, P, P, P,
+                                                 P]
+            lib.dico_subpixel_interp.restype = i32
+            lib.dico_bilinear.argtypes = [P, i32, i32, i32, dbl, dbl, P, P]
+            lib.dico_bilinear.restype = dbl
             lib.dico_bicubic.argtypes = [P, i32, i32, i32, dbl, dbl, P, P]
             lib.dico_bicubic.restype = dbl
             lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P, P]
@@ -113,7 +120,8 @@ def integer_search(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius:
 
 def subpixel(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
              u0, v0, status0, method: int = ICGN, tol: float = 1e-3, max_iter: int = 50,
-             poi_idx=None, threads: int | None = None, trajectory: bool = False) -> dict:
+             poi_idx=None, threads: int | None = None, trajectory: bool = False,
+             interp: int = BICUBIC) -> dict:
     f = np.ascontiguousarray(f, np.float64)
     g = np.ascontiguousarray(g, np.float64)
     H, W = f.shape
@@ -130,11 +138,11 @@ def subpixel(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
     it = np.zeros(n, np.int32)
     st = np.zeros(n, np.uint8)
     traj = np.zeros((n, max_iter + 1, 6), np.float64) if trajectory else None
-    rc = _load().dico_subpixel(_ptr(f), _ptr(g), W, H, W, subset, step, radius, method,
-                               tol, max_iter, _ptr(idx), n if idx is not None else -1,
-                               _ptr(u0), _ptr(v0), _ptr(status0),
-                               threads or default_threads(), _ptr(p), _ptr(zn), _ptr(it),
-                               _ptr(st), _ptr(traj))
+    rc = _load().dico_subpixel_interp(_ptr(f), _ptr(g), W, H, W, subset, step, radius,
+                                      method, interp, tol, max_iter, _ptr(idx),
+                                      n if idx is not None else -1, _ptr(u0), _ptr(v0),
+                                      _ptr(status0), threads or default_threads(), _ptr(p),
+                                      _ptr(zn), _ptr(it), _ptr(st), _ptr(traj))
     if rc:
         raise ValueError("oracle subpixel failed")
     out = dict(p=p, u=p[:, 0], ux=p[:, 1], uy=p[:, 2], v=p[:, 3], vx=p[:, 4], vy=p[:, 5],
@@ -149,6 +157,15 @@ def bicubic(img: np.ndarray, x: float, y: float) -> tuple[float, float, float]:
     H, W = img.shape
     gx, gy = C.c_double(), C.c_double()
     v = _load().dico_bicubic(_ptr(img), W, H, W, float(x), float(y), C.byref(gx), C.byref(gy))
+    return v, gx.value, gy.value
+
+
+def bilinear(img: np.ndarray, x: float, y: float) -> tuple[float, float, float]:
+    """Eq. 5 at (x, y): value and the gradient of the patch (NaN outside)."""
+    img = np.ascontiguousarray(img, np.float64)
+    H, W = img.shape
+    gx, gy = C.c_double(), C.c_double()
+    v = _load().dico_bilinear(_ptr(img), W, H, W, float(x), float(y), C.byref(gx), C.byref(gy))
     return v, gx.value, gy.value
 
 

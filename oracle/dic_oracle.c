@@ -23,7 +23,8 @@
  *    forward-additive Newton-Raphson algorithm in its Gauss-Newton form
  *    (Table 2).  Grey levels between pixels come from bicubic interpolation
  *    (Section 2.2) with the Keys cubic-convolution kernel, a = -0.5, on the
- *    4x4 neighbourhood, evaluated straight from the pixels (no look-up table).
+ *    4x4 neighbourhood, evaluated straight from the pixels (no look-up table),
+ *    or from the bilinear interpolation of Eq. 5.
  *  - The summed ZNSSD of every subset at given shape parameters and its
  *    gradient with respect to the deformed-image pixels and the parameters
  *    (hand-derived adjoint, FP64).
@@ -208,6 +209,41 @@ double dico_bicubic(const double *img, int W, int H, int pitch, double x, double
   return interp(img, pitch, x, y, gx, gy);
 }
 
+/* ------------------------------------------------------ bilinear (Eq. 5) */
+/* G(x*, y*) = a00 + a10 x' + a01 y' + a11 x'y' (Eq. 5, Section 2.2), with
+ * x', y' the distances along x and y from the next integer pixel position
+ * (read: the pixel (floor x*, floor y*)) and the four coefficients from the
+ * linear system that makes G equal the grey levels of the four surrounding
+ * pixels, G(0,0) = g00, G(1,0) = g10, G(0,1) = g01, G(1,1) = g11, solved by
+ * substitution.  The gradient is that of the same patch. */
+static double interp_bilinear(const double *img, int pitch, double x, double y, double *gx,
+                              double *gy) {
+  double fx0 = floor(x), fy0 = floor(y);
+  int ix = (int)fx0, iy = (int)fy0;
+  double xp = x - fx0, yp = y - fy0;
+  const double *r = img + (int64_t)iy * pitch + ix;
+  double g00 = r[0], g10 = r[1], g01 = r[pitch], g11 = r[pitch + 1];
+  double a00 = g00;
+  double a10 = g10 - a00;
+  double a01 = g01 - a00;
+  double a11 = g11 - a00 - a10 - a01;
+  if (gx) *gx = a10 + a11 * yp;
+  if (gy) *gy = a01 + a11 * xp;
+  return a00 + a10 * xp + a01 * yp + a11 * xp * yp;
+}
+
+double dico_bilinear(const double *img, int W, int H, int pitch, double x, double y,
+                     double *gx, double *gy) {
+  if (!(x >= 0.0 && x < W - 1.0 && y >= 0.0 && y < H - 1.0)) return NAN;
+  return interp_bilinear(img, pitch, x, y, gx, gy);
+}
+
+/* interpolation of g: 0 bicubic (Keys), 1 bilinear (Eq. 5) */
+static double interp_g(int mode, const double *img, int pitch, double x, double y,
+                       double *gx, double *gy) {
+  return mode ? interp_bilinear(img, pitch, x, y, gx, gy) : interp(img, pitch, x, y, gx, gy);
+}
+
 /* ------------------------------------------------------------ 6x6 solve */
 /* Cholesky factorisation of a symmetric 6x6 matrix in place (lower). */
 static int chol6(double A[6][6]) {
@@ -283,15 +319,15 @@ static double dp_norm(const double dp[6], int M) {
 /* g at every warped subset point; returns mean and sqrt(sum (g-gbar)^2).
  * Optional derivative outputs. */
 static void sample_subset(const double *g, int pitch, const double p[6], int x0, int y0,
-                          int M, double *gv, double *gxv, double *gyv, double *gbar,
-                          double *dg) {
+                          int M, int mode, double *gv, double *gxv, double *gyv,
+                          double *gbar, double *dg) {
   int S = 2 * M + 1, N = S * S;
   double s = 0;
   for (int i = 0; i < N; ++i) {
     int dx = i % S - M, dy = i / S - M;
     double x, y;
     warp_pt(p, x0, y0, dx, dy, &x, &y);
-    gv[i] = interp(g, pitch, x, y, gxv ? &gxv[i] : NULL, gyv ? &gyv[i] : NULL);
+    gv[i] = interp_g(mode, g, pitch, x, y, gxv ? &gxv[i] : NULL, gyv ? &gyv[i] : NULL);
     s += gv[i];
   }
   double m = s / N, q = 0;
@@ -302,7 +338,7 @@ static void sample_subset(const double *g, int pitch, const double p[6], int x0,
 
 /* ------------------------------------------------------------- sub-pixel */
 static void subpixel_one(const double *f, const double *g, int W, int H, int pitch,
-                         int x0, int y0, int M, int method, double tol, int max_iter,
+                         int x0, int y0, int M, int method, int mode, double tol, int max_iter,
                          int32_t iu0, int32_t iv0, uint8_t st0, double *pout,
                          double *zncc, int32_t *iters, uint8_t *status, double *traj) {
   const int S = 2 * M + 1, N = S * S;
@@ -357,7 +393,7 @@ static void subpixel_one(const double *f, const double *g, int W, int H, int pit
     }
     for (int it = 1; it <= max_iter; ++it) {
       double gbar, dg;
-      sample_subset(g, pitch, p, x0, y0, M, gv, NULL, NULL, &gbar, &dg);
+      sample_subset(g, pitch, p, x0, y0, M, mode, gv, NULL, NULL, &gbar, &dg);
       if (!(dg > 0.0) || !isfinite(dg)) {
         st = ST_NONFINITE;
         break;
@@ -397,7 +433,7 @@ static void subpixel_one(const double *f, const double *g, int W, int H, int pit
     /* ---------------- FA-NR (Gauss-Newton Hessian, rebuilt each step) --- */
     for (int it = 1; it <= max_iter; ++it) {
       double gbar, dg;
-      sample_subset(g, pitch, p, x0, y0, M, gv, gxv, gyv, &gbar, &dg);
+      sample_subset(g, pitch, p, x0, y0, M, mode, gv, gxv, gyv, &gbar, &dg);
       if (!(dg > 0.0) || !isfinite(dg)) {
         st = ST_NONFINITE;
         break;
@@ -451,7 +487,7 @@ final:
   } else {
     /* Eq. 1 at the returned shape, interpolated target grey levels */
     double gbar, dg;
-    sample_subset(g, pitch, p, x0, y0, M, gv, NULL, NULL, &gbar, &dg);
+    sample_subset(g, pitch, p, x0, y0, M, mode, gv, NULL, NULL, &gbar, &dg);
     double s = 0;
     for (int i = 0; i < N; ++i) s += fc[i] * (gv[i] - gbar);
     *zncc = (dg > 0.0) ? s / (df * dg) : 0.0;
@@ -459,14 +495,16 @@ final:
   free(fc);
 }
 
-int dico_subpixel(const double *f, const double *g, int W, int H, int pitch, int subset,
-                  int step, int R, int method, double tol, int max_iter,
-                  const int64_t *poi_idx, int64_t n_idx, const int32_t *u0,
-                  const int32_t *v0, const uint8_t *st0, int nthreads, double *p_out,
-                  double *zncc, int32_t *iters, uint8_t *status, double *traj) {
+int dico_subpixel_interp(const double *f, const double *g, int W, int H, int pitch,
+                         int subset, int step, int R, int method, int mode, double tol,
+                         int max_iter, const int64_t *poi_idx, int64_t n_idx,
+                         const int32_t *u0, const int32_t *v0, const uint8_t *st0,
+                         int nthreads, double *p_out, double *zncc, int32_t *iters,
+                         uint8_t *status, double *traj) {
   int nx, ny;
   if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
   if (method != 0 && method != 1) return -1;
+  if (mode != 0 && mode != 1) return -1;
   if (max_iter < 1) return -1;
   const int M = subset / 2;
   const int64_t n = poi_idx ? n_idx : (int64_t)nx * ny;
@@ -476,11 +514,21 @@ int dico_subpixel(const double *f, const double *g, int W, int H, int pitch, int
     int64_t poi = poi_idx ? poi_idx[k] : k;
     int x0, y0;
     poi_centre(poi, nx, M, R, step, &x0, &y0);
-    subpixel_one(f, g, W, H, pitch, x0, y0, M, method, tol, max_iter, u0[k], v0[k],
+    subpixel_one(f, g, W, H, pitch, x0, y0, M, method, mode, tol, max_iter, u0[k], v0[k],
                  st0[k], &p_out[k * 6], &zncc[k], &iters[k], &status[k],
                  traj ? &traj[k * (int64_t)(max_iter + 1) * 6] : NULL);
   }
   return 0;
+}
+
+int dico_subpixel(const double *f, const double *g, int W, int H, int pitch, int subset,
+                  int step, int R, int method, double tol, int max_iter,
+                  const int64_t *poi_idx, int64_t n_idx, const int32_t *u0,
+                  const int32_t *v0, const uint8_t *st0, int nthreads, double *p_out,
+                  double *zncc, int32_t *iters, uint8_t *status, double *traj) {
+  return dico_subpixel_interp(f, g, W, H, pitch, subset, step, R, method, 0, tol, max_iter,
+                              poi_idx, n_idx, u0, v0, st0, nthreads, p_out, zncc, iters,
+                              status, traj);
 }
 
 /* ------------------------------------------------------- ZNSSD + adjoint */
@@ -522,7 +570,7 @@ int dico_znssd(const double *f, const double *g, int W, int H, int pitch, int su
       q += fc[i] * fc[i];
     }
     double df = sqrt(q), gbar, dg;
-    sample_subset(g, pitch, pk, x0, y0, M, gv, gxv, gyv, &gbar, &dg);
+    sample_subset(g, pitch, pk, x0, y0, M, 0, gv, gxv, gyv, &gbar, &dg);
     if (!(df > 0) || !(dg > 0)) continue;
     double C = 0, Lk = 0;
     for (int i = 0; i < N; ++i) {

@@ -179,12 +179,51 @@ def test_bicubic_does_not_reproduce_cubics():
     assert abs(v - 0.01 * 5.25 ** 3) > 1e-4
 
 
+# ------------------------------------------------------ bilinear (Eq. 5)
+def test_bilinear_nodes_and_bilinear_functions():
+    """Eq. 5 interpolates the four surrounding pixels, so it equals the
+    pixel at every node and reproduces any function a + b x + c y + d x y
+    exactly, value and gradient (b + d y, c + d x), on every cell."""
+    rng = np.random.default_rng(2)
+    img = rng.uniform(0, 255, (10, 11))
+    for y in range(0, 9):
+        for x in range(0, 10):
+            assert oracle.bilinear(img, x, y)[0] == img[y, x]
+    yy, xx = np.mgrid[0:12, 0:12].astype(np.float64)
+    c = [3.0, 0.7, -1.1, 0.09]
+    b = lambda x, y: c[0] + c[1] * x + c[2] * y + c[3] * x * y
+    img = b(xx, yy)
+    for _ in range(200):
+        x, y = rng.uniform(0, 10.999, 2)
+        v, gx, gy = oracle.bilinear(img, x, y)
+        assert v == pytest.approx(b(x, y), abs=1e-11)
+        assert gx == pytest.approx(c[1] + c[3] * y, abs=1e-11)
+        assert gy == pytest.approx(c[2] + c[3] * x, abs=1e-11)
+
+
+def test_bilinear_is_continuous_and_not_quadratic():
+    """Across a cell boundary the value is continuous (the two patches
+    agree on their common edge); a quadratic is not reproduced, which tells
+    Eq. 5 apart from the bicubic kernel: x^2 between the nodes 2 and 3 is the
+    chord, 6.5 at x = 2.5, not 6.25."""
+    rng = np.random.default_rng(3)
+    img = rng.uniform(0, 255, (8, 8))
+    for y in (1.3, 2.7, 4.0):
+        left = oracle.bilinear(img, 3.0 - 1e-9, y)[0]
+        right = oracle.bilinear(img, 3.0, y)[0]
+        assert left == pytest.approx(right, abs=1e-6)
+    yy, xx = np.mgrid[0:8, 0:8].astype(np.float64)
+    assert oracle.bilinear(xx ** 2, 2.5, 4.0)[0] == pytest.approx(6.5, abs=1e-12)
+    assert oracle.bicubic(xx ** 2, 2.5, 4.0)[0] == pytest.approx(6.25, abs=1e-12)
+
+
 # --------------------------------------------------------------- sub-pixel
+@pytest.mark.parametrize("interp", [oracle.BICUBIC, oracle.BILINEAR])
 @pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
 @pytest.mark.parametrize("du,dv", [(2, -1), (-3, 2)])
-def test_subpixel_exact_integer_shift_fixed_point(method, du, dv):
-    """g(x + du, y + dv) = f(x, y) exactly.  The bicubic interpolant equals
-    the pixels at integer nodes, so p = (du, 0, 0, dv, 0, 0) makes every
+def test_subpixel_exact_integer_shift_fixed_point(method, du, dv, interp):
+    """g(x + du, y + dv) = f(x, y) exactly.  Both interpolants equal the
+    pixels at integer nodes, so p = (du, 0, 0, dv, 0, 0) makes every
     residual zero: it is an exact fixed point.  Started one pixel away in
     each direction, the iteration must come back to it (through sub-pixel
     positions) to round-off, with C = 1."""
@@ -195,7 +234,7 @@ def test_subpixel_exact_integer_shift_fixed_point(method, du, dv):
     n = int(np.prod(oracle.grid(76, 76, subset, step, r)))
     z = np.zeros(n, np.int32)
     s = oracle.subpixel(f, g, subset, step, r, z + du + 1, z + dv - 1, np.zeros(n, np.uint8),
-                        method=method, tol=1e-11, max_iter=100)
+                        method=method, tol=1e-11, max_iter=100, interp=interp)
     ok = s["status"] == oracle.ST_OK
     assert ok.mean() > 0.9
     want = np.array([du, 0, 0, dv, 0, 0], np.float64)
@@ -220,6 +259,27 @@ def test_subpixel_rigid_speckle_accuracy(rigid256, method):
     grads = s["p"][:, [1, 2, 4, 5]]
     assert np.abs(grads).mean() < 2e-3 and np.abs(grads).max() < 1e-2
     assert s["zncc"].min() > 0.99
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_subpixel_rigid_speckle_accuracy_bilinear(rigid256, method):
+    """The same field with the bilinear interpolation of Eq. 5: within the
+    paper's guaranteed 0.1 px (Section 3), and measurably less accurate than
+    bicubic on the same POIs (the interpolation error the paper trades for
+    computation, Section 2.2)."""
+    p = rigid256
+    r = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
+    kw = dict(method=method)
+    s1 = oracle.subpixel(p.ref, p.defm, p.subset, p.step, p.radius, r["u0"], r["v0"],
+                         r["status"], interp=oracle.BILINEAR, **kw)
+    s3 = oracle.subpixel(p.ref, p.defm, p.subset, p.step, p.radius, r["u0"], r["v0"],
+                         r["status"], **kw)
+    assert (s1["status"] == oracle.ST_OK).all()
+    e1 = np.hypot(s1["u"] - 3.4, s1["v"] + 2.7)
+    e3 = np.hypot(s3["u"] - 3.4, s3["v"] + 2.7)
+    assert e1.max() < 0.1 and e1.mean() < 0.02
+    assert e1.mean() > e3.mean()
+    assert s1["zncc"].min() > 0.99
 
 
 def test_subpixel_affine_speckle_accuracy(affine1024):
