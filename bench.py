@@ -289,6 +289,14 @@ def run_gpu(args):
     fanr_value = convn * len(stn) / (sum(stn) / 1e3)
     fanr_sub_ms = statistics.mean(sen[1])
     dnr.close()
+    # the chosen form with the bilinear interpolation of Eq. 5
+    dbl = make(args.solve_bits, args.form)
+    dic.dic_set_interpolation(dbl.h, dic.DIC_INTERP_BILINEAR)
+    dbl.set_pair(ref_d, def_d)
+    stb, seb, convb, _, _ = timed_loop(dbl, max(10, args.steps // 4), 3)
+    bil_value = convb * len(stb) / (sum(stb) / 1e3)
+    bil_sub_ms = statistics.mean(seb[1])
+    dbl.close()
 
     # e2e through the public call with host buffers: H2D of both images,
     # the three kernels, D2H of every per-POI output, all inside the events
@@ -415,6 +423,9 @@ def run_gpu(args):
                           "chosen_fanr": {"method": "FA-NR (Gauss-Newton form)",
                                           "solve": f"fp{args.solve_bits}",
                                           "value": fanr_value, "subpixel_ms": fanr_sub_ms},
+                          "chosen_bilinear": {"interpolation": "bilinear (Eq. 5)",
+                                              "solve": f"fp{args.solve_bits}",
+                                              "value": bil_value, "subpixel_ms": bil_sub_ms},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
                                          "value": plain_value}},
                 "converged_fraction": conv / n, "wall_s_timed": wall}

@@ -62,9 +62,15 @@ typedef enum { DIC_ICGN = 0, DIC_FANR = 1 } dic_method;
 typedef enum {
   DIC_FORM_PLAIN_FP32 = 0, /* FP32 FMA correlation per POI, exact integer sums  */
   DIC_FORM_BF16TC = 1      /* BF16 tensor-core correlation (tcgen05) across POIs,
-                              exact FP32 accumulation, exact re-rank of the top
-                              four candidates per POI                           */
+                              exact FP32 accumulation, exact comparison of the
+                              near-tied candidates of every tile and POI       */
 } dic_form;
+
+/* Interpolation of the deformed image between pixels (Section 2.2). */
+typedef enum {
+  DIC_INTERP_BICUBIC = 0,  /* Keys cubic convolution, a = -1/2, 4x4 pixels      */
+  DIC_INTERP_BILINEAR = 1  /* Eq. 5: a00 + a10 x' + a01 y' + a11 x'y' on 2x2    */
+} dic_interp;
 
 /* Per-POI status codes written by dic_integer_search / dic_subpixel. */
 enum {
@@ -103,25 +109,40 @@ const char *dic_last_error(dic_t h);
 /* Stream for all later work (a cudaStream_t passed as void*; NULL = default). */
 dic_status dic_set_stream(dic_t h, void *cuda_stream);
 
-/* Integer-search arithmetic form (see dic_form).  The tensor-core form needs
- * at most 256 POIs whose search windows meet a 16x8 block of positions
- * ((2R+16)/step + 1)*((2R+8)/step + 1) <= 256); dic_integer_search returns
- * DIC_ERR_UNSUPPORTED otherwise.  It allocates per-POI scratch (a BF16 copy
- * of every subset, 2*S*round16(S) bytes per POI) on first use. */
+/* Integer-search arithmetic form (see dic_form).  The tensor-core form splits
+ * the POIs whose search windows meet a 16x8 block of positions into row
+ * chunks of at most 256 (and 512 TMEM columns of accumulators); it needs one
+ * row of that block, (2R+8)/step + 1 POIs, to fit, and returns
+ * DIC_ERR_UNSUPPORTED from dic_integer_search otherwise.  It allocates
+ * scratch on first use: a BF16 copy of every subset (2*S*TWK bytes per POI,
+ * TWK = 16, 32 or 64 >= S), eight shifted BF16 copies of g (16 bytes per
+ * pixel), box-sum maps and one 24-byte winner slot per (position tile,
+ * POI). */
 dic_status dic_set_form(dic_t h, dic_form form);
 
-/* Precision of the per-POI 6x6 Gauss-Newton solve: 32 (FP32) or 64 (FP64
- * Cholesky).  The per-point work is FP32 either way.  Default 32. */
+/* Precision of the per-POI 6x6 Gauss-Newton solve: 32 (FP32) or 64 (FP64):
+ * the matrix is inverted in that precision (symmetric Gauss-Jordan sweep
+ * on its unit-diagonal scaling) and multiplied by the right-hand side.  The
+ * per-point work is FP32 either way.  Default 32. */
 dic_status dic_set_solve_precision(dic_t h, int bits);
 
+/* Interpolation of g in dic_subpixel (Section 2.2): DIC_INTERP_BICUBIC
+ * (default) or DIC_INTERP_BILINEAR (Eq. 5; FA-NR then takes the gradient of
+ * the bilinear patch the sample falls in, IC-GN keeps the central-difference
+ * gradients of f).  dic_run_batch, dic_znssd / dic_backward and
+ * dic_subpixel_noalloc interpolate bicubically; dic_run_batch returns
+ * DIC_ERR_UNSUPPORTED with bilinear set.  DIC_ERR_ARG for other values. */
+dic_status dic_set_interpolation(dic_t h, dic_interp interp);
+
 /* Bind a reference/deformed image pair (device pointers, borrowed) and
- * enqueue the precompute kernel: central-difference gradients of f and the
- * 16 bicubic coefficients of every 1x1 cell of g (Section 2.2's bicubic
- * interpolation with the look-up table of its ref. [18]).
+ * enqueue the precompute kernel: central-difference gradients of f, g as
+ * float, and g's BF16 tap quads (the four taps of a bicubic stencil row per
+ * pixel; Section 2.2's interpolation evaluates its weights per sample
+ * instead of the look-up table of its ref. [18]).
  *   width, height  >= 4 pixels each
  *   pitch_bytes    >= width; both pointers 16-byte aligned and pitch a
  *                  multiple of 16 enable TMA staging, otherwise plain loads
- * Allocates scratch of 72 bytes per pixel on first use or growth
+ * Allocates scratch of 20 bytes per pixel on first use or growth
  * (DIC_ERR_OOM on failure). */
 dic_status dic_set_pair(dic_t h, const uint8_t *ref_dev, const uint8_t *def_dev,
                         int width, int height, int pitch_bytes);

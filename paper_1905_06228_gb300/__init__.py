@@ -23,6 +23,7 @@ DIC_OK, DIC_ERR_ARG, DIC_ERR_CUDA, DIC_ERR_OOM, DIC_ERR_STATE, DIC_ERR_TIMEOUT, 
     DIC_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 DIC_ICGN, DIC_FANR = 0, 1
 DIC_FORM_PLAIN_FP32, DIC_FORM_BF16TC = 0, 1
+DIC_INTERP_BICUBIC, DIC_INTERP_BILINEAR = 0, 1
 POI_OK, POI_ZERO_VAR_REF, POI_OUT_OF_BOUNDS, POI_MAX_ITER, POI_NONFINITE, POI_SINGULAR, \
     POI_ZERO_VAR_DEF = range(7)
 
@@ -56,6 +57,7 @@ SIGNATURES = {
     "dic_set_stream": (i32, [P, P]),
     "dic_set_form": (i32, [P, i32]),
     "dic_set_solve_precision": (i32, [P, i32]),
+    "dic_set_interpolation": (i32, [P, i32]),
     "dic_set_pair": (i32, [P, P, P, i32, i32, i32]),
     "dic_set_pair_f32": (i32, [P, P, P, i32, i32, i32]),
     "dic_num_pois": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
@@ -150,6 +152,10 @@ def dic_set_form(h, form: int) -> None:
 
 def dic_set_solve_precision(h, bits: int) -> None:
     _check(lib().dic_set_solve_precision(h, bits), h)
+
+
+def dic_set_interpolation(h, interp: int) -> None:
+    _check(lib().dic_set_interpolation(h, interp), h)
 
 
 def dic_set_pair(h, ref, defm, width: int | None = None, height: int | None = None,

@@ -211,6 +211,14 @@ dic_status dic_set_solve_precision(dic_t h, int bits) {
   return DIC_OK;
 }
 
+dic_status dic_set_interpolation(dic_t h, dic_interp interp) {
+  if (!h) return DIC_ERR_ARG;
+  if (interp != DIC_INTERP_BICUBIC && interp != DIC_INTERP_BILINEAR)
+    return fail(h, DIC_ERR_ARG, "unknown interpolation %d", (int)interp);
+  h->interp = interp;
+  return DIC_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -492,7 +500,8 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int
   p.zncc = zncc;
   p.iters = iters;
   p.status = status;
-  cudaError_t e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, h->stream);
+  cudaError_t e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, h->stream,
+                                       h->interp == DIC_INTERP_BILINEAR);
   if (e != cudaSuccess) return cuda_fail(h, e, "subpixel launch");
   return DIC_OK;
 }
@@ -870,6 +879,8 @@ dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out* out) {
   if (method != DIC_ICGN && method != DIC_FANR) return fail(h, DIC_ERR_ARG, "unknown method");
   if (!out) return fail(h, DIC_ERR_ARG, "null output descriptor");
   dic::BatchState* b = h->batch;
+  if (h->interp != DIC_INTERP_BICUBIC)
+    return fail(h, DIC_ERR_UNSUPPORTED, "the batch form interpolates bicubically only");
   if (b->total == 0) return DIC_OK;
   const dic_batch_out& o = *out;
   if (!o.u0 || !o.v0 || !o.zncc0 || !o.status0 || !o.u || !o.v || !o.ux || !o.uy || !o.vx ||

@@ -204,6 +204,25 @@ struct PtWalk2 {
   }
 };
 
+// Bilinear grey level (Eq. 5, Section 2.2) at fractional offsets (x', y') =
+// (tx, ty) of the cell whose top-left pixel is `cell`:
+//   G = a00 + a10 x' + a01 y' + a11 x' y',
+// the coefficients solving the linear system of the four surrounding pixels
+// (a00 = p00, a10 = p10 - p00, a01 = p01 - p00, a11 = p11 - p10 - p01 + p00);
+// with DERIV also the gradient of that patch (a10 + a11 y', a01 + a11 x').
+template <bool DERIV>
+__device__ __forceinline__ float bilinear(const float* __restrict__ img, int W, size_t cell,
+                                          float tx, float ty, float& gx, float& gy) {
+  const float p00 = __ldg(img + cell), p10 = __ldg(img + cell + 1);
+  const float p01 = __ldg(img + cell + W), p11 = __ldg(img + cell + W + 1);
+  const float a10 = p10 - p00, a01 = p01 - p00, a11 = (p11 - p10) - a01;
+  if (DERIV) {
+    gx = fmaf(a11, ty, a10);
+    gy = fmaf(a11, tx, a01);
+  }
+  return fmaf(fmaf(a11, tx, a01), ty, fmaf(a10, tx, p00));
+}
+
 // Subset point walk of one lane: points i = lane, lane+32, ... in row-major
 // (dy outer) order, with (dx, dy) advanced incrementally.
 struct PtWalk {

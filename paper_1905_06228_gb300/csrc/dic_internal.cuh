@@ -156,8 +156,9 @@ cudaError_t launch_subpixel_batch(const SubpixelParams* jobs, const int64_t* off
                                   unsigned long long* counter, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchParams& p, const CUtensorMap* tm_ref,
                           const CUtensorMap* tm_def, cudaStream_t st);
+// bilinear: 1 for the bilinear interpolation of Eq. 5, 0 for bicubic (Keys)
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
-                            cudaStream_t st);
+                            cudaStream_t st, int bilinear = 0);
 
 // Size of the byte box that TMA stages for a subset / search window.
 __host__ __device__ inline int tma_box_width(int span) { return ((span + 15 + 15) / 16) * 16; }
@@ -219,6 +220,7 @@ struct dic_s {
   float tol = 0.f;
   int form = DIC_FORM_PLAIN_FP32;
   int solve_bits = 32;
+  int interp = DIC_INTERP_BICUBIC;
   cudaStream_t stream = nullptr;
 
   bool have_pair = false;

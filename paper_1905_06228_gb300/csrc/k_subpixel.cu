@@ -265,8 +265,9 @@ __host__ __device__ inline size_t warp_smem_bytes(int N, size_t point_bytes) {
   return ((size_t)N * point_bytes + 15) / 16 * 16 + 36 * sizeof(double) + 12 * sizeof(float);
 }
 
-// Refinement of one POI by one warp; wsm is the warp's shared block.
-template <bool FANR, typename TS, typename TP>
+// Refinement of one POI by one warp; wsm is the warp's shared block.  BIL:
+// bilinear interpolation of g (Eq. 5) instead of bicubic.
+template <bool FANR, typename TS, typename TP, bool BIL = false>
 __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t poi, int lane,
                                              unsigned char* wsm) {
   using PS = PointStore<TP>;
@@ -466,7 +467,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       // exactly (0, 1, 0, 0) and their derivatives (-1/2, 0, 1/2, 0), so the
       // interpolant is the pixel and its gradient the central differences --
       // bitwise what the interpolating path below computes, from one load
-      // per sample (three for FA-NR).  The walk matches PtWalk2's.
+      // per sample (five for FA-NR).  With bilinear interpolation the patch
+      // at a pixel gives the pixel and the forward differences (a10, a01).
+      // The walk matches PtWalk2's.
       const float* gb = p.gimg + (size_t)(y0 + (int)prm[3]) * W + (x0 + (int)prm[0]);
       float2 DX = dup2((float)(lane % S - M)), DY = dup2((float)(lane / S - M));
       const float ddx = (float)(32 % S), ddy = (float)(32 / S), fM = (float)M, fS = (float)S;
@@ -479,7 +482,10 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       for (int i = lane; i < N; i += 32) {
         const float* gp = gb + off;
         float gx = 0.f, gy = 0.f;
-        if (FANR) {
+        if (FANR && BIL) {
+          gx = __ldg(gp + 1) - __ldg(gp);
+          gy = __ldg(gp + W) - __ldg(gp);
+        } else if (FANR) {
           gx = fmaf(0.5f, __ldg(gp + 1), -0.5f * __ldg(gp - 1));
           gy = fmaf(0.5f, __ldg(gp + W), -0.5f * __ldg(gp - W));
         }
@@ -502,7 +508,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
         float gx = 0.f, gy = 0.f;
         const size_t cell = wa.locate(w.DX, w.DY, W, H, t);
         float g;
-        if (FANR && kQuads)
+        if (BIL)
+          g = bilinear<FANR>(p.gimg, W, cell, t.x, t.y, gx, gy);
+        else if (FANR && kQuads)
           g = bicubic_q_grad(p.gq, W, cell, t.x, t.y, gx, gy);
         else if (FANR)
           g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
@@ -634,7 +642,8 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     for (int i = lane; i < N; i += 32, w.next()) {
       float tx, ty, gx, gy;
       const size_t cell = locate(prm, w.dx, w.dy, x0, y0, W, H, tx, ty);
-      const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
+      const float d = (BIL ? bilinear<false>(p.gimg, W, cell, tx, ty, gx, gy)
+                           : bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy)) - c;
       float2 gr;
       float f;
       PS::unpack(spt[i], gr, f);
@@ -654,7 +663,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 }
 
 // One warp per POI of one pair.
-template <bool FANR, typename TS, typename TP>
+template <bool FANR, typename TS, typename TP, bool BIL>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, FANR ? DIC_SUB_MINB_NR : DIC_SUB_MINB)
 subpixel_kernel(const SubpixelParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -662,7 +671,7 @@ subpixel_kernel(const SubpixelParams p) {
   const int64_t poi = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
   if (poi >= p.n_pois) return;
   const size_t wb = warp_smem_bytes(p.S * p.S, sizeof(typename PointStore<TP>::T));
-  subpixel_poi<FANR, TS, TP>(p, poi, lane, smem + (size_t)wid * wb);
+  subpixel_poi<FANR, TS, TP, BIL>(p, poi, lane, smem + (size_t)wid * wb);
 }
 
 // Persistent form over many pairs: every warp repeatedly takes the next POI
@@ -701,7 +710,7 @@ subpixel_batch_kernel(const SubpixelParams* __restrict__ jobs,
   }
 }
 
-template <bool FANR, typename TS, typename TP>
+template <bool FANR, typename TS, typename TP, bool BIL>
 cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
   // kWarpsPerCta warps per CTA, fewer where the subset's shared memory
   // would not fit (large subsets)
@@ -713,12 +722,12 @@ cudaError_t launch_one(const SubpixelParams& p, cudaStream_t st) {
   if (smem > 48 * 1024) {
     // the limit, not this launch's size: a graph may hold launches of
     // several subset sizes, each checked against the attribute when it runs
-    cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS, TP>,
+    cudaError_t e = cudaFuncSetAttribute(subpixel_kernel<FANR, TS, TP, BIL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
   const unsigned grid = (unsigned)((p.n_pois + wpc - 1) / wpc);
-  subpixel_kernel<FANR, TS, TP><<<grid, 32 * wpc, smem, st>>>(p);
+  subpixel_kernel<FANR, TS, TP, BIL><<<grid, 32 * wpc, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -773,22 +782,28 @@ cudaError_t launch_subpixel_batch(const SubpixelParams* jobs, const int64_t* off
                                                     grid, st);
 }
 
-cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
-                            cudaStream_t st) {
-  if (p.n_pois == 0) return cudaSuccess;
-  if (!p.ref_f32 && !p.gq) return cudaErrorInvalidValue;  // 8-bit pairs need the tap quads
+template <bool BIL>
+cudaError_t launch_interp(const SubpixelParams& p, int method, int solve_fp64, cudaStream_t st) {
   if (p.ref_f32) {
     if (method == DIC_ICGN)
-      return solve_fp64 ? launch_one<false, double, float>(p, st)
-                        : launch_one<false, float, float>(p, st);
-    return solve_fp64 ? launch_one<true, double, float>(p, st)
-                      : launch_one<true, float, float>(p, st);
+      return solve_fp64 ? launch_one<false, double, float, BIL>(p, st)
+                        : launch_one<false, float, float, BIL>(p, st);
+    return solve_fp64 ? launch_one<true, double, float, BIL>(p, st)
+                      : launch_one<true, float, float, BIL>(p, st);
   }
   if (method == DIC_ICGN)
-    return solve_fp64 ? launch_one<false, double, uint8_t>(p, st)
-                      : launch_one<false, float, uint8_t>(p, st);
-  return solve_fp64 ? launch_one<true, double, uint8_t>(p, st)
-                    : launch_one<true, float, uint8_t>(p, st);
+    return solve_fp64 ? launch_one<false, double, uint8_t, BIL>(p, st)
+                      : launch_one<false, float, uint8_t, BIL>(p, st);
+  return solve_fp64 ? launch_one<true, double, uint8_t, BIL>(p, st)
+                    : launch_one<true, float, uint8_t, BIL>(p, st);
+}
+
+cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
+                            cudaStream_t st, int bilinear) {
+  if (p.n_pois == 0) return cudaSuccess;
+  if (!p.ref_f32 && !p.gq) return cudaErrorInvalidValue;  // 8-bit pairs need the tap quads
+  return bilinear ? launch_interp<true>(p, method, solve_fp64, st)
+                  : launch_interp<false>(p, method, solve_fp64, st);
 }
 
 }  // namespace dic

@@ -16,7 +16,7 @@ NAMES = ("u", "ux", "uy", "v", "vx", "vy")
 def run_gpu(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
             method: int = 0, solve_bits: int = 32, tol: float = 1e-3, max_iter: int = 50,
             device: str = "cuda:0", pitch_pad: int = 0, subpixel: bool = True,
-            form: int = 0) -> dict:
+            form: int = 0, interp: int = 0) -> dict:
     import torch
 
     import paper_1905_06228_gb300 as dic
@@ -38,6 +38,8 @@ def run_gpu(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
             dic.dic_set_solve_precision(h, solve_bits)
         if form:
             dic.dic_set_form(h, form)
+        if interp:
+            dic.dic_set_interpolation(h, interp)
         dic.dic_set_pair(h, tf, tg, W, H, pitch)
         n, nx, ny = dic.dic_num_pois(h)
         out = {"n": n, "nx": nx, "ny": ny}
@@ -73,14 +75,15 @@ def compare_search(gpu: dict, ref: dict, idx=None) -> None:
 
 def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method: int,
                      tol: float = 1e-3, max_iter: int = 50, idx=None,
-                     min_iter_agreement: float = 0.9, min_compared: float = 0.0) -> dict:
+                     min_iter_agreement: float = 0.9, min_compared: float = 0.0,
+                     interp: int = 0) -> dict:
     """Shape parameters of every POI against the oracle's iterate at the
     GPU's own iteration count (the stop test can fall on either side of the
     tolerance in FP32 versus FP64)."""
     sel = np.arange(len(gpu["u"])) if idx is None else np.asarray(idx)
     ref = oracle.subpixel(f, g, subset, step, radius, start["u0"], start["v0"], start["status"],
                           method=method, tol=tol, max_iter=max_iter, poi_idx=idx,
-                          trajectory=True)
+                          trajectory=True, interp=interp)
     gp = gpu["p"][sel]
     git = gpu["iters"][sel]
     gst = gpu["status"][sel]
@@ -98,7 +101,8 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
             sub = oracle.subpixel(f, g, subset, step, radius, start["u0"][rows],
                                   start["v0"][rows], start["status"][rows], method=method,
                                   tol=0.0 + 1e-300, max_iter=int(k),
-                                  poi_idx=(sel[rows] if idx is not None else rows))
+                                  poi_idx=(sel[rows] if idx is not None else rows),
+                                  interp=interp)
             want[rows] = sub["p"]
     err = np.abs(gp - want)
     # shapes are compared where both sides converged; a POI that ran to the

@@ -62,6 +62,58 @@ def test_affine1024_sampled(affine1024, method, solve_bits):
     assert (gpu["status"] == 0).mean() > 0.99
 
 
+# ------------------------------------------ bilinear interpolation (Eq. 5)
+@pytest.mark.parametrize("method", [0, 1])
+def test_bilinear_rigid256_full(rigid256, method):
+    """Sub-pixel refinement over the bilinear interpolation of Eq. 5
+    against the oracle with the same interpolation, every POI."""
+    p = rigid256
+    gpu = run_gpu(p.ref, p.defm, p.subset, p.step, p.radius, method=method, solve_bits=64,
+                  interp=1)
+    ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
+    compare_search(gpu, ref)
+    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method,
+                          min_compared=0.99, interp=oracle.BILINEAR)
+    print(st)
+    assert np.abs(gpu["u"] - 3.4).max() < 0.1 and np.abs(gpu["v"] + 2.7).max() < 0.1
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_bilinear_affine1024_sampled(affine1024, method):
+    p = affine1024
+    gpu = run_gpu(p.ref, p.defm, p.subset, p.step, p.radius, method=method, solve_bits=64,
+                  form=1, interp=1)
+    idx = np.sort(np.random.default_rng(12).choice(gpu["n"], 600, replace=False))
+    ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx)
+    compare_search(gpu, ref, idx)
+    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method, idx=idx,
+                          min_compared=0.99, interp=oracle.BILINEAR)
+    print(st)
+    assert (gpu["status"] == 0).mean() > 0.99
+
+
+def test_bilinear_argument_checks():
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    h = dic.dic_create(21, 5, 10)
+    try:
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_set_interpolation(h, 5)
+        assert e.value.code == dic.DIC_ERR_ARG
+        f, g = configs.tiny(90, 96, 96, 400)
+        tf, tg = torch.from_numpy(f).cuda(), torch.from_numpy(g).cuda()
+        dic.dic_set_interpolation(h, dic.DIC_INTERP_BILINEAR)
+        dic.dic_set_pairs(h, [(tf, tg, 15, 8, 4)])
+        total, _ = dic.dic_batch_pois(h, 1)
+        out = dic.batch_outputs(total, torch.device("cuda:0"))
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_run_batch(h, 0, out)
+        assert e.value.code == dic.DIC_ERR_UNSUPPORTED
+    finally:
+        dic.dic_destroy(h)
+
+
 # --------------------------------------------------------------- edge cases
 def test_smallest_subset_search():
     """Subset 3 (N = 9 < 32 lanes): integer search bit-exact.  The
