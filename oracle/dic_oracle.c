@@ -19,7 +19,7 @@
  *    exactly (sign of num, then num_a^2*Dg_b against num_b^2*Dg_a in 128-bit
  *    integers); ties keep the lowest linear index (dv+R)(2R+1)+(du+R).
  *  - Sub-pixel refinement (Section 2.2) by the inverse-compositional
- *    Gauss-Newton algorithm with a first-order ("affine") warp, and by the
+ *    Gauss-Newton algorithm with a first-order (affine) warp, and by the
  *    forward-additive Newton-Raphson algorithm in its Gauss-Newton form
  *    (Table 2).  Grey levels between pixels come from bicubic interpolation
  *    (Section 2.2) with the Keys cubic-convolution kernel, a = -0.5, on the
@@ -211,11 +211,11 @@ double dico_bicubic(const double *img, int W, int H, int pitch, double x, double
 
 /* ------------------------------------------------------ bilinear (Eq. 5) */
 /* G(x*, y*) = a00 + a10 x' + a01 y' + a11 x'y' (Eq. 5, Section 2.2), with
- * x', y' the distances along x and y from the next integer pixel position
- * (read: the pixel (floor x*, floor y*)) and the four coefficients from the
- * linear system that makes G equal the grey levels of the four surrounding
- * pixels, G(0,0) = g00, G(1,0) = g10, G(0,1) = g01, G(1,1) = g11, solved by
- * substitution.  The gradient is that of the same patch. */
+ * x', y' the offsets along x and y from the integer pixel (floor x*,
+ * floor y*) and the four coefficients from the linear system that makes G
+ * equal the grey levels of the four surrounding pixels, G(0,0) = g00,
+ * G(1,0) = g10, G(0,1) = g01, G(1,1) = g11, solved by substitution.  The
+ * gradient is that of the same patch. */
 static double interp_bilinear(const double *img, int pitch, double x, double y, double *gx,
                               double *gy) {
   double fx0 = floor(x), fy0 = floor(y);
