@@ -179,8 +179,7 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int
 
 /* ---------------------------------------------------------------- batches
  * Many image pairs of uneven size in one go -- the GPU form of the paper's
- * "image parallel" mode (Section 2.3, Table 6), where whole pairs are
- * processed concurrently. */
+ * parallelism over whole image pairs (Section 2.3, Table 6). */
 typedef struct {
   const uint8_t *ref_dev;  /* device, borrowed (as dic_set_pair)             */
   const uint8_t *def_dev;
@@ -204,10 +203,11 @@ typedef struct {
 } dic_batch_out;
 
 /* Bind n_pairs pairs (host array of descriptors, copied).  Allocates the
- * scratch of every pair (72 bytes per pixel in total; DIC_ERR_OOM on
- * failure) and validates every descriptor (DIC_ERR_ARG); a pair whose search
- * window does not fit in shared memory returns DIC_ERR_UNSUPPORTED naming it
- * in dic_last_error.  Replaces any earlier batch. */
+ * precompute scratch of every pair (20 bytes per pixel; DIC_ERR_OOM on
+ * failure) and validates every descriptor (DIC_ERR_ARG); a pair that neither
+ * search form can run (FP32: the search window must fit shared memory;
+ * tensor-core: see dic_set_form) returns DIC_ERR_UNSUPPORTED naming it in
+ * dic_last_error.  Replaces any earlier batch. */
 dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc *descs);
 
 /* Total POIs of the bound batch and, if offsets is not NULL, the host array
@@ -215,11 +215,16 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc *descs);
 dic_status dic_batch_pois(dic_t h, int64_t *total, int64_t *offsets);
 
 /* Run precompute, integer search and sub-pixel refinement of the whole batch
- * as one CUDA graph on the handle's stream: per-pair precompute launches,
- * then persistent search kernels (one per subset-width class) and one
- * persistent sub-pixel kernel whose warps take POIs from a global counter.
- * The graph is built on the first call and rebuilt when method, outputs or
- * tuning change; later calls only launch it.  Requires dic_set_pairs. */
+ * as one CUDA graph on the handle's stream: per-pair precompute launches;
+ * the integer search in the handle's form (tensor-core: one search per pair
+ * on shared scratch, allocated on first use for the largest pair; FP32: one
+ * persistent kernel per subset-width class over a work counter); then one
+ * persistent sub-pixel kernel whose warps take POIs from a global counter,
+ * or per-pair sub-pixel launches overlapping the next searches (see
+ * dic_set_batch_shape).  The graph is built on the first call and rebuilt
+ * when method, outputs, form or tuning change; later calls only launch it.
+ * Requires dic_set_pairs.  DIC_ERR_UNSUPPORTED names a pair the form cannot
+ * run, or when bilinear interpolation is set. */
 dic_status dic_run_batch(dic_t h, dic_method method, const dic_batch_out *out);
 
 /* Sub-pixel launch shape of later dic_run_batch calls: warps_per_cta 2, 4
