@@ -8,9 +8,9 @@
  * cross-correlation (ZNCC, Eq. 1) of a (2M+1)x(2M+1) subset by brute-force
  * search (Section 2.1), then refines it to sub-pixel accuracy with a
  * first-order (6-parameter, affine) subset shape function over bicubically
- * interpolated deformed-image grey levels, by the inverse-compositional
- * Gauss-Newton algorithm or by forward-additive Newton-Raphson
- * (Section 2.2, Table 2).
+ * (or, on request, bilinearly: Eq. 5) interpolated deformed-image grey
+ * levels, by the inverse-compositional Gauss-Newton algorithm or by
+ * forward-additive Newton-Raphson (Section 2.2, Table 2).
  *
  * Conventions shared by every call:
  *  - Images are 8-bit grey, row-major, pixel (x, y) at byte y*pitch + x;
@@ -19,8 +19,10 @@
  *    and owns them; the library never frees caller memory and keeps image
  *    pointers only as borrowed references between dic_set_pair and the next
  *    dic_set_pair / dic_destroy (the images must stay alive and unchanged).
- *  - The library owns its scratch (float copy of the deformed image, gradient
- *    field), allocates it in dic_set_pair and frees it in dic_destroy.
+ *  - The library owns its scratch (float copy and tap quads of the deformed
+ *    image, gradient field; the search forms' and batches' own scratch),
+ *    allocates it on first use (dic_set_pair, dic_integer_search,
+ *    dic_set_pairs, dic_run_batch) and frees it in dic_destroy.
  *  - Work is enqueued asynchronously on the stream given to dic_set_stream
  *    (default: the legacy default stream).  Argument errors are returned
  *    synchronously; a CUDA launch error is returned as DIC_ERR_CUDA with the
@@ -171,7 +173,10 @@ dic_status dic_integer_search(dic_t h, int32_t *u0, int32_t *v0, float *zncc0,
  * (u0, v0, status0), e.g. the outputs of dic_integer_search.  POIs whose
  * status0 is not DIC_POI_OK are passed through with zero gradients.
  * Outputs (device, n_pois each): the six shape parameters, zncc (Eq. 1 at the
- * returned shape), iters (solves performed) and status. */
+ * returned shape; for a converged POI, at the shape its last iteration
+ * sampled, which differs from the returned one by the final update, below
+ * the tolerance, at a stationary point of Eq. 1), iters (solves performed)
+ * and status. */
 dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int32_t *v0,
                         const uint8_t *status0, float *u, float *v, float *ux, float *uy,
                         float *vx, float *vy, float *zncc, int32_t *iters,
