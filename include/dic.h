@@ -108,6 +108,16 @@ void dic_destroy(dic_t h);
 /* Message of the last failed call on this handle ("" if none). */
 const char *dic_last_error(dic_t h);
 
+/* Failure report of the device side.  Every wait inside the search kernels
+ * (on a TMA copy or an MMA, through an mbarrier) is bounded; a kernel whose
+ * wait gives up records it in the handle's error flag, waits (bounded) for
+ * its own copies in flight and returns, leaving its results incomplete.
+ * dic_check synchronises the handle's stream, reads the flag and returns
+ * DIC_ERR_TIMEOUT (clearing the flag; which kernel in dic_last_error) if it
+ * is set, DIC_OK otherwise (also before any launch); DIC_ERR_CUDA if the
+ * stream itself failed.  No counterpart in the paper. */
+dic_status dic_check(dic_t h);
+
 /* Stream for all later work (a cudaStream_t passed as void*; NULL = default). */
 dic_status dic_set_stream(dic_t h, void *cuda_stream);
 

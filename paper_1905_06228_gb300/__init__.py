@@ -54,6 +54,7 @@ SIGNATURES = {
     "dic_create": (i32, [C.POINTER(P), i32, i32, i32, i32, f32, i32]),
     "dic_destroy": (None, [P]),
     "dic_last_error": (C.c_char_p, [P]),
+    "dic_check": (i32, [P]),
     "dic_set_stream": (i32, [P, P]),
     "dic_set_form": (i32, [P, i32]),
     "dic_set_solve_precision": (i32, [P, i32]),
@@ -139,6 +140,11 @@ def dic_destroy(h) -> None:
 
 def dic_last_error(h) -> str:
     return lib().dic_last_error(h).decode()
+
+
+def dic_check(h) -> None:
+    """Raise DICError(DIC_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(lib().dic_check(h), h)
 
 
 def dic_set_stream(h, stream) -> None:

@@ -185,6 +185,24 @@ void dic_destroy(dic_t h) {
 
 const char* dic_last_error(dic_t h) { return h ? h->last_error.c_str() : "null handle"; }
 
+dic_status dic_check(dic_t h) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->err_flag) return DIC_OK;  // nothing launched yet
+  unsigned int flag = 0;
+  cudaError_t e = cudaMemcpyAsync(&flag, h->err_flag, sizeof flag, cudaMemcpyDeviceToHost,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "error-flag read");
+  if (flag == 0) return DIC_OK;
+  e = cudaMemsetAsync(h->err_flag, 0, sizeof(unsigned int), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "error-flag reset");
+  return fail(h, DIC_ERR_TIMEOUT,
+              "a bounded device wait gave up (flag 0x%x: 1 FP32 search staging, 2 tensor-core "
+              "tile pipeline); the affected integer-search results are incomplete",
+              flag);
+}
+
 dic_status dic_set_stream(dic_t h, void* s) {
   if (!h) return DIC_ERR_ARG;
   h->stream = static_cast<cudaStream_t>(s);

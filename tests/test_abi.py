@@ -125,3 +125,15 @@ def test_form_and_noalloc_argument_checks():
     # images beyond the static array's limit are refused before any device work
     args = [16, 16, 1024, 1024, 1024, 21, 5, 10, 0, 1e-3, 50, 32] + [None] * 13
     assert lib.dic_subpixel_noalloc(*args) == dic.DIC_ERR_ARG
+
+
+def test_check_before_any_launch():
+    """dic_check on a fresh handle has no flag to read: DIC_OK without any
+    device work; a null handle is DIC_ERR_ARG."""
+    lib = dic.lib()
+    assert lib.dic_check(None) == dic.DIC_ERR_ARG
+    h = dic.dic_create(21, 5, 10)
+    try:
+        assert lib.dic_check(h) == dic.DIC_OK
+    finally:
+        dic.dic_destroy(h)

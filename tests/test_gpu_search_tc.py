@@ -38,6 +38,29 @@ def test_rigid256(rigid256):
     compare_search(b, oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius))
 
 
+def test_no_wait_gave_up_on_a_normal_run(affine1024):
+    """After a full tensor-core search, FP32 search and sub-pixel pass on the
+    affine workload, the device error flag of the bounded waits is clear."""
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    p = affine1024
+    h = dic.dic_create(p.subset, p.step, p.radius)
+    try:
+        tf = torch.from_numpy(p.ref).cuda()
+        tg = torch.from_numpy(p.defm).cuda()
+        dic.dic_set_pair(h, tf, tg)
+        n, _, _ = dic.dic_num_pois(h)
+        t = lambda dt: torch.empty(n, dtype=dt, device="cuda")
+        o = [t(torch.int32), t(torch.int32), t(torch.float32), t(torch.uint8)]
+        for form in (TC, 0):
+            dic.dic_set_form(h, form)
+            dic.dic_integer_search(h, *o)
+        dic.dic_check(h)
+    finally:
+        dic.dic_destroy(h)
+
+
 def test_affine1024(affine1024):
     p = affine1024
     b = _both(p.ref, p.defm, p.subset, p.step, p.radius)
