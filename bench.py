@@ -1,8 +1,9 @@
 """Benchmark of the DIC hot path on GB300: converged POI/s.
 
 One step = one pass of the whole hot path over one image pair: bind the pair
-(precompute kernel: gradients + bicubic table), brute-force ZNCC integer
-search, IC-GN sub-pixel refinement.  Workload ``affine1024``: one 1024x1024
+(precompute kernel: gradients of f, float copy and BF16 tap quads of g),
+brute-force ZNCC integer search (BF16 tensor-core form), IC-GN sub-pixel
+refinement with the FP64 6x6 solve.  Workload ``affine1024``: one 1024x1024
 speckle pair (40000 speckles, affine exx=0.5 %, eyy=-0.2 %, 1 deg,
 t=(7.3, 4.1) px, noise sigma 2), subset 31x31, grid step 5 (36100 POIs),
 search +-20 px, tol 1e-3, at most 50 iterations.  Synthetic, seeded inputs.
@@ -686,7 +687,7 @@ def run_batch_workload(args):
                                  if tuple(chosen) == (0, 0) else
                                  "one persistent sub-pixel kernel")),
                        "autotuned": {"warps_per_cta": chosen[0], "grid_mult": chosen[1]},
-                       "l2": "inputs and tables larger than L2"},
+                       "l2": "inputs and scratch larger than L2"},
             "pairs_per_s": len(tens) / (ms / 1e3),
             "per_pair_launches": {"ms_per_step": ms_single,
                                   "value": conv / (ms_single / 1e3)},
