@@ -8,7 +8,8 @@ present when work is requested, a ``RuntimeError`` is raised.
 
 Method (Thoma & Ravi): brute-force ZNCC integer search (Eq. 1, Section 2.1)
 then first-order IC-GN or Newton-Raphson sub-pixel refinement over bicubic
-interpolation (Section 2.2, Table 2), for every POI of a regular grid.
+(or bilinear, Eq. 5) interpolation (Section 2.2, Table 2), for every POI of a
+regular grid.
 """
 from __future__ import annotations
 
