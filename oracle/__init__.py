@@ -12,6 +12,8 @@ follows the paper's method as stated in the C file's header:
                          a first-order warp and Keys bicubic interpolation.
 * ``znssd``           -- summed ZNSSD and its hand-derived FP64 gradient.
 * ``bicubic``         -- the bicubic interpolant itself (Section 2.2).
+* ``pso_search``      -- particle swarm integer search (Section 2.1, Eqs. 2-4)
+                         and the modified swarm with the star search folded in.
 """
 from __future__ import annotations
 
@@ -69,6 +71,10 @@ def _load():
             lib.dico_bicubic.restype = dbl
             lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P, P]
             lib.dico_znssd.restype = i32
+            lib.dico_pso_search.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, i32,
+                                            i32, i32, dbl, dbl, dbl, i64, i64, P, i32, P, P,
+                                            P, P, P, P, P]
+            lib.dico_pso_search.restype = i32
             _lib = lib
     return _lib
 
@@ -195,3 +201,52 @@ def znssd(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, p: 
     if per_poi:
         out = out + (lp,)
     return out if len(out) > 1 else out[0]
+
+
+def pso_search(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
+               rand: np.ndarray, modified: bool = False, c1: float = 2.0, c2: float = 2.0,
+               vinit: float | None = None, stop: tuple[int, int] = (995, 1000),
+               poi_idx=None, threads: int | None = None, trace: bool = False) -> dict:
+    """Particle swarm integer search (Eqs. 2-4) over the same window as the
+    brute-force search.  ``rand`` holds the swarm's uniforms, shape
+    (POIs, generations, particles, 4): generation 0 draws the start position
+    and velocity, generation t >= 1 the r1 (x, y) and r2 (x, y) of Eq. 2.
+    ``stop`` = (n, d) ends a POI's swarm once its best C >= n / d.
+    ``vinit`` (pixels, default radius / 2) scales the start velocity.
+    With ``trace`` the result holds ``trace[k, t, i] = (px, py, vx, vy, qx, qy,
+    bx, by)``: particle i's position and velocity when generation t is
+    evaluated, its nearest pixel and its best pixel afterwards (NaN for
+    generations not run)."""
+    f = np.ascontiguousarray(f, np.uint8)
+    g = np.ascontiguousarray(g, np.uint8)
+    assert f.shape == g.shape and f.ndim == 2
+    H, W = f.shape
+    nx, ny = grid(W, H, subset, step, radius)
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        n = nx * ny
+    rand = np.ascontiguousarray(rand, np.float64)
+    assert rand.ndim == 4 and rand.shape[0] == n and rand.shape[3] == 4
+    gmax, particles = rand.shape[1], rand.shape[2]
+    if vinit is None:
+        vinit = radius / 2.0
+    u0 = np.zeros(n, np.int32)
+    v0 = np.zeros(n, np.int32)
+    zn = np.zeros(n, np.float64)
+    st = np.zeros(n, np.uint8)
+    gens = np.zeros(n, np.int32)
+    evals = np.zeros(n, np.int32)
+    tr = np.full((n, gmax, particles, 8), np.nan) if trace else None
+    rc = _load().dico_pso_search(_ptr(f), _ptr(g), W, H, W, subset, step, radius, _ptr(idx),
+                                 n if idx is not None else -1, int(bool(modified)), particles,
+                                 gmax, float(c1), float(c2), float(vinit), int(stop[0]),
+                                 int(stop[1]), _ptr(rand), threads or default_threads(),
+                                 _ptr(u0), _ptr(v0), _ptr(zn), _ptr(st), _ptr(gens),
+                                 _ptr(evals), _ptr(tr))
+    if rc:
+        raise ValueError("oracle pso_search failed (%d)" % rc)
+    out = dict(u0=u0, v0=v0, zncc=zn, status=st, generations=gens, evaluations=evals,
+               nx=nx, ny=ny)
+    if trace:
+        out["trace"] = tr
+    return out

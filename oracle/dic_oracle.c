@@ -606,3 +606,213 @@ int dico_znssd(const double *f, const double *g, int W, int H, int pitch, int su
   *loss = total;
   return 0;
 }
+
+/* ------------------------------------------- particle swarm integer search */
+/* Integer search by particle swarm optimisation (Section 2.1, Eqs. 2-4) and
+ * by the modified swarm whose particles also look at the four pixels around
+ * them, the star search folded into the swarm (Sections 3 and 5).
+ *
+ * Per POI, with the swarm's random numbers passed in as
+ * rand[k][t][i][0..3] (uniforms in [0,1); k the POI, t the generation, i the
+ * particle):
+ *   t = 0   p_i = R (2 u_0 - 1, 2 u_1 - 1),  v_i = vinit (2 u_2 - 1, 2 u_3 - 1)
+ *   t >= 1  Eq. 2 with w = w(t-1) of Eq. 4, r1 = (u_0, u_1), r2 = (u_2, u_3)
+ *           per direction, evaluated as ((w v) + (c1 r1)(pbest - p)) +
+ *           (c2 r2)(gbest - p); then Eq. 3, p clamped to [-R, R] per
+ *           direction (the velocity is kept).
+ *   every generation, each particle evaluates Eq. 1 at its nearest pixel
+ *   q = floor(p + 1/2); the modified swarm also evaluates q +- (1,0) and
+ *   q +- (0,1) inside the window, keeps the best of the five (ties: centre,
+ *   +x, -x, +y, -y) and moves onto it.  pbest takes the evaluated pixel if it
+ *   is strictly better (at t = 0 unconditionally); after all particles,
+ *   gbest takes the first strictly better pbest in particle order.
+ *   The swarm stops after `gmax` generations, or after the first generation
+ *   whose gbest reaches C >= stop_num / stop_den (tested exactly).
+ * Each pixel is evaluated at most once per POI (a look-up table, as the
+ * paper's implementation keeps); `evals` counts the distinct pixels.
+ * Candidates compare exactly as in the brute-force search; a pixel whose
+ * target subset is flat has no correlation and ranks below every other. */
+typedef struct {
+  int64_t num, den; /* C = num / sqrt(Df * den) */
+  int def;          /* den != 0 */
+} zc_t;
+
+static int zc_greater(zc_t a, zc_t b) {
+  if (!a.def) return 0;
+  if (!b.def) return 1;
+  return zncc_greater(a.num, a.den, b.num, b.den);
+}
+
+/* C >= sn / sd, exactly (0 <= sn, 1 <= sd <= 2^20). */
+static int zc_at_least(zc_t a, int64_t Df, int64_t sn, int64_t sd) {
+  if (!a.def || a.num < 0) return 0;
+  __int128 lhs = (__int128)a.num * (__int128)a.num * ((__int128)sd * (__int128)sd);
+  __int128 rhs = ((__int128)sn * (__int128)sn) * ((__int128)Df * (__int128)a.den);
+  return lhs >= rhs;
+}
+
+typedef struct {
+  const uint8_t *f, *g;
+  int pitch, x0, y0, M, R;
+  int64_t N, Sf;
+  uint8_t *seen;
+  zc_t *memo;
+  int evals;
+} pso_ctx;
+
+static zc_t pso_eval(pso_ctx *c, int du, int dv) {
+  int64_t slot = (int64_t)(dv + c->R) * (2 * c->R + 1) + (du + c->R);
+  if (c->seen[slot]) return c->memo[slot];
+  int64_t Sg = 0, Sgg = 0, Sfg = 0;
+  for (int dy = -c->M; dy <= c->M; ++dy)
+    for (int dx = -c->M; dx <= c->M; ++dx) {
+      int64_t a = c->f[(int64_t)(c->y0 + dy) * c->pitch + (c->x0 + dx)];
+      int64_t b = c->g[(int64_t)(c->y0 + dy + dv) * c->pitch + (c->x0 + dx + du)];
+      Sg += b;
+      Sgg += b * b;
+      Sfg += a * b;
+    }
+  zc_t z;
+  z.den = c->N * Sgg - Sg * Sg;
+  z.num = c->N * Sfg - c->Sf * Sg;
+  z.def = z.den != 0;
+  c->seen[slot] = 1;
+  c->memo[slot] = z;
+  c->evals++;
+  return z;
+}
+
+static void pso_one(pso_ctx *c, int modified, int P, int gmax, double c1, double c2,
+                    double vinit, int64_t sn, int64_t sd, const double *rand,
+                    double *trace, double (*p)[2], double (*v)[2], int (*pb)[2],
+                    zc_t *pbc, int32_t *u0, int32_t *v0, double *zncc, uint8_t *status,
+                    int32_t *gens) {
+  const int M = c->M, R = c->R;
+  int64_t Sff = 0;
+  c->Sf = 0;
+  for (int dy = -M; dy <= M; ++dy)
+    for (int dx = -M; dx <= M; ++dx) {
+      int64_t a = c->f[(int64_t)(c->y0 + dy) * c->pitch + (c->x0 + dx)];
+      c->Sf += a;
+      Sff += a * a;
+    }
+  const int64_t Df = c->N * Sff - c->Sf * c->Sf;
+  *gens = 0;
+  if (Df == 0) {
+    *u0 = 0; *v0 = 0; *zncc = 0.0; *status = ST_ZERO_VAR_REF;
+    return;
+  }
+  static const int star[4][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}};
+  int gb[2] = {0, 0};
+  zc_t gc = {0, 0, 0};
+  for (int t = 0; t < gmax; ++t) {
+    const double *rt = rand + (int64_t)t * P * 4;
+    if (t == 0) {
+      for (int i = 0; i < P; ++i)
+        for (int d = 0; d < 2; ++d) {
+          p[i][d] = (double)R * (2.0 * rt[i * 4 + d] - 1.0);
+          v[i][d] = vinit * (2.0 * rt[i * 4 + 2 + d] - 1.0);
+        }
+    } else {
+      const double w = 0.9 - (double)(t - 1) / (2.0 * (double)gmax); /* Eq. 4 */
+      for (int i = 0; i < P; ++i)
+        for (int d = 0; d < 2; ++d) {
+          double r1 = rt[i * 4 + d], r2 = rt[i * 4 + 2 + d];
+          double inert = w * v[i][d];
+          double cogn = (c1 * r1) * ((double)pb[i][d] - p[i][d]);
+          double soc = (c2 * r2) * ((double)gb[d] - p[i][d]);
+          v[i][d] = (inert + cogn) + soc; /* Eq. 2 */
+          double np = p[i][d] + v[i][d];  /* Eq. 3 */
+          p[i][d] = np < -R ? (double)-R : (np > R ? (double)R : np);
+        }
+    }
+    for (int i = 0; i < P; ++i) {
+      double *tr = trace ? trace + ((int64_t)t * P + i) * 8 : NULL;
+      if (tr) { tr[0] = p[i][0]; tr[1] = p[i][1]; tr[2] = v[i][0]; tr[3] = v[i][1]; }
+      int q[2] = {(int)floor(p[i][0] + 0.5), (int)floor(p[i][1] + 0.5)};
+      int best[2] = {q[0], q[1]};
+      zc_t bc = pso_eval(c, q[0], q[1]);
+      if (modified) {
+        for (int s = 0; s < 4; ++s) {
+          int nx = q[0] + star[s][0], ny = q[1] + star[s][1];
+          if (nx < -R || nx > R || ny < -R || ny > R) continue;
+          zc_t z = pso_eval(c, nx, ny);
+          if (zc_greater(z, bc)) { best[0] = nx; best[1] = ny; bc = z; }
+        }
+        p[i][0] = best[0];
+        p[i][1] = best[1];
+      }
+      if (t == 0 || zc_greater(bc, pbc[i])) {
+        pb[i][0] = best[0]; pb[i][1] = best[1]; pbc[i] = bc;
+      }
+      if (tr) { tr[4] = q[0]; tr[5] = q[1]; tr[6] = pb[i][0]; tr[7] = pb[i][1]; }
+    }
+    for (int i = 0; i < P; ++i)
+      if ((t == 0 && i == 0) || zc_greater(pbc[i], gc)) {
+        gb[0] = pb[i][0]; gb[1] = pb[i][1]; gc = pbc[i];
+      }
+    *gens = t + 1;
+    if (zc_at_least(gc, Df, sn, sd)) break;
+  }
+  *u0 = gb[0]; *v0 = gb[1];
+  if (!gc.def) {
+    *zncc = 0.0; *status = ST_ZERO_VAR_DEF;
+    return;
+  }
+  *zncc = (double)gc.num / sqrt((double)Df * (double)gc.den);
+  *status = ST_OK;
+}
+
+int dico_pso_search(const uint8_t *f, const uint8_t *g, int W, int H, int pitch, int subset,
+                    int step, int R, const int64_t *poi_idx, int64_t n_idx, int modified,
+                    int particles, int gmax, double c1, double c2, double vinit,
+                    int64_t stop_num, int64_t stop_den, const double *rand, int nthreads,
+                    int32_t *u0, int32_t *v0, double *zncc, uint8_t *status, int32_t *gens,
+                    int32_t *evals, double *trace) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  if (particles < 1 || particles > 4096 || gmax < 1 || gmax > 1000 || stop_num < 0 ||
+      stop_den < 1 || stop_den > (1 << 20) || subset > 127 || !rand)
+    return -1;
+  const int M = subset / 2;
+  const int64_t total = (int64_t)nx * ny;
+  const int64_t n = poi_idx ? n_idx : total;
+  const int64_t win = (int64_t)(2 * R + 1) * (2 * R + 1);
+  const int64_t per_poi = (int64_t)gmax * particles * 4;
+  if (poi_idx)
+    for (int64_t k = 0; k < n; ++k)
+      if (poi_idx[k] < 0 || poi_idx[k] >= total) return -1;
+  if (nthreads <= 0) nthreads = 1;
+  int failed = 0;
+#pragma omp parallel num_threads(nthreads)
+  {
+    uint8_t *seen = malloc((size_t)win);
+    zc_t *memo = malloc(sizeof(zc_t) * (size_t)win);
+    double (*p)[2] = malloc(sizeof(double[2]) * (size_t)particles);
+    double (*v)[2] = malloc(sizeof(double[2]) * (size_t)particles);
+    int (*pb)[2] = malloc(sizeof(int[2]) * (size_t)particles);
+    zc_t *pbc = malloc(sizeof(zc_t) * (size_t)particles);
+    int ok = seen && memo && p && v && pb && pbc;
+    if (!ok) {
+#pragma omp atomic write
+      failed = 1;
+    }
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t k = 0; k < n; ++k) {
+      if (!ok) continue;
+      int64_t poi = poi_idx ? poi_idx[k] : k;
+      pso_ctx c;
+      c.f = f; c.g = g; c.pitch = pitch; c.M = M; c.R = R;
+      c.N = (int64_t)subset * subset;
+      c.seen = seen; c.memo = memo; c.evals = 0;
+      memset(seen, 0, (size_t)win);
+      poi_centre(poi, nx, M, R, step, &c.x0, &c.y0);
+      pso_one(&c, modified, particles, gmax, c1, c2, vinit, stop_num, stop_den,
+              rand + k * per_poi, trace ? trace + k * per_poi * 2 : NULL, p, v, pb, pbc,
+              &u0[k], &v0[k], &zncc[k], &status[k], &gens[k]);
+      evals[k] = c.evals;
+    }
+    free(seen); free(memo); free(p); free(v); free(pb); free(pbc);
+  }
+  return failed ? -2 : 0;
+}
