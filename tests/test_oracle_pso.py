@@ -151,6 +151,64 @@ def test_social_term_collapses_swarm_onto_gbest():
     assert res["zncc"][0] == pytest.approx(max(c), abs=1e-12)
 
 
+def test_pbest_is_best_pixel_seen_so_far():
+    """Each particle's pbest after generation t is the first pixel, among those
+    it evaluated in generations 0..t, with the largest Eq. 1 value."""
+    f, g = _pair(seed=6, noise=3.0)
+    subset, step, r, parts, gens = 9, 12, 6, 12, 5
+    nx, _ = oracle.grid(f.shape[1], f.shape[0], subset, step, r)
+    u = _rand(4, gens, parts, seed=9)
+    res = oracle.pso_search(f, g, subset, step, r, u, stop=NEVER, poi_idx=[4, 5, 6, 7],
+                            trace=True)
+    moved = 0
+    for j, k in enumerate([4, 5, 6, 7]):
+        if res["status"][j] != oracle.ST_OK:
+            continue
+        x0, y0 = _centre(k, nx, subset, step, r)
+        tr = res["trace"][j]
+        for i in range(parts):
+            best, bc = None, -math.inf
+            for t in range(gens):
+                q = tuple(tr[t, i, 4:6].astype(int))
+                c = _eq1_at(f, g, x0, y0, subset // 2, *q)
+                if best is None or c > bc:
+                    best, bc = q, c
+                assert tuple(tr[t, i, 6:8].astype(int)) == best
+                moved += q != best
+    assert moved > 20      # particles often stand on worse pixels than their best
+
+
+def test_gbest_keeps_first_particle_on_exact_ties():
+    """A texture of period 3 in x matches the reference exactly at every third
+    horizontal offset (C = 1 at several pixels).  With c1 = 0, c2 = 1, r2 = 1
+    and v(0) = 0 the whole swarm lands on gbest after one update: the pixel
+    of the lowest-numbered particle that found an exact match."""
+    rng = np.random.default_rng(3)
+    period = rng.integers(0, 256, (60, 3)).astype(np.uint8)
+    g = np.ascontiguousarray(np.tile(period, (1, 20)))        # 60 x 60, period 3 in x
+    f = np.ascontiguousarray(np.roll(g, -1, axis=1))           # exact at du = 1 + 3k, dv = 0
+    subset, step, r, parts = 7, 30, 4, 60
+    nx, ny = oracle.grid(60, 60, subset, step, r)
+    m = subset // 2
+    u = swarm.uniforms(8, nx * ny, 2, parts)
+    u[:, 1, :, 2:4] = 1.0
+    res = oracle.pso_search(f, g, subset, step, r, u, c1=0.0, c2=1.0, vinit=0.0, stop=NEVER,
+                            trace=True)
+    ties = 0
+    for k in range(nx * ny):
+        x0, y0 = _centre(k, nx, subset, step, r)
+        tr = res["trace"][k]
+        ref = f[y0 - m:y0 + m + 1, x0 - m:x0 + m + 1]
+        exact = [i for i in range(parts)
+                 if np.array_equal(ref, g[y0 + int(tr[0, i, 5]) - m:y0 + int(tr[0, i, 5]) + m + 1,
+                                          x0 + int(tr[0, i, 4]) - m:x0 + int(tr[0, i, 4]) + m + 1])]
+        assert exact
+        ties += len({tuple(tr[0, i, 4:6]) for i in exact}) > 1
+        gb = tr[0, exact[0], 4:6]
+        np.testing.assert_allclose(tr[1, :, 0:2], np.broadcast_to(gb, (parts, 2)), atol=1e-13)
+    assert ties >= 1
+
+
 # ------------------------------------------------------------ star search
 def test_modified_swarm_takes_best_of_five():
     """Generation 0 of the modified swarm: each particle's best is the best of
