@@ -212,7 +212,7 @@ def pso_search(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int
     (POIs, generations, particles, 4): generation 0 draws the start position
     and velocity, generation t >= 1 the r1 (x, y) and r2 (x, y) of Eq. 2.
     ``stop`` = (n, d) ends a POI's swarm once its best C >= n / d.
-    ``vinit`` (pixels, default radius / 2) scales the start velocity.
+    ``vinit`` (pixels, default radius / 4) scales the start velocity.
     With ``trace`` the result holds ``trace[k, t, i] = (px, py, vx, vy, qx, qy,
     bx, by)``: particle i's position and velocity when generation t is
     evaluated, its nearest pixel and its best pixel afterwards (NaN for
@@ -229,7 +229,7 @@ def pso_search(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int
     assert rand.ndim == 4 and rand.shape[0] == n and rand.shape[3] == 4
     gmax, particles = rand.shape[1], rand.shape[2]
     if vinit is None:
-        vinit = radius / 2.0
+        vinit = radius / 4.0
     u0 = np.zeros(n, np.int32)
     v0 = np.zeros(n, np.int32)
     zn = np.zeros(n, np.float64)
