@@ -353,3 +353,38 @@ def test_argument_errors():
         oracle.pso_search(f, g, 9, 12, 6, u, stop=(-1, 2), poi_idx=[0])
     with pytest.raises(ValueError):
         oracle.pso_search(f, g, 9, 12, 6, u, poi_idx=[10 ** 6])   # no such POI
+
+
+def _golden_counts():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "swarm_evaluation_counts.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            out[line[0]] = int(line[1])
+    return out
+
+
+def test_evaluation_counts_printed_in_section5():
+    """Section 5's counts: at most 250 (standard) and 1250 (modified) Eq. 1
+    evaluations per POI for 50 particles and 5 generations, reached when no
+    pixel repeats (a wide window, particles in ballistic flight)."""
+    gold = _golden_counts()
+    parts, gens = gold["particles"], gold["generations"]
+    r, subset = 1000, 9
+    size = 2 * (subset // 2 + r + 2) + 9
+    img = np.random.default_rng(5).integers(0, 256, (size, size), dtype=np.uint8)
+    nx, ny = oracle.grid(size, size, subset, 3, r)
+    assert nx * ny == 9
+    u = swarm.uniforms(6, nx * ny, gens, parts)
+    u[:, 0, :, 0:2] = 0.1 + 0.8 * u[:, 0, :, 0:2]    # start at most 0.8 R out: no wall
+    u[:, 0, :, 2:4] = 0.8 + 0.2 * u[:, 0, :, 2:4]    # v(0) in [0.6, 1] vinit per direction
+    u[:, 1:] = 0.0
+    for mod, key in ((False, "max_evaluations_standard"), (True, "max_evaluations_modified")):
+        res = oracle.pso_search(img, img, subset, 3, r, u, modified=mod, vinit=60.0,
+                                stop=NEVER)
+        assert (res["generations"] == gens).all()
+        assert res["evaluations"].max() == gold[key]
+        assert (res["evaluations"] <= gold[key]).all()
