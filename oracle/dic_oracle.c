@@ -28,6 +28,10 @@
  *  - The summed ZNSSD of every subset at given shape parameters and its
  *    gradient with respect to the deformed-image pixels and the parameters
  *    (hand-derived adjoint, FP64).
+ *  - Integer search by particle swarm optimisation (Section 2.1, Eqs. 2-4)
+ *    and by the modified swarm with one star-search step per generation
+ *    (Sections 3, 5); the swarm's random numbers are inputs.  Readings are
+ *    stated at that section below.
  *
  * The paper leaves the shape function, the update rules, the bicubic kernel,
  * the gradient operator, the convergence norm and the POI grid unstated; the
