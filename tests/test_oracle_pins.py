@@ -243,6 +243,76 @@ def test_subpixel_exact_integer_shift_fixed_point(method, du, dv, interp):
     assert (s["iters"][ok] >= 3).all()
 
 
+def test_icgn_and_fanr_contract_at_the_same_rate():
+    """Near the exact fixed point of an integer shift the two methods are the
+    same linear iteration: IC-GN's gradients of f (central differences)
+    equal FA-NR's gradients of the interpolated g there (the Keys derivative
+    at a node is the central difference), so their Hessians, residuals and
+    steps agree to first order.  Each POI's asymptotic contraction rate
+    (geometric mean of e(k+1)/e(k) over 1e-9 < e < 1e-4) must agree."""
+    big, _ = configs.tiny(17, 96, 96, 420)
+    du, dv = 2, -1
+    f = np.ascontiguousarray(big[10:86, 10:86]).astype(np.float64)
+    g = np.ascontiguousarray(big[10 - dv:86 - dv, 10 - du:86 - du]).astype(np.float64)
+    subset, step, r = 15, 6, 4
+    n = int(np.prod(oracle.grid(76, 76, subset, step, r)))
+    z = np.zeros(n, np.int32)
+    want = np.array([du, 0, 0, dv, 0, 0], np.float64)
+    rates = []
+    for method in (oracle.ICGN, oracle.FANR):
+        s = oracle.subpixel(f, g, subset, step, r, z + du + 1, z + dv - 1, np.zeros(n, np.uint8),
+                            method=method, tol=0.0, max_iter=80, trajectory=True)
+        e = np.linalg.norm(s["traj"] - want, axis=-1)
+        rk = np.full(n, np.nan)
+        for k in range(n):
+            sel = [i for i in range(1, 80) if 1e-9 < e[k, i] < 1e-4 and np.isfinite(e[k, i + 1])]
+            if len(sel) >= 3:
+                rk[k] = np.exp(np.mean(np.log(e[k, [i + 1 for i in sel]] / e[k, sel])))
+        rates.append(rk)
+    ok = np.isfinite(rates[0]) & np.isfinite(rates[1])
+    assert ok.mean() > 0.9
+    assert (rates[0][ok] < 0.9).all()                       # they do contract
+    assert (np.abs(rates[0][ok] - rates[1][ok]) < 0.01).mean() >= 0.95
+
+
+def _warp_matrix(p):
+    return np.array([[1 + p[1], p[2], p[0]], [p[4], 1 + p[5], p[3]], [0, 0, 1]], np.float64)
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_stop_rule_from_trajectory(method):
+    """Reading R9: a POI stops at the first solve whose step has
+    sqrt(du^2 + dv^2 + M^2 (dux^2 + duy^2 + dvx^2 + dvy^2)) < tol.  The steps
+    are recovered from the returned trajectory without the oracle's update
+    code: FA-NR adds the step (p_k - p_(k-1)); IC-GN composes with its
+    inverse, so W(dp) = W(p_k)^-1 W(p_(k-1)) as 3x3 matrices."""
+    f, g = configs.tiny(21, 64, 64, 260, Rigid(0.6, -0.35), noise=1.0)
+    f = f.astype(np.float64)
+    g = g.astype(np.float64)
+    subset, step, r, tol = 15, 4, 3, 1e-3
+    m = subset // 2
+    res0 = oracle.integer_search(f.astype(np.uint8), g.astype(np.uint8), subset, step, r)
+    s = oracle.subpixel(f, g, subset, step, r, res0["u0"], res0["v0"], res0["status"],
+                        method=method, tol=tol, max_iter=50, trajectory=True)
+    checked = 0
+    for k in np.flatnonzero(s["status"] == oracle.ST_OK):
+        n = s["iters"][k]
+        norms = []
+        for i in range(1, n + 1):
+            a, b = s["traj"][k, i - 1], s["traj"][k, i]
+            if method == oracle.FANR:
+                d = b - a
+            else:
+                wd = np.linalg.solve(_warp_matrix(b), _warp_matrix(a))
+                d = np.array([wd[0, 2], wd[0, 0] - 1, wd[0, 1], wd[1, 2], wd[1, 0], wd[1, 1] - 1])
+            norms.append(math.sqrt(d[0] ** 2 + d[3] ** 2 + m * m * (d[1] ** 2 + d[2] ** 2 +
+                                                                  d[4] ** 2 + d[5] ** 2)))
+        assert norms[-1] < tol * (1 + 1e-9)
+        assert all(x >= tol * (1 - 1e-9) for x in norms[:-1])
+        checked += 1
+    assert checked > 50
+
+
 @pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
 def test_subpixel_rigid_speckle_accuracy(rigid256, method):
     """Imposed rigid field (3.4, -2.7) px on analytically re-rendered
