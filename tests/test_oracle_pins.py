@@ -313,6 +313,40 @@ def test_stop_rule_from_trajectory(method):
     assert checked > 50
 
 
+def test_fanr_lands_on_the_dense_grid_minimum_of_znssd(rigid256):
+    """Brute force over the objective: on noise-free speckles (rigid256),
+    ZNSSD = 2 - 2C (Eq. 1) evaluated on a dense (u, v) grid of 5e-4 px
+    around FA-NR's result (gradient parameters held at FA-NR's values) is
+    smallest at FA-NR's (u, v), within one grid step.  IC-GN's fixed point
+    (stationary for its reference-gradient Jacobian rather than the target
+    gradient) lies within 3e-3 px of it; the two methods agree within
+    5e-3 px."""
+    pr = rigid256
+    f8, g8 = pr.ref, pr.defm
+    f, g = f8.astype(np.float64), g8.astype(np.float64)
+    subset, step, r = pr.subset, pr.step, pr.radius
+    idx = np.arange(0, 484, 61)
+    s0 = oracle.integer_search(f8, g8, subset, step, r, poi_idx=idx)
+    res = [oracle.subpixel(f, g, subset, step, r, s0["u0"], s0["v0"], s0["status"], method=m,
+                           tol=1e-8, max_iter=200, poi_idx=idx)
+           for m in (oracle.ICGN, oracle.FANR)]
+    assert (res[0]["status"] == oracle.ST_OK).all() and (res[1]["status"] == oracle.ST_OK).all()
+    assert np.abs(res[0]["p"][:, [0, 3]] - res[1]["p"][:, [0, 3]]).max() < 5e-3
+    h, kk = 5e-4, 6
+    steps = h * np.arange(-kk, kk + 1)
+    for j, k in enumerate(idx):
+        grid_p = np.repeat(res[1]["p"][j][None], len(steps) ** 2, 0)
+        grid_p[:, 0] += np.repeat(steps, len(steps))
+        grid_p[:, 3] += np.tile(steps, len(steps))
+        _, per = oracle.znssd(f, g, subset, step, r, grid_p, poi_idx=np.full(len(grid_p), k),
+                              grad=False, per_poi=True)
+        i = int(np.argmin(per))
+        assert i // len(steps) not in (0, 2 * kk) and i % len(steps) not in (0, 2 * kk)
+        best = grid_p[i, [0, 3]]
+        assert np.abs(best - res[1]["p"][j, [0, 3]]).max() <= h + 1e-12      # FA-NR
+        assert np.abs(best - res[0]["p"][j, [0, 3]]).max() <= 3e-3           # IC-GN
+
+
 @pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
 def test_subpixel_rigid_speckle_accuracy(rigid256, method):
     """Imposed rigid field (3.4, -2.7) px on analytically re-rendered
