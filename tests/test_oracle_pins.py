@@ -442,6 +442,44 @@ def test_subpixel_status_paths():
     assert (s["status"] == oracle.ST_ZERO_VAR_REF).all()
 
 
+def test_bounds_rule_at_its_edges():
+    """Reading R12: a shape is usable while every corner of the warped subset
+    lies in [1, W-2) x [1, H-2) (the 4x4 stencil stays inside).  The ZNSSD
+    skips (loss 0) exactly the shapes that break it; probe each edge with
+    translations that put the extreme corner just inside and on it."""
+    f, g = configs.tiny(9, 48, 48, 120, Rigid(0.6, -0.35), noise=1.0)
+    f = f.astype(np.float64)
+    g = g.astype(np.float64)
+    subset, step, r = 11, 6, 2
+    m = subset // 2
+    nx, ny = oracle.grid(48, 48, subset, step, r)
+    b = m + r + 2
+    x0 = y0 = b                                    # POI 0, top-left corner at (x0-m, y0-m)
+    eps = 1e-9
+    lo = 1.0 - (x0 - m)                            # u that puts the left edge at x = 1
+    hi = (48 - 2.0) - (x0 + m)                     # u that puts the right edge at x = W - 2
+    cases = [((lo, 0.0), True), ((lo - eps, 0.0), False),
+             ((hi - eps, 0.0), True), ((hi, 0.0), False),
+             ((0.0, lo), True), ((0.0, lo - eps), False),
+             ((0.0, hi - eps), True), ((0.0, hi), False)]
+    p = np.zeros((len(cases), 6))
+    for i, ((u, v), _) in enumerate(cases):
+        p[i, 0], p[i, 3] = u, v
+    _, per = oracle.znssd(f, g, subset, step, r, p, poi_idx=np.zeros(len(cases), np.int64),
+                          grad=False, per_poi=True)
+    for (uv, inside), loss in zip(cases, per):
+        assert (loss > 0) == inside, (uv, inside, loss)
+    # a gradient term moves the edges apart: with u = lo + 0.1 m the left
+    # edge sits at x = 1 - (ux - 0.1) m, inside for ux just below 0.1
+    q = np.zeros((2, 6))
+    q[:, 0] = lo + 0.1 * m
+    q[0, 1] = 0.1 - 1e-6
+    q[1, 1] = 0.1 + 1e-6
+    _, per2 = oracle.znssd(f, g, subset, step, r, q, poi_idx=np.zeros(2, np.int64), grad=False,
+                           per_poi=True)
+    assert per2[0] > 0 and per2[1] == 0
+
+
 # -------------------------------------------------------- ZNSSD and adjoint
 def _adjoint_case():
     f, g = configs.tiny(31, 40, 40, 100, Rigid(0.8, 0.3), noise=1.0)
