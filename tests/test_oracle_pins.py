@@ -442,6 +442,47 @@ def test_subpixel_status_paths():
     assert (s["status"] == oracle.ST_ZERO_VAR_REF).all()
 
 
+def test_nonfinite_and_singular_statuses():
+    """A NaN grey level inside the warped subset makes the sums non-finite
+    (status NONFINITE, no step taken); a reference that varies along x only
+    has fy = 0 everywhere, so IC-GN's Hessian (rows of fy terms all zero) is
+    singular (status SINGULAR) while the shape stays at its start."""
+    f, g = configs.tiny(9, 48, 48, 120, Rigid(0.6, -0.35), noise=1.0)
+    f = f.astype(np.float64)
+    g = g.astype(np.float64)
+    subset, step, r = 11, 6, 2
+    nx, ny = oracle.grid(48, 48, subset, step, r)
+    n = nx * ny
+    z = np.zeros(n, np.int32)
+    ok = np.zeros(n, np.uint8)
+    gn = g.copy()
+    gn[:, :] = np.nan                                  # every subset sees NaN
+    for method in (oracle.ICGN, oracle.FANR):
+        s = oracle.subpixel(f, gn, subset, step, r, z, z, ok, method=method)
+        assert (s["status"] == oracle.ST_NONFINITE).all()
+        assert (s["p"] == 0).all() and (s["iters"] == 0).all()
+    ramp = np.tile(np.sin(np.arange(48) * 0.7) * 60 + 100, (48, 1))   # varies along x only
+    s = oracle.subpixel(ramp, g, subset, step, r, z, z, ok, method=oracle.ICGN)
+    assert (s["status"] == oracle.ST_SINGULAR).all()
+    assert (s["p"] == 0).all() and (s["iters"] == 0).all()
+    # FA-NR builds its Hessian from the target each iteration: singular at the
+    # first solve when g varies along x only
+    s = oracle.subpixel(f, ramp, subset, step, r, z, z, ok, method=oracle.FANR)
+    assert (s["status"] == oracle.ST_SINGULAR).all()
+    assert (s["p"] == 0).all() and (s["iters"] == 1).all()
+    # one NaN pixel stops only the POIs whose subsets contain it
+    k = n // 2
+    b = subset // 2 + r + 2
+    x0, y0 = b + (k % nx) * step, b + (k // nx) * step
+    g1 = g.copy()
+    g1[y0, x0] = np.nan
+    s = oracle.subpixel(f, g1, subset, step, r, z, z, ok, method=oracle.ICGN)
+    xs, ys = b + (np.arange(n) % nx) * step, b + (np.arange(n) // nx) * step
+    near = (np.abs(xs - x0) <= subset // 2 + 2) & (np.abs(ys - y0) <= subset // 2 + 2)
+    assert s["status"][k] == oracle.ST_NONFINITE
+    assert (s["status"][~near] != oracle.ST_NONFINITE).all()
+
+
 def test_bounds_rule_at_its_edges():
     """Reading R12: a shape is usable while every corner of the warped subset
     lies in [1, W-2) x [1, H-2) (the 4x4 stencil stays inside).  The ZNSSD
