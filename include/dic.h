@@ -287,17 +287,23 @@ dic_status dic_backward(dic_t h, const float *p6, const float *grad_loss, float 
  * the whole device-memory budget through its own allocator.
  *
  * Same arithmetic as dic_set_pair (precompute) followed by dic_subpixel, but
- * without a handle: the float deformed image and the gradient field go to one
- * fixed array inside the library (a static device symbol of 1.25 MiB, held by
- * every GPU that loads the library until the process exits).
+ * without a handle: the precompute output goes to one fixed array inside the
+ * library (a static device symbol of 1.25 MiB, held by every GPU that loads
+ * the library until the process exits), in three regions of 65536 pixels
+ * each: the float deformed image (4 bytes per pixel), the gradient field of
+ * the reference (8 bytes per pixel) and the BF16 tap quads of the deformed
+ * image (8 bytes per pixel).
  *   - width * height must be <= 65536 pixels (e.g. 256 x 256); larger
- *     images, and every other invalid argument, return DIC_ERR_ARG before any
- *     GPU work is enqueued.  Other arguments as in dic_create / dic_set_pair /
- *     dic_subpixel; solve_bits is 32 or 64; cuda_stream may be NULL.
+ *     images, search_radius > 1000 (as dic_create), and every other invalid
+ *     argument return DIC_ERR_ARG before any GPU work is enqueued.  Other
+ *     arguments as in dic_create / dic_set_pair / dic_subpixel; ref_dev and
+ *     def_dev share width, height and pitch_bytes; solve_bits is 32 or 64;
+ *     cuda_stream may be NULL.
  *   - Allocates nothing: no cudaMalloc, no cudaFree, no library allocator.
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  Later calls only enqueue two kernels.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ *     device may load the library's module there, so make it before any
+ *     stream capture.  Then the call enqueues two kernels.
  *   - All calls share the one array.  Each call overwrites every entry it
  *     reads, so no clearing is needed, but calls whose work overlaps on the
  *     GPU (different streams, or host threads) race on the array: serialise

@@ -266,7 +266,13 @@ def dic_subpixel_noalloc(ref, defm, subset_size, grid_step, search_radius, metho
                          max_iter=50, solve_bits=32, stream=None, width=None, height=None,
                          pitch=None) -> None:
     """Sub-pixel refinement with no device allocation (images up to 65536
-    pixels); see include/dic.h."""
+    pixels); see include/dic.h.  Both images are 8-bit with the same shape
+    and row stride (the library reads both with ref's geometry)."""
+    if ref.dtype.itemsize != 1 or defm.dtype.itemsize != 1 or ref.is_floating_point() \
+            or defm.is_floating_point():
+        raise RuntimeError("images must be 8-bit")
+    if tuple(ref.shape) != tuple(defm.shape) or ref.stride(-2) != defm.stride(-2):
+        raise RuntimeError("reference and deformed images need the same shape and row stride")
     hgt, wid = ref.shape[-2:]
     sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().dic_subpixel_noalloc(_ptr(ref), _ptr(defm), width or wid, height or hgt,

@@ -13,8 +13,6 @@
 // array that lives in this file as a static __device__ symbol.  Every GPU
 // that loads the library holds kNoAllocScratchBytes of it until the process
 // exits.
-#include <mutex>
-
 #include "dic_internal.cuh"
 
 namespace {
@@ -30,26 +28,15 @@ constexpr size_t kNoAllocScratchBytes = kGimgBytes + kGradBytes + kNoAllocMaxPix
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
-
 // Device address of the array on the current device.  In host code the
 // symbol's name is only a host-side stand-in, so the address has to come
-// from the runtime.  Done once per device.
+// from the runtime.  It is looked up on every call (the lookup allocates
+// nothing), so a module reloaded after a device reset is found again.
 cudaError_t scratch_on_current_device(unsigned char** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(p);
   return cudaSuccess;
 }
 
@@ -65,14 +52,18 @@ extern "C" dic_status dic_subpixel_noalloc(
     return DIC_ERR_ARG;
   if ((size_t)width * (size_t)height > kNoAllocMaxPixels) return DIC_ERR_ARG;
   if (subset_size < 3 || subset_size > dic::kMaxSubset || (subset_size & 1) == 0 ||
-      grid_step < 1 || search_radius < 0 || !(conv_tol > 0.f) || max_iter < 1)
+      grid_step < 1 || search_radius < 0 || search_radius > 1000 || !(conv_tol > 0.f) ||
+      max_iter < 1)
     return DIC_ERR_ARG;
   if (method != DIC_ICGN && method != DIC_FANR) return DIC_ERR_ARG;
   if (solve_bits != 32 && solve_bits != 64) return DIC_ERR_ARG;
-  const int M = subset_size / 2, B = M + search_radius + 2;
-  const int ax = width - 1 - 2 * B, ay = height - 1 - 2 * B;
-  const int nx = ax >= 0 ? ax / grid_step + 1 : 0;
-  const int ny = ay >= 0 ? ay / grid_step + 1 : 0;
+  // the margin B = M + R + 2 in 64 bits (R <= 1000 keeps it small; the
+  // grid is empty unless 2B < width and 2B < height)
+  const int M = subset_size / 2;
+  const int64_t B = (int64_t)M + search_radius + 2;
+  const int64_t ax = (int64_t)width - 1 - 2 * B, ay = (int64_t)height - 1 - 2 * B;
+  const int nx = ax >= 0 ? (int)(ax / grid_step + 1) : 0;
+  const int ny = ay >= 0 ? (int)(ay / grid_step + 1) : 0;
   if ((int64_t)nx * ny == 0) return DIC_OK;
   if (!u0 || !v0 || !status0 || !u || !v || !ux || !uy || !vx || !vy || !zncc || !iters ||
       !status)

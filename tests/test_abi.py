@@ -125,6 +125,11 @@ def test_form_and_noalloc_argument_checks():
     # images beyond the static array's limit are refused before any device work
     args = [16, 16, 1024, 1024, 1024, 21, 5, 10, 0, 1e-3, 50, 32] + [None] * 13
     assert lib.dic_subpixel_noalloc(*args) == dic.DIC_ERR_ARG
+    # a search radius beyond dic_create's bound is refused on the host (the
+    # margin M + R + 2 would overflow for radii near INT_MAX)
+    for radius in (1001, 2**31 - 1):
+        args = [16, 16, 256, 256, 256, 21, 5, radius, 0, 1e-3, 50, 32] + [None] * 13
+        assert lib.dic_subpixel_noalloc(*args) == dic.DIC_ERR_ARG
 
 
 def test_check_before_any_launch():
