@@ -11,6 +11,7 @@ follows the paper's method as stated in the C file's header:
 * ``subpixel``        -- IC-GN / Newton-Raphson (Section 2.2, Table 2) with
                          a first-order warp and Keys bicubic interpolation.
 * ``znssd``           -- summed ZNSSD and its hand-derived FP64 gradient.
+* ``zncc_at``         -- Eq. 1 at given shapes (interpolated target subset).
 * ``bicubic``         -- the bicubic interpolant itself (Section 2.2).
 * ``pso_search``      -- particle swarm integer search (Section 2.1, Eqs. 2-4)
                          and the modified swarm with the star search folded in.
@@ -40,7 +41,8 @@ def build(force: bool = False) -> str:
     """Compile the oracle (gcc -O2 -fopenmp, no fast-math)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-std=c11",
                                "-Wall", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -71,6 +73,9 @@ def _load():
             lib.dico_bicubic.restype = dbl
             lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P, P]
             lib.dico_znssd.restype = i32
+            lib.dico_zncc_at.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, P, i64, P,
+                                         i32, P]
+            lib.dico_zncc_at.restype = i32
             lib.dico_pso_search.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, i32,
                                             i32, i32, dbl, dbl, dbl, i64, i64, P, i32, P, P,
                                             P, P, P, P, P]
@@ -155,6 +160,28 @@ def subpixel(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
                zncc=zn, iters=it, status=st, nx=nx, ny=ny)
     if trajectory:
         out["traj"] = traj
+    return out
+
+
+def zncc_at(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, p: np.ndarray,
+            poi_idx=None, interp: int = BICUBIC, threads: int | None = None) -> np.ndarray:
+    """Eq. 1 at the given shapes ``p`` (n x 6): reference subset against the
+    interpolated target grey levels at the warped subset points.  NaN where
+    the warped subset leaves the image or either subset is flat."""
+    f = np.ascontiguousarray(f, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    H, W = f.shape
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        nx, ny = grid(W, H, subset, step, radius)
+        n = nx * ny
+    p = np.ascontiguousarray(p, np.float64).reshape(n, 6)
+    out = np.zeros(n, np.float64)
+    rc = _load().dico_zncc_at(_ptr(f), _ptr(g), W, H, W, subset, step, radius, interp,
+                              _ptr(idx), n if idx is not None else -1, _ptr(p),
+                              threads or default_threads(), _ptr(out))
+    if rc:
+        raise ValueError("oracle zncc_at failed")
     return out
 
 

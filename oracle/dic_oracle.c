@@ -525,6 +525,55 @@ int dico_subpixel_interp(const double *f, const double *g, int W, int H, int pit
   return 0;
 }
 
+/* Eq. 1 at given shapes: for POI k, the ZNCC of the reference subset and the
+ * target grey levels interpolated (mode 0 bicubic, 1 bilinear) at the warped
+ * subset points W(xi; p_k), C = sum (f_i - fbar)(g_i - gbar) / (df dg).
+ * A POI whose warped subset leaves [1, W-2) x [1, H-2), or whose reference
+ * or target subset is flat, gets NAN. */
+int dico_zncc_at(const double *f, const double *g, int W, int H, int pitch, int subset,
+                 int step, int R, int mode, const int64_t *poi_idx, int64_t n_idx,
+                 const double *p, int nthreads, double *zncc) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  if (mode != 0 && mode != 1) return -1;
+  const int M = subset / 2, S = subset, N = S * S;
+  const int64_t n = poi_idx ? n_idx : (int64_t)nx * ny;
+  if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+  {
+    double *fc = malloc(sizeof(double) * N * 2);
+    double *gv = fc + N;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n; ++k) {
+      int64_t poi = poi_idx ? poi_idx[k] : k;
+      int x0, y0;
+      poi_centre(poi, nx, M, R, step, &x0, &y0);
+      const double *pk = &p[k * 6];
+      zncc[k] = NAN;
+      if (!in_bounds(pk, x0, y0, M, W, H)) continue;
+      double fs = 0;
+      for (int i = 0; i < N; ++i) {
+        int dx = i % S - M, dy = i / S - M;
+        fc[i] = f[(int64_t)(y0 + dy) * pitch + (x0 + dx)];
+        fs += fc[i];
+      }
+      double fbar = fs / N, q = 0;
+      for (int i = 0; i < N; ++i) {
+        fc[i] -= fbar;
+        q += fc[i] * fc[i];
+      }
+      double df = sqrt(q), gbar, dg;
+      sample_subset(g, pitch, pk, x0, y0, M, mode, gv, NULL, NULL, &gbar, &dg);
+      if (!(df > 0.0) || !(dg > 0.0)) continue;
+      double c = 0;
+      for (int i = 0; i < N; ++i) c += fc[i] * (gv[i] - gbar);
+      zncc[k] = c / (df * dg);
+    }
+    free(fc);
+  }
+  return 0;
+}
+
 int dico_subpixel(const double *f, const double *g, int W, int H, int pitch, int subset,
                   int step, int R, int method, double tol, int max_iter,
                   const int64_t *poi_idx, int64_t n_idx, const int32_t *u0,

@@ -73,13 +73,60 @@ def compare_search(gpu: dict, ref: dict, idx=None) -> None:
     assert np.abs(gpu["zncc0"][sel] - ref["zncc"]).max() < TOL_ZNCC
 
 
+def oracle_iterates(f, g, subset, step, radius, start: dict, method: int, ref: dict, k,
+                    idx=None, interp: int = 0) -> np.ndarray:
+    """The oracle's shape after k[j] solves for POI j: its recorded trajectory
+    where it ran that far, else a rerun capped at k[j] solves with a
+    tolerance that never stops it.  A solve whose update was rejected (the
+    subset would leave the image, or the step is not finite) counts in the
+    iteration count but leaves the shape unchanged, so the trajectory has no
+    entry for it: the shape is then the one before it."""
+    k = np.asarray(k)
+    out = np.full((len(k), 6), np.nan)
+    have = k <= ref["iters"]
+    rows = np.nonzero(have)[0]
+    out[rows] = ref["traj"][rows, k[rows]]
+    rej = rows[np.isnan(out[rows]).any(1) & (k[rows] >= 1)]
+    out[rej] = ref["traj"][rej, k[rej] - 1]
+    sel = None if idx is None else np.asarray(idx)
+    for kk in np.unique(k[~have]):
+        rows = np.nonzero(~have & (k == kk))[0]
+        sub = oracle.subpixel(f, g, subset, step, radius, start["u0"][rows], start["v0"][rows],
+                              start["status"][rows], method=method, tol=1e-300,
+                              max_iter=int(kk), poi_idx=(sel[rows] if sel is not None else rows),
+                              interp=interp)
+        out[rows] = sub["p"]
+    return out
+
+
 def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method: int,
                      tol: float = 1e-3, max_iter: int = 50, idx=None,
-                     min_iter_agreement: float = 0.9, min_compared: float = 0.0,
-                     interp: int = 0) -> dict:
-    """Shape parameters of every POI against the oracle's iterate at the
-    GPU's own iteration count (the stop test can fall on either side of the
-    tolerance in FP32 versus FP64)."""
+                     min_iter_agreement: float = 0.99, min_compared: float = 0.99,
+                     interp: int = 0, label: str = "") -> dict:
+    """Every POI's sub-pixel result against the FP64 oracle (reading P1).
+
+    * Statuses agree exactly, POI by POI (a swap between OK and MAX_ITER, the
+      FP32 stop test falling on the other side of the tolerance at the cap,
+      is counted and allowed for at most 0.1 % of the POIs).
+    * Iteration counts agree on at least ``min_iter_agreement`` of the POIs.
+    * Shapes: the GPU's shape after its k solves against the oracle's
+      iterate after k solves (the stop test can end the two runs one solve
+      apart), u and v within 1e-3 px, gradients within 1e-5.  Every POI that
+      converged (OK) must be inside the tolerance.  A POI that did not
+      converge (MAX_ITER, or OUT_OF_BOUNDS: the last in-bounds iterate of an
+      iteration that left the image) followed a non-contracting iteration
+      whose FP32 and FP64 rounding differences grow with every solve, so its
+      shape is not a parity quantity: it is counted ("wandering") when it
+      falls outside the tolerance, and checked for validity instead -- its
+      reported ZNCC must equal the oracle's Eq. 1 at the GPU's own returned
+      shape.  The share of POIs compared inside the tolerance must reach
+      ``min_compared``.
+    * ZNCC: a converged POI reports Eq. 1 at the shape its last solve
+      sampled (reading R11), compared with the oracle's Eq. 1 at its iterate
+      after k - 1 solves; every other POI that ran reports Eq. 1 at its
+      returned shape, compared with the oracle's Eq. 1 at that same shape.
+      Both within 1e-5.
+    """
     sel = np.arange(len(gpu["u"])) if idx is None else np.asarray(idx)
     ref = oracle.subpixel(f, g, subset, step, radius, start["u0"], start["v0"], start["status"],
                           method=method, tol=tol, max_iter=max_iter, poi_idx=idx,
@@ -87,46 +134,56 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
     gp = gpu["p"][sel]
     git = gpu["iters"][sel]
     gst = gpu["status"][sel]
-    want = ref["p"].copy()
-    same = (git == ref["iters"]) & (gst == ref["status"])
-    diff = np.nonzero(~same)[0]
-    # iterate k of the oracle for the POIs where the counts differ
-    for k in np.unique(git[diff]):
-        rows = diff[git[diff] == k]
-        if k == 0:
-            continue
-        if np.all(k <= ref["iters"][rows]):
-            want[rows] = ref["traj"][rows, k]
-        else:
-            sub = oracle.subpixel(f, g, subset, step, radius, start["u0"][rows],
-                                  start["v0"][rows], start["status"][rows], method=method,
-                                  tol=0.0 + 1e-300, max_iter=int(k),
-                                  poi_idx=(sel[rows] if idx is not None else rows),
-                                  interp=interp)
-            want[rows] = sub["p"]
+    rit, rst = ref["iters"], ref["status"]
+    n = len(gst)
+    swap = (gst != rst) & np.isin(gst, (0, 3)) & np.isin(rst, (0, 3))
+    assert swap.sum() <= 0.001 * n, ("OK/MAX_ITER swaps", int(swap.sum()))
+    np.testing.assert_array_equal(gst[~swap], rst[~swap], err_msg=label + " statuses")
+    agree = float((git == rit).mean())
+    assert agree >= min_iter_agreement, (label, "iteration agreement", agree)
+
+    want = oracle_iterates(f, g, subset, step, radius, start, method, ref, git, idx, interp)
     err = np.abs(gp - want)
-    # shapes are compared where both sides converged; a POI that ran to the
-    # iteration cap follows an unconverged (possibly wandering) path whose
-    # FP32 and FP64 iterates need not stay within the tolerance
-    # A POI whose two paths took different numbers of steps by more than one
-    # wandered (ill-conditioned fit); it is counted, not compared.
-    ok_status = (gst == 0) & (ref["status"] == 0) & (np.abs(git - ref["iters"]) <= 1)
-    bad = np.nonzero(ok_status & (err[:, [0, 3]].max(1) >= TOL_UV))[0]
-    assert len(bad) == 0, dict(poi=bad[:5], gpu=gp[bad[:5]], want=want[bad[:5]],
-                               git=git[bad[:5]], rit=ref["iters"][bad[:5]])
-    bad = np.nonzero(ok_status & (err[:, [1, 2, 4, 5]].max(1) >= TOL_GRAD))[0]
-    assert len(bad) == 0, dict(poi=bad[:5], gpu=gp[bad[:5]], want=want[bad[:5]],
-                               git=git[bad[:5]], rit=ref["iters"][bad[:5]])
-    agree = same.mean()
-    assert agree >= min_iter_agreement, agree
-    both_ok = (gst == 0) & (ref["status"] == 0)
-    assert ok_status.sum() >= min_compared * both_ok.sum(), (ok_status.sum(), both_ok.sum())
-    # statuses other than OK / MAX_ITER must agree exactly
-    hard = ~np.isin(ref["status"], (0, 3)) | ~np.isin(gst, (0, 3))
-    np.testing.assert_array_equal(gst[hard], ref["status"][hard])
-    zs = same & (gst == 0)
-    assert np.abs(gpu["zncc"][sel][zs] - ref["zncc"][zs]).max(initial=0) < TOL_ZNCC
-    return dict(iter_agreement=float(agree), compared=int(ok_status.sum()), n=len(gst),
-                max_iter=int((gst == 3).sum()),
-                max_err_uv=float(err[ok_status][:, [0, 3]].max(initial=0)),
-                max_err_grad=float(err[ok_status][:, [1, 2, 4, 5]].max(initial=0)))
+    # NaN (no comparable iterate) counts as outside the tolerance
+    over = ~(err[:, [0, 3]].max(1) < TOL_UV) | ~(err[:, [1, 2, 4, 5]].max(1) < TOL_GRAD)
+    ran = git >= 1
+    conv = ran & (gst == 0)
+    wander = ran & (gst != 0)
+    bad = np.nonzero(conv & over)[0]
+    assert len(bad) == 0, dict(label=label, poi=bad[:5], gpu=gp[bad[:5]], want=want[bad[:5]],
+                               git=git[bad[:5]], rit=rit[bad[:5]])
+    n_wander_over = int((wander & over).sum())
+    compared = int(ran.sum()) - n_wander_over
+    assert compared >= min_compared * ran.sum(), (label, "compared", compared, int(ran.sum()))
+
+    # ZNCC: converged POIs at the oracle's iterate after k - 1 solves,
+    # every other POI that ran at the GPU's returned shape
+    zg = gpu["zncc"][sel]
+    zs_conv = np.nonzero(conv)[0]
+    zerr_conv = 0.0
+    if len(zs_conv):
+        before = oracle_iterates(f, g, subset, step, radius,
+                                 {k: v[zs_conv] for k, v in start.items()
+                                  if k in ("u0", "v0", "status")},
+                                 method, {k: (v[zs_conv] if hasattr(v, "__len__") else v)
+                                          for k, v in ref.items()},
+                                 git[zs_conv] - 1, sel[zs_conv], interp)
+        c = oracle.zncc_at(f, g, subset, step, radius, before,
+                           poi_idx=sel[zs_conv], interp=interp)
+        zerr_conv = float(np.abs(zg[zs_conv] - c).max())
+        assert zerr_conv < TOL_ZNCC, (label, "zncc converged", zerr_conv)
+    zs_other = np.nonzero(ran & np.isin(gst, (2, 3)))[0]
+    zerr_other = 0.0
+    if len(zs_other):
+        c = oracle.zncc_at(f, g, subset, step, radius, gp[zs_other].astype(np.float64),
+                           poi_idx=sel[zs_other], interp=interp)
+        zerr_other = float(np.abs(zg[zs_other] - c).max())
+        assert zerr_other < TOL_ZNCC, (label, "zncc at returned shape", zerr_other)
+    st = dict(label=label, n=n, ran=int(ran.sum()), converged=int(conv.sum()),
+              not_converged=int(wander.sum()), wandering_outside_tol=n_wander_over,
+              compared_within_tol=compared, iter_agreement=agree, ok_maxiter_swaps=int(swap.sum()),
+              max_err_uv=float(err[ran][:, [0, 3]].max(initial=0)),
+              max_err_grad=float(err[ran][:, [1, 2, 4, 5]].max(initial=0)),
+              max_err_zncc_converged=zerr_conv, max_err_zncc_other=zerr_other)
+    print("parity", st)
+    return st

@@ -33,30 +33,31 @@ def test_rigid256_full(rigid256, method, solve_bits):
     ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
     assert gpu["n"] == 484
     compare_search(gpu, ref)
-    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method,
-                          min_compared=0.99)
-    print(st)
+    compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method,
+                     label=f"rigid256 m{method} fp{solve_bits}")
 
 
-# ------------------------------------------- bench workload, sampled POIs
-@pytest.mark.parametrize("method,solve_bits", [(0, 32), (0, 64), (1, 32), (1, 64)])
-def test_affine1024_sampled(affine1024, method, solve_bits):
+# ------------------------------------------------- bench workload, all POIs
+@pytest.fixture(scope="module")
+def affine_search(affine1024):
+    p = affine1024
+    return oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
+
+
+@pytest.mark.parametrize("method,solve_bits,form", [(0, 32, 1), (0, 64, 1), (1, 32, 1),
+                                                    (1, 64, 1), (0, 64, 0)])
+def test_affine1024_full(affine1024, affine_search, method, solve_bits, form):
+    """The bench workload (1024x1024, subset 31, step 5, search +-20) at all
+    36100 POIs: integer search bit-exact in both search forms, every POI's
+    sub-pixel result against the oracle."""
     p = affine1024
     gpu = run_gpu(p.ref, p.defm, p.subset, p.step, p.radius, method=method,
-                  solve_bits=solve_bits)
+                  solve_bits=solve_bits, form=form)
     assert gpu["n"] == 36100
-    rng = np.random.default_rng(11)
-    idx = np.sort(rng.choice(gpu["n"], 1500, replace=False))
-    # include the first and last rows and columns of the grid
-    nx = gpu["nx"]
-    edge = np.unique(np.r_[np.arange(nx), gpu["n"] - nx + np.arange(nx), np.arange(0, gpu["n"], nx)])
-    idx = np.unique(np.r_[idx, edge])
-    ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx)
-    compare_search(gpu, ref, idx)
-    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method, idx=idx,
-                          min_compared=0.99)
-    print(st)
-    # properties at every POI: integer start within the window, results finite
+    compare_search(gpu, affine_search)
+    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, affine_search, method,
+                          label=f"affine1024 m{method} fp{solve_bits} form{form}")
+    assert st["compared_within_tol"] == st["n"] == 36100
     assert (np.abs(gpu["u0"]) <= p.radius).all() and (np.abs(gpu["v0"]) <= p.radius).all()
     assert np.isfinite(gpu["p"]).all()
     assert (gpu["status"] == 0).mean() > 0.99
@@ -72,26 +73,23 @@ def test_bilinear_rigid256_full(rigid256, method):
                   interp=1)
     ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius)
     compare_search(gpu, ref)
-    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method,
-                          min_compared=0.99, interp=oracle.BILINEAR)
-    print(st)
+    compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method,
+                     interp=oracle.BILINEAR, label=f"rigid256 bilinear m{method}")
     assert np.abs(gpu["u"] - 3.4).max() < 0.1 and np.abs(gpu["v"] + 2.7).max() < 0.1
 
 
 @pytest.mark.parametrize("method", [0, 1])
-def test_bilinear_affine1024_sampled(affine1024, method):
+def test_bilinear_affine1024_full(affine1024, affine_search, method):
+    """Eq. 5 interpolation on the bench workload, all 36100 POIs."""
     p = affine1024
     gpu = run_gpu(p.ref, p.defm, p.subset, p.step, p.radius, method=method, solve_bits=64,
                   form=1, interp=1)
-    idx = np.sort(np.random.default_rng(12).choice(gpu["n"], 600, replace=False))
-    ref = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx)
-    compare_search(gpu, ref, idx)
-    st = compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, ref, method, idx=idx,
-                          min_compared=0.99, interp=oracle.BILINEAR)
-    print(st)
+    compare_search(gpu, affine_search)
+    compare_subpixel(gpu, p.ref, p.defm, p.subset, p.step, p.radius, affine_search, method,
+                     interp=oracle.BILINEAR, label=f"affine1024 bilinear m{method}")
     # FA-NR over Eq. 5 follows a gradient that jumps at cell edges, so a few
-    # POIs oscillate to the iteration cap (the oracle's do too: the status
-    # and iteration counts above agree); IC-GN's gradient is f's and smooth
+    # POIs oscillate to the iteration cap (the oracle's do too: the statuses
+    # agree POI by POI); IC-GN's gradient is f's and smooth
     assert (gpu["status"] == 0).mean() > (0.99 if method == 0 else 0.97)
 
 
@@ -138,15 +136,22 @@ def test_smallest_subset_search():
     (51, 20, 5, 140),
     (63, 30, 3, 150),   # largest subset
 ])
-def test_sizes(subset, step, radius, size):
+@pytest.mark.parametrize("method", [0, 1])
+def test_sizes(subset, step, radius, size, method):
+    """Every POI against the oracle.  Subsets 5 and 9 are smaller than the
+    speckles (radius 2.5-4 px), so most of their six-parameter fits are
+    ill-posed and do not converge; their non-converged shapes are not a
+    parity quantity (checked for validity instead, see compare_subpixel),
+    and the bar on POIs inside the tolerance is 0.9 there, 0.99 elsewhere."""
     f, g = configs.tiny(1000 + subset, size, size, int(0.03 * size * size),
                         Rigid(1.4, -0.7), noise=1.5)
-    gpu = run_gpu(f, g, subset, step, radius, method=0, solve_bits=64)
+    gpu = run_gpu(f, g, subset, step, radius, method=method, solve_bits=64)
     ref = oracle.integer_search(f, g, subset, step, radius)
     assert gpu["n"] == len(ref["u0"]) > 0
     compare_search(gpu, ref)
-    st = compare_subpixel(gpu, f, g, subset, step, radius, ref, 0, min_iter_agreement=0.8)
-    print(subset, st)
+    compare_subpixel(gpu, f, g, subset, step, radius, ref, method,
+                     min_compared=0.9 if subset <= 9 else 0.99,
+                     label=f"subset {subset} m{method}")
 
 
 def test_unaligned_pitch_uses_plain_loads():

@@ -569,3 +569,80 @@ def test_adjoint_matches_central_differences():
         fd = (oracle.znssd(f, gp, p=p, grad=False, **kw)
               - oracle.znssd(f, gm, p=p, grad=False, **kw)) / 2e-3
         assert dg[y, x] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+# ------------------------------------------------- Eq. 1 at a given shape
+@pytest.mark.parametrize("interp", [oracle.BICUBIC, oracle.BILINEAR])
+def test_zncc_at_integer_shapes_is_the_exact_search_value(interp):
+    """At integer shapes every warped point is a pixel, where both
+    interpolants give the pixel itself, so Eq. 1 at (u0, 0, 0, v0, 0, 0)
+    must be the brute-force search's value, which comes from exact integer
+    sums (independent code); and Eq. 1 written out literally here at a few
+    POIs."""
+    f, g = configs.tiny(31, 64, 60, 160, Rigid(1.6, -2.3), noise=2.0)
+    s = oracle.integer_search(f, g, 9, 6, 4)
+    n = len(s["u0"])
+    p = np.zeros((n, 6))
+    p[:, 0], p[:, 3] = s["u0"], s["v0"]
+    c = oracle.zncc_at(f, g, 9, 6, 4, p, interp=interp)
+    assert np.abs(c - s["zncc"]).max() < 1e-12
+    nx = s["nx"]
+    b = 4 + 4 + 2
+    for k in (0, n // 2, n - 1):
+        x0, y0 = b + (k % nx) * 6, b + (k // nx) * 6
+        lit = _eq1_map(f, g, x0, y0, 4, 4)[s["v0"][k] + 4, s["u0"][k] + 4]
+        assert abs(c[k] - lit) < 1e-12
+
+
+def test_zncc_at_invariance_bounds_and_flat_subsets():
+    """Eq. 1 at a non-integer shape is invariant under g -> a g + b (a > 0)
+    and flips sign for a < 0; it equals 1 - L/2 with L the summed ZNSSD of
+    the same subset; shapes that push a corner off [1, W-2) and flat
+    reference subsets give NaN."""
+    f, g = configs.tiny(32, 70, 70, 200, Rigid(0.4, 0.7), noise=1.0)
+    nx, ny = oracle.grid(70, 70, 11, 7, 3)
+    n = nx * ny
+    rng = np.random.default_rng(5)
+    p = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-0.02, 0.02, n),
+                         rng.uniform(-0.02, 0.02, n), rng.uniform(-1, 1, n),
+                         rng.uniform(-0.02, 0.02, n), rng.uniform(-0.02, 0.02, n)])
+    c = oracle.zncc_at(f, g, 11, 7, 3, p)
+    assert np.isfinite(c).all() and (np.abs(c) <= 1 + 1e-12).all()
+    c2 = oracle.zncc_at(f, 1.7 * g.astype(np.float64) + 13.0, 11, 7, 3, p)
+    assert np.abs(c2 - c).max() < 1e-12
+    c3 = oracle.zncc_at(f, 255.0 - g.astype(np.float64), 11, 7, 3, p)
+    assert np.abs(c3 + c).max() < 1e-12
+    _, _, _, lp = oracle.znssd(f, g, 11, 7, 3, p, per_poi=True)
+    assert np.abs((1 - lp / 2) - c).max() < 1e-12
+    q = p.copy()
+    q[0, 0] = -40.0
+    assert np.isnan(oracle.zncc_at(f, g, 11, 7, 3, q)[0])
+    flat = np.full_like(f, 77)
+    assert np.isnan(oracle.zncc_at(flat, g, 11, 7, 3, p)).all()
+
+
+@pytest.mark.parametrize("interp", [oracle.BICUBIC, oracle.BILINEAR])
+def test_zncc_at_non_integer_shape_written_out(interp):
+    """Eq. 1 written out here at a non-integer first-order shape: the warp of
+    every subset point, the (separately pinned) interpolant sampled point by
+    point, means subtracted, normalised."""
+    f, g = configs.tiny(33, 48, 48, 110, Rigid(0.3, -0.2), noise=1.0)
+    subset, step, r = 7, 9, 2
+    nx, ny = oracle.grid(48, 48, subset, step, r)
+    k = nx + 1
+    x0, y0 = 3 + 2 + 2 + (k % nx) * step, 3 + 2 + 2 + (k // nx) * step
+    pk = np.array([0.37, 0.021, -0.013, -0.61, 0.008, 0.017])
+    p = np.zeros((nx * ny, 6))
+    p[k] = pk
+    c = oracle.zncc_at(f, g, subset, step, r, p, interp=interp)[k]
+    sample = oracle.bicubic if interp == oracle.BICUBIC else oracle.bilinear
+    a, b = [], []
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            a.append(float(f[y0 + dy, x0 + dx]))
+            x = x0 + dx + pk[0] + pk[1] * dx + pk[2] * dy
+            y = y0 + dy + pk[3] + pk[4] * dx + pk[5] * dy
+            b.append(sample(g, x, y)[0])
+    a, b = np.array(a) - np.mean(a), np.array(b) - np.mean(b)
+    lit = (a * b).sum() / math.sqrt((a * a).sum() * (b * b).sum())
+    assert abs(c - lit) < 1e-12
