@@ -86,6 +86,11 @@ def parse():
                     help="affine1024 is the headline; the others measure the batched form "
                          "and the adjoint")
     ap.add_argument("--pairs", type=int, default=0, help="limit the number of pairs (0 = all)")
+    ap.add_argument("--sub-records", default="all", choices=["all", "none"],
+                    help="add the batched (sine2048x64, mixed32) and adjoint (affine1024x8) "
+                         "records to the default line (1 GPU only)")
+    ap.add_argument("--sub-steps", type=int, default=5)
+    ap.add_argument("--sub-warmup", type=int, default=3)
     return ap.parse_args()
 
 
@@ -140,7 +145,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "10"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -397,9 +402,36 @@ def run_gpu(args):
                                "precompute_ms": pre_bytes / hbm * 1e3},
                      "hbm_basis": "measured" if peaks_all else "fallback"}
 
+    # measured FP32 FMA throughput beside the nominal peak the fraction uses
+    fp32_meas = dic.dic_measure_peak(dic.DIC_PEAK_FP32_FMA, stream) / 1e12
+    roofline["measured_fma_peak"] = fp32_meas
+    roofline["frac_of_measured_fma"] = sub_achieved / fp32_meas
+    sub_records = None
+    if world == 1 and args.sub_records == "all":
+        d.close()
+        for dd in (d32, dob, dnr, dbl):
+            dd.close()
+        del flush
+        torch.cuda.empty_cache()
+        t_sub = time.perf_counter()
+        atomic_peak = dic.dic_measure_peak(dic.DIC_PEAK_SMEM_ATOMIC_F32, stream)
+        sub_records = {
+            "batch_sine2048x64": batch_record("sine2048x64", dev, args.sub_steps,
+                                              args.sub_warmup, solve_bits=args.solve_bits,
+                                              fp32_peak=fp32_peak),
+            "batch_mixed32": batch_record("mixed32", dev, args.sub_steps, args.sub_warmup,
+                                          solve_bits=args.solve_bits, fp32_peak=fp32_peak),
+            "adjoint_affine1024x8": adjoint_record(dev, args.sub_steps, args.sub_warmup,
+                                                   fp32_peak=fp32_peak,
+                                                   atomic_peak=atomic_peak),
+            "measured_peaks": {"fp32_fma_tflops": fp32_meas,
+                               "smem_atomic_f32_per_s": atomic_peak},
+            "wall_s": None}
+        sub_records["wall_s"] = time.perf_counter() - t_sub
+
     cpu = None
     if rank == 0:
-        cpu = cpu_baseline(pair, args.cpu_sample)
+        cpu = cpu_baseline(pair, args.cpu_sample, single=True)
     if world > 1:
         torch.distributed.barrier()
     if rank == 0:
@@ -429,7 +461,8 @@ def run_gpu(args):
                                               "value": bil_value, "subpixel_ms": bil_sub_ms},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
                                          "value": plain_value}},
-                "converged_fraction": conv / n, "wall_s_timed": wall}
+                "converged_fraction": conv / n, "wall_s_timed": wall,
+                "sub_records": sub_records}
         print(json.dumps(line))
     d.close()
     if world > 1:
@@ -443,7 +476,7 @@ def cpu_sample_idx(n: int, k: int):
     return np.unique(np.linspace(0, n - 1, k).round().astype(np.int64))
 
 
-def cpu_baseline(pair, sample: int) -> dict:
+def cpu_baseline(pair, sample: int, single: bool = False) -> dict:
     """The FP64 oracle, as it stands, on an evenly spaced POI sample of the
     same pair, on every host core."""
     import numpy as np
@@ -459,8 +492,22 @@ def cpu_baseline(pair, sample: int) -> dict:
                         r["status"], tol=TOL, max_iter=MAX_ITER, poi_idx=idx, threads=threads)
     dt = time.perf_counter() - t0
     conv = int((s["status"] == 0).sum())
-    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{len(idx)} evenly spaced POIs of {WORKLOAD} (search + IC-GN), {dt:.1f} s"}
+    out = {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{len(idx)} evenly spaced POIs of {WORKLOAD} (search + IC-GN), {dt:.1f} s"}
+    if single:
+        # the same oracle on one host core, on a smaller evenly spaced sample
+        idx1 = cpu_sample_idx(nx * ny, 256)
+        t0 = time.perf_counter()
+        r = oracle.integer_search(pair.ref, pair.defm, SUBSET, STEP, RADIUS, poi_idx=idx1,
+                                  threads=1)
+        s = oracle.subpixel(pair.ref, pair.defm, SUBSET, STEP, RADIUS, r["u0"], r["v0"],
+                            r["status"], tol=TOL, max_iter=MAX_ITER, poi_idx=idx1, threads=1)
+        dt1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": int((s["status"] == 0).sum()) / dt1, "unit": UNIT,
+                                "cores": 1, "sample": f"{len(idx1)} evenly spaced POIs, "
+                                                      f"{dt1:.1f} s"}
+        out["cpu_model"] = cpu_model()
+    return out
 
 
 def run_reference(args):
@@ -496,115 +543,141 @@ def run_reference(args):
 
 
 # ------------------------------------------------- batched / adjoint forms
-def run_batch_workload(args):
-    """Many pairs in one CUDA graph of persistent kernels (sine2048x64,
-    mixed32) against the same pairs run one by one through the single-pair
-    calls; or the ZNSSD adjoint over the 8-pair differentiation set."""
+def cpu_model() -> str:
+    """Host CPU model (lscpu's model name, else /proc/cpuinfo, else the
+    machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_sample(pairs, pair_ids, pois_per_pair: int, threads: int) -> dict:
+    """The FP64 oracle (integer search + IC-GN), as it stands, on evenly
+    spaced POIs of the chosen pairs; converged POIs per second."""
     import numpy as np
+
+    import oracle
+    conv, n, dt = 0, 0, 0.0
+    for k in pair_ids:
+        p = pairs[k]
+        nx, ny = oracle.grid(p.ref.shape[1], p.ref.shape[0], p.subset, p.step, p.radius)
+        idx = cpu_sample_idx(nx * ny, pois_per_pair)
+        t0 = time.perf_counter()
+        r = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx,
+                                  threads=threads)
+        s = oracle.subpixel(p.ref, p.defm, p.subset, p.step, p.radius, r["u0"], r["v0"],
+                            r["status"], tol=TOL, max_iter=MAX_ITER, poi_idx=idx,
+                            threads=threads)
+        dt += time.perf_counter() - t0
+        conv += int((s["status"] == 0).sum())
+        n += len(idx)
+    return {"value": conv / dt, "seconds": dt, "pois": n}
+
+
+def subpixel_work(iters, status, status0, subset: int) -> tuple[int, int]:
+    """Interpolated and first-pass pixel samples of one sub-pixel launch: one
+    pass per solve (the first at the integer start reads pixels) plus one
+    interpolating pass at the returned shape for POIs that did not
+    converge; N = subset^2 samples per pass."""
+    import torch
+    its = iters.to(torch.int64)
+    ran = (status0 == 0) & (its >= 1)
+    extra = (status != 0).to(torch.int64)
+    n = subset * subset
+    return (int(((its - 1) + extra)[ran].sum().item()) * n, int(ran.sum().item()) * n)
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+def batch_record(workload: str, dev, steps: int, warmup: int, form: int = 1,
+                 solve_bits: int = 64, n_pairs: int = 0, cpu_pairs: int = 4,
+                 cpu_pois: int = 1024, plain_steps: int = 1, fp32_peak: float | None = None,
+                 clocks: bool = True) -> dict:
+    """Many pairs in one CUDA graph (sine2048x64, mixed32): converged POI/s of
+    the batch (autotuned launch shape), the same pairs through the
+    single-pair calls (per-kernel times and rooflines from CUDA events on the
+    launching stream), the plain FP32-search batch, and the oracle on a
+    sample of the same pairs."""
     import torch
 
     import paper_1905_06228_gb300 as dic
     from workloads import configs
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    dic.build()
-    if args.workload == "sine2048x64":
-        n_pairs = args.pairs or 64
+    if workload == "sine2048x64":
+        n_pairs = n_pairs or 64
         pairs = [configs.sine2048(k) for k in range(n_pairs)]
-    elif args.workload == "mixed32":
-        n_pairs = args.pairs or 32
-        pairs = [configs.mixed(k) for k in range(n_pairs)]
     else:
-        n_pairs = args.pairs or 8
-        pairs = [configs.affine1024x8(k) for k in range(n_pairs)]
+        n_pairs = n_pairs or 32
+        pairs = [configs.mixed(k) for k in range(n_pairs)]
+    props = torch.cuda.get_device_properties(dev)
+    if fp32_peak is None:
+        fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+    peaks = load_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
     h = dic.dic_create(21, 5, 10, 1, TOL, MAX_ITER)
-    dic.dic_set_solve_precision(h, args.solve_bits)
+    dic.dic_set_solve_precision(h, solve_bits)
     stream = torch.cuda.Stream(dev)
     dic.dic_set_stream(h, stream)
-    skipped = []
-    tens = []
-    for k, p in enumerate(pairs):
-        tens.append((torch.from_numpy(p.ref).to(dev), torch.from_numpy(p.defm).to(dev),
-                     p.subset, p.step, p.radius))
+    tens = [(torch.from_numpy(p.ref).to(dev), torch.from_numpy(p.defm).to(dev),
+             p.subset, p.step, p.radius) for p in pairs]
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    if args.workload == "affine1024x8":
-        # adjoint: forward ZNSSD + backward at the imposed shapes, all pairs
-        results = []
-        total_ms = 0.0
-        n_poi = 0
-        for k, (f8, g8, s_, st_, r_) in enumerate(tens):
-            p = pairs[k]
-            nx = (1024 - 1 - 2 * (s_ // 2 + r_ + 2)) // st_ + 1
-            n = nx * nx
-            b = s_ // 2 + r_ + 2
-            kk = np.arange(n)
-            x0 = (b + (kk % nx) * st_).astype(np.float64)
-            y0 = (b + (kk // nx) * st_).astype(np.float64)
-            shp = torch.from_numpy(np.stack(p.deformation.displacement(x0, y0), 1)
-                                   .astype(np.float32)).to(dev).contiguous()
-            f = f8.float().contiguous()
-            g = g8.float().contiguous()
-            hh = dic.dic_create(s_, st_, r_)
-            dic.dic_set_stream(hh, stream)
-            dg = torch.empty_like(g)
-            dp = torch.empty_like(shp)
-            tot = torch.empty((), dtype=torch.float32, device=dev)
-            with torch.cuda.stream(stream):
-                dic.dic_set_pair_f32(hh, f, g)
-                for _ in range(args.warmup):
-                    dic.dic_znssd(hh, shp, None, tot)
-                    dic.dic_backward(hh, shp, None, 1.0, dg, dp)
-                torch.cuda.synchronize(dev)
-                a, e = ev(), ev()
-                a.record(stream)
-                for _ in range(args.steps):
-                    dic.dic_znssd(hh, shp, None, tot)
-                    dic.dic_backward(hh, shp, None, 1.0, dg, dp)
-                e.record(stream)
-            torch.cuda.synchronize(dev)
-            total_ms += a.elapsed_time(e) / args.steps
-            n_poi += n
-            dic.dic_destroy(hh)
-        samples = n_poi * SUBSET * SUBSET
-        line = {"metric": "adjoint POI/s (ZNSSD forward + backward)", "value": n_poi / (total_ms / 1e3),
-                "unit": "POI/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded speckle renders)",
-                "config": {"workload": "affine1024x8", "pairs": n_pairs, "pois": n_poi,
-                           "subset": 31, "grid_step": 8},
-                "samples_per_s": samples / (total_ms / 1e3),
-                "scatter_atomics_per_s": 16 * samples / (total_ms / 1e3)}
-        print(json.dumps(line))
-        dic.dic_destroy(h)
-        return
-    form = 1 if args.form == "tc" else 0
     dic.dic_set_form(h, form)
     dic.dic_set_pairs(h, tens)
     total, offs = dic.dic_batch_pois(h, len(tens))
     out = dic.batch_outputs(total, dev)
+    torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
         chosen = dic.dic_autotune(h, dic.DIC_ICGN, out)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             dic.dic_run_batch(h, dic.DIC_ICGN, out)
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(0)
-    sampler.start()
-    starts = [ev() for _ in range(args.steps)]
-    ends = [ev() for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index or 0) if clocks else None
+    if sampler:
+        sampler.start()
+    starts = [ev() for _ in range(steps)]
+    ends = [ev() for _ in range(steps)]
     with torch.cuda.stream(stream):
-        for i in range(args.steps):
+        for i in range(steps):
             starts[i].record(stream)
             dic.dic_run_batch(h, dic.DIC_ICGN, out)
             ends[i].record(stream)
     torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
+    clk = sampler.stop() if sampler else None
     ms = statistics.mean(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     conv = int((out["status"] == 0).sum())
-    # the same pairs through the single-pair calls, one after the other
+    # work of the step: search flops 2 N (2R+1)^2 per POI, sub-pixel samples
+    # from the batch's own outputs, precompute bytes per pixel
+    search_flop = sub_flop = 0.0
+    pre_bytes = 0
+    for k, p in enumerate(pairs):
+        a, b = offs[k], offs[k + 1]
+        search_flop += 2.0 * p.subset ** 2 * (2 * p.radius + 1) ** 2 * (b - a)
+        si, sp = subpixel_work(out["iters"][a:b], out["status"][a:b], out["status0"][a:b],
+                               p.subset)
+        sub_flop += FLOP_PER_SAMPLE * si + FLOP_PER_PIXEL_SAMPLE * sp
+        pre_bytes += PRECOMPUTE_BYTES_PER_PX * p.ref.size
+    t_roof = search_flop / (bf16_peak * 1e12) + sub_flop / (fp32_peak * 1e12) + pre_bytes / hbm
+    # the same pairs through the single-pair calls, one after the other, with
+    # events around each pair's search and sub-pixel launch
     singles = []
     for (f8, g8, s_, st_, r_) in tens:
         hh = dic.dic_create(s_, st_, r_, 1, TOL, MAX_ITER)
-        dic.dic_set_solve_precision(hh, args.solve_bits)
+        dic.dic_set_solve_precision(hh, solve_bits)
         dic.dic_set_form(hh, form)
         dic.dic_set_stream(hh, stream)
         singles.append(hh)
@@ -614,36 +687,46 @@ def run_batch_workload(args):
             dic.dic_set_pair(hh, f8, g8)
             n_each.append(dic.dic_num_pois(hh)[0])
     bufs = [dic.batch_outputs(n, dev) for n in n_each]
+    pev = [(ev(), ev(), ev()) for _ in tens]
 
-    def one_by_one():
-        for hh, (f8, g8, *_r), o in zip(singles, tens, bufs):
+    def one_by_one(record=False):
+        for j, (hh, (f8, g8, *_r), o) in enumerate(zip(singles, tens, bufs)):
             dic.dic_set_pair(hh, f8, g8)
+            if record:
+                pev[j][0].record(stream)
             dic.dic_integer_search(hh, o["u0"], o["v0"], o["zncc0"], o["status0"])
+            if record:
+                pev[j][1].record(stream)
             dic.dic_subpixel(hh, dic.DIC_ICGN, o["u0"], o["v0"], o["status0"], o["u"], o["v"],
                              o["ux"], o["uy"], o["vx"], o["vy"], o["zncc"], o["iters"],
                              o["status"])
+            if record:
+                pev[j][2].record(stream)
     with torch.cuda.stream(stream):
         one_by_one()
         torch.cuda.synchronize(dev)
-        a, e = ev(), ev()
-        a.record(stream)
-        for _ in range(max(1, args.steps // 2)):
-            one_by_one()
-        e.record(stream)
+        a_, e_ = ev(), ev()
+        a_.record(stream)
+        one_by_one(record=True)
+        e_.record(stream)
     torch.cuda.synchronize(dev)
-    ms_single = a.elapsed_time(e) / max(1, args.steps // 2)
+    ms_single = a_.elapsed_time(e_)
+    search_ms = sum(x.elapsed_time(y) for x, y, _ in pev)
+    sub_ms = sum(y.elapsed_time(z) for _, y, z in pev)
     for hh in singles:
         dic.dic_destroy(hh)
+    del bufs
     # the plain form of the same batch: FP32 integer search (persistent
     # kernels per template width); pairs whose FP32 window does not fit
     # shared memory are left out of this comparison and named
     plain = None
-    if form == 1:
+    skipped = []
+    if form == 1 and plain_steps > 0:
         keep = list(range(len(tens)))
         hp = None
         while keep:
             hp = dic.dic_create(21, 5, 10, 1, TOL, MAX_ITER)
-            dic.dic_set_solve_precision(hp, args.solve_bits)
+            dic.dic_set_solve_precision(hp, 32)
             dic.dic_set_stream(hp, stream)
             dic.dic_set_pairs(hp, [tens[k] for k in keep])
             tp, _ = dic.dic_batch_pois(hp, len(keep))
@@ -660,41 +743,178 @@ def run_batch_workload(args):
                 skipped.append(keep.pop(bad))
         if hp is not None:
             torch.cuda.synchronize(dev)
-            n_plain = max(1, args.steps // 20)
             with torch.cuda.stream(stream):
-                a, e = ev(), ev()
-                a.record(stream)
-                for _ in range(n_plain):
+                a_, e_ = ev(), ev()
+                a_.record(stream)
+                for _ in range(plain_steps):
                     dic.dic_run_batch(hp, dic.DIC_ICGN, op)
-                e.record(stream)
+                e_.record(stream)
             torch.cuda.synchronize(dev)
-            ms_plain = a.elapsed_time(e) / n_plain
+            ms_plain = a_.elapsed_time(e_) / plain_steps
             conv_plain = int((op["status"] == 0).sum())
-            plain = {"search": "fp32-exact", "pairs": len(keep), "pairs_left_out": skipped,
-                     "ms_per_step": ms_plain, "value": conv_plain / (ms_plain / 1e3)}
+            plain = {"search": "fp32-exact", "solve": "fp32", "pairs": len(keep),
+                     "pairs_left_out": skipped, "ms_per_step": ms_plain,
+                     "value": conv_plain / (ms_plain / 1e3)}
             dic.dic_destroy(hp)
-    line = {"metric": METRIC, "value": conv / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16+f32" if form == 1 else "f32",
-            "data": "synthetic (seeded speckle renders)",
-            "config": {"workload": args.workload, "pairs": len(tens), "pois": int(total),
-                       "form": ("one CUDA graph: " +
-                                ("tensor-core search pair by pair, " if form == 1 else
-                                 "persistent FP32 search per template width, ") +
-                                ("per-pair sub-pixel launches on a second stream, each "
-                                 "overlapping the next pairs' searches"
-                                 if tuple(chosen) == (0, 0) else
-                                 "one persistent sub-pixel kernel")),
-                       "autotuned": {"warps_per_cta": chosen[0], "grid_mult": chosen[1]},
-                       "l2": "inputs and scratch larger than L2"},
-            "pairs_per_s": len(tens) / (ms / 1e3),
-            "per_pair_launches": {"ms_per_step": ms_single,
-                                  "value": conv / (ms_single / 1e3)},
-            "plain_fp32_batch": plain,
-            "converged_fraction": conv / max(1, int(total)), "clocks": clocks}
-    print(json.dumps(line))
     dic.dic_destroy(h)
+    threads = os.cpu_count() or 1
+    ids = sorted(set(round(i * (len(pairs) - 1) / max(1, cpu_pairs - 1))
+                     for i in range(cpu_pairs)))
+    cs = oracle_sample(pairs, ids, cpu_pois, threads)
+    shape = tuple(chosen)
+    return {
+        "workload": workload, "pairs": len(tens), "pois": int(total),
+        "ms_per_step": ms, "value": conv / (ms / 1e3), "unit": UNIT,
+        "pairs_per_s": len(tens) / (ms / 1e3), "converged_fraction": conv / max(1, int(total)),
+        "form": ("one CUDA graph: " + ("tensor-core search pair by pair, " if form == 1 else
+                                       "persistent FP32 search per template width, ") +
+                 ("per-pair sub-pixel launches on a second stream, each overlapping the next "
+                  "pairs' searches" if shape == (0, 0) else "one persistent sub-pixel kernel")),
+        "autotuned": {"warps_per_cta": chosen[0], "grid_mult": chosen[1]},
+        "solve": f"fp{solve_bits}", "steps": steps, "warmup": warmup,
+        "roofline_path": {"roofline_ms": t_roof * 1e3, "measured_ms": ms,
+                          "frac": t_roof * 1e3 / ms,
+                          "terms_ms": {"search": search_flop / (bf16_peak * 1e12) * 1e3,
+                                       "subpixel": sub_flop / (fp32_peak * 1e12) * 1e3,
+                                       "precompute": pre_bytes / hbm * 1e3}},
+        "roofline_search": {"bound": "tensor", "achieved": search_flop / (search_ms / 1e3) / 1e12,
+                            "peak": bf16_peak, "unit": "TFLOP/s",
+                            "frac": search_flop / (search_ms / 1e3) / 1e12 / bf16_peak,
+                            "ms": search_ms,
+                            "basis": "per-pair search launches, events; measured BF16 peak"},
+        "roofline_subpixel": {"bound": "alu", "achieved": sub_flop / (sub_ms / 1e3) / 1e12,
+                              "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": sub_flop / (sub_ms / 1e3) / 1e12 / fp32_peak,
+                              "ms": sub_ms,
+                              "basis": "per-pair sub-pixel launches, events; nominal FP32"},
+        "per_pair_launches": {"ms_per_step": ms_single, "value": conv / (ms_single / 1e3),
+                              "batch_gain": ms_single / ms},
+        "plain_fp32_batch": plain,
+        "cpu_baseline": {"value": cs["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": (f"{cs['pois']} POIs: {cpu_pois} evenly spaced POIs of each "
+                                    f"of pairs {ids} (search + IC-GN), {cs['seconds']:.1f} s; "
+                                    "a rate on the sample, not extrapolated")},
+        "l2": "inputs and scratch larger than L2",
+        "clocks": clk}
+
+
+# FP32 operations per subset sample of the ZNSSD forward (dic_znssd) and
+# backward (dic_backward) launches, counted from the kernel: each launch
+# samples g twice (value pass: warp 12, Keys weights 34, 4x4 convolution 35,
+# sums 6 = 87; value-and-gradient pass: warp 12, value and derivative weights
+# 62, convolutions 77, loss 7 = 158); the backward launch adds the adjoint
+# (weight 5, dL/dp 12, Keys weights 34, 16 scatter products 20 = 71).
+ADJ_FLOP_FWD = 87 + 158
+ADJ_FLOP_BWD = 87 + 158 + 71
+ADJ_SCATTER_PER_SAMPLE = 16
+
+
+def adjoint_record(dev, steps: int, warmup: int, n_pairs: int = 8,
+                   fp32_peak: float | None = None, atomic_peak: float | None = None,
+                   cpu_pois: int = 256) -> dict:
+    """ZNSSD forward + backward at the imposed shapes over the affine1024x8
+    differentiation set (8 pairs, subset 31, step 8: 14161 POIs each)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1905_06228_gb300 as dic
+    from workloads import configs
+    pairs = [configs.affine1024x8(k) for k in range(n_pairs)]
+    stream = torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    total_ms, n_poi, samples = 0.0, 0, 0
+    shapes = []
+    for p in pairs:
+        s_, st_, r_ = p.subset, p.step, p.radius
+        nx = (1024 - 1 - 2 * (s_ // 2 + r_ + 2)) // st_ + 1
+        n = nx * nx
+        b = s_ // 2 + r_ + 2
+        kk = np.arange(n)
+        x0 = (b + (kk % nx) * st_).astype(np.float64)
+        y0 = (b + (kk // nx) * st_).astype(np.float64)
+        shp = np.stack(p.deformation.displacement(x0, y0), 1).astype(np.float32)
+        shapes.append(shp)
+        f = torch.from_numpy(p.ref).to(dev).float().contiguous()
+        g = torch.from_numpy(p.defm).to(dev).float().contiguous()
+        sh = torch.from_numpy(shp).to(dev).contiguous()
+        hh = dic.dic_create(s_, st_, r_)
+        dic.dic_set_stream(hh, stream)
+        dg = torch.empty_like(g)
+        dp = torch.empty_like(sh)
+        tot = torch.empty((), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            dic.dic_set_pair_f32(hh, f, g)
+            for _ in range(warmup):
+                dic.dic_znssd(hh, sh, None, tot)
+                dic.dic_backward(hh, sh, None, 1.0, dg, dp)
+            a, e = ev(), ev()
+            a.record(stream)
+            for _ in range(steps):
+                dic.dic_znssd(hh, sh, None, tot)
+                dic.dic_backward(hh, sh, None, 1.0, dg, dp)
+            e.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += a.elapsed_time(e) / steps
+        n_poi += n
+        samples += n * s_ * s_
+        dic.dic_destroy(hh)
+    rate = samples / (total_ms / 1e3)
+    flops = (ADJ_FLOP_FWD + ADJ_FLOP_BWD) * rate / 1e12
+    adds = ADJ_SCATTER_PER_SAMPLE * rate
+    # the oracle's FP64 ZNSSD + adjoint (single-threaded, as it stands) on a
+    # POI sample of the first pair
+    p = pairs[0]
+    idx = cpu_sample_idx(len(shapes[0]), cpu_pois)
+    t0 = time.perf_counter()
+    oracle.znssd(p.ref, p.defm, p.subset, p.step, p.radius, shapes[0][idx].astype(np.float64),
+                 poi_idx=idx)
+    dt = time.perf_counter() - t0
+    rec = {"workload": "affine1024x8", "pairs": n_pairs, "pois": n_poi, "subset": 31,
+           "grid_step": 8, "metric": "adjoint POI/s (ZNSSD forward + backward)",
+           "value": n_poi / (total_ms / 1e3), "unit": "POI/s", "ms_per_step": total_ms,
+           "steps": steps, "warmup": warmup, "samples_per_s": rate,
+           "scatter_atomics_per_s": adds,
+           "roofline": {"bound": "alu", "achieved": flops, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": flops / fp32_peak if fp32_peak else None,
+                        "work": (f"{ADJ_FLOP_FWD} + {ADJ_FLOP_BWD} flop per subset sample "
+                                 "(forward + backward launch)")},
+           "roofline_atomic": {"bound": "smem atomics", "achieved": adds / 1e9,
+                               "peak": atomic_peak / 1e9 if atomic_peak else None,
+                               "unit": "G adds/s",
+                               "frac": adds / atomic_peak if atomic_peak else None,
+                               "peak_basis": "measured (dic_measure_peak, shared-memory float "
+                                             "atomic adds)"},
+           "cpu_baseline": {"value": len(idx) / dt, "unit": "POI/s", "cores": 1,
+                            "kind": "oracle",
+                            "sample": f"{len(idx)} evenly spaced POIs of pair 0, ZNSSD + FP64 "
+                                      f"adjoint, single thread, {dt:.1f} s"}}
+    return rec
+
+
+def run_batch_workload(args):
+    """One record of the batched forms (sine2048x64, mixed32) or of the
+    adjoint (affine1024x8), printed as its own JSON line."""
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    dic.build()
+    fp32_peak = dic.dic_measure_peak(dic.DIC_PEAK_FP32_FMA) / 1e12
+    if args.workload == "affine1024x8":
+        rec = adjoint_record(dev, args.steps, args.warmup, n_pairs=args.pairs or 8,
+                             fp32_peak=fp32_peak,
+                             atomic_peak=dic.dic_measure_peak(dic.DIC_PEAK_SMEM_ATOMIC_F32))
+    else:
+        rec = batch_record(args.workload, dev, args.steps, args.warmup,
+                           form=1 if args.form == "tc" else 0, solve_bits=args.solve_bits,
+                           n_pairs=args.pairs)
+    rec.update({"metric": rec.get("metric", METRIC), "n_gpus": 1, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "data": "synthetic (seeded speckle renders)",
+                "fp32_fma_measured_tflops": fp32_peak})
+    print(json.dumps(rec))
 
 
 def main():

@@ -280,6 +280,22 @@ dic_status dic_znssd(dic_t h, const float *p6, float *loss_per_poi, float *loss_
 dic_status dic_backward(dic_t h, const float *p6, const float *grad_loss, float scale,
                         float *dL_ddef, float *dL_dp);
 
+/* ------------------------------------------------------------ measurement
+ * Throughput peaks of the units that bound the kernels which have neither a
+ * tensor-core nor an HBM roofline, measured on the current device by a
+ * microbenchmark (no counterpart in the paper; the benchmark divides the
+ * kernels' algorithmic rates by them):
+ *   DIC_PEAK_FP32_FMA         FP32 multiply-add throughput, flop/s (2 per FMA),
+ *                             the unit of the sub-pixel refinement
+ *   DIC_PEAK_SMEM_ATOMIC_F32  shared-memory float atomic adds per second, the
+ *                             unit of dic_backward's scatter into its tiles
+ * Runs four launches of a few milliseconds on cuda_stream (NULL = default),
+ * synchronises, and writes the best of the last three to *rate.  Allocates
+ * and frees a small device buffer.  DIC_ERR_ARG for an unknown kind or a
+ * null rate; DIC_ERR_CUDA if a launch fails. */
+enum { DIC_PEAK_FP32_FMA = 0, DIC_PEAK_SMEM_ATOMIC_F32 = 1 };
+dic_status dic_measure_peak(int kind, void *cuda_stream, double *rate);
+
 /* Sub-pixel refinement that allocates no device memory.  The paper has no
  * counterpart; this call exists for callers that must not call cudaMalloc /
  * cudaFree -- e.g. real-time acquisition loops that cannot absorb the device

@@ -25,6 +25,7 @@ DIC_OK, DIC_ERR_ARG, DIC_ERR_CUDA, DIC_ERR_OOM, DIC_ERR_STATE, DIC_ERR_TIMEOUT, 
 DIC_ICGN, DIC_FANR = 0, 1
 DIC_FORM_PLAIN_FP32, DIC_FORM_BF16TC = 0, 1
 DIC_INTERP_BICUBIC, DIC_INTERP_BILINEAR = 0, 1
+DIC_PEAK_FP32_FMA, DIC_PEAK_SMEM_ATOMIC_F32 = 0, 1
 POI_OK, POI_ZERO_VAR_REF, POI_OUT_OF_BOUNDS, POI_MAX_ITER, POI_NONFINITE, POI_SINGULAR, \
     POI_ZERO_VAR_DEF = range(7)
 
@@ -72,6 +73,7 @@ SIGNATURES = {
     "dic_backward": (i32, [P, P, P, f32, P, P]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "dic_measure_peak": (i32, [i32, P, C.POINTER(C.c_double)]),
     "dic_subpixel_noalloc": (i32, [P, P, i32, i32, i32, i32, i32, i32, i32, f32, i32, i32,
                                    P, P, P, P, P, P, P, P, P, P, P, P, P]),
 }
@@ -281,6 +283,15 @@ def dic_subpixel_noalloc(ref, defm, subset_size, grid_step, search_radius, metho
                                       _ptr(u0), _ptr(v0), _ptr(status0), _ptr(u), _ptr(v),
                                       _ptr(ux), _ptr(uy), _ptr(vx), _ptr(vy), _ptr(zncc),
                                       _ptr(iters), _ptr(status), C.c_void_p(sp)))
+
+
+def dic_measure_peak(kind: int, stream=None) -> float:
+    """Measured FP32 FMA flop/s (DIC_PEAK_FP32_FMA) or shared-memory float
+    atomic adds/s (DIC_PEAK_SMEM_ATOMIC_F32) of the current device."""
+    sp = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    r = C.c_double()
+    _check(lib().dic_measure_peak(kind, C.c_void_p(sp), C.byref(r)))
+    return r.value
 
 
 # ------------------------------------------------------------ convenience

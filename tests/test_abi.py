@@ -142,3 +142,14 @@ def test_check_before_any_launch():
         assert lib.dic_check(h) == dic.DIC_OK
     finally:
         dic.dic_destroy(h)
+
+
+def test_measure_peak_argument_checks():
+    """Unknown kinds and a null output are refused on the host, before any
+    device work."""
+    lib = dic.lib()
+    import ctypes
+    r = ctypes.c_double()
+    assert lib.dic_measure_peak(7, None, ctypes.byref(r)) == dic.DIC_ERR_ARG
+    assert lib.dic_measure_peak(-1, None, ctypes.byref(r)) == dic.DIC_ERR_ARG
+    assert lib.dic_measure_peak(dic.DIC_PEAK_FP32_FMA, None, None) == dic.DIC_ERR_ARG
