@@ -156,6 +156,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout_s: float = 3.0):
+        """Block until the first sample has arrived (nvidia-smi starts slowly)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout_s:
+            time.sleep(0.01)
+
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -265,9 +271,12 @@ def run_gpu(args):
         conv = int((p_out["status"] == 0).sum().item())
         return step_ms, (search_ms, sub_ms), conv, wall, clocks
 
+    # clocks: sampled from just before the headline's timed loop to the end of
+    # the last timed loop of this line (forms and e2e), every 10 ms
     sampler = ClockSampler(local)
-    step_ms, (search_ms, sub_ms), conv, wall, clocks = timed_loop(d, args.steps, args.warmup,
-                                                                   sampler)
+    sampler.start()
+    sampler.wait_first()
+    step_ms, (search_ms, sub_ms), conv, wall, _ = timed_loop(d, args.steps, args.warmup)
     total_ms, conv_all = reduce_over_ranks(sum(step_ms), conv, dev)
     ms_per_step = total_ms / args.steps
     value = conv_all * args.steps / (total_ms / 1e3)
@@ -327,6 +336,8 @@ def run_gpu(args):
                 h_s[k].copy_(s_out[k], non_blocking=True)
             e_ends[i].record(stream)
     torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    clocks["window"] = "headline, forms and e2e timed loops"
     e_ms, e_conv = reduce_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)) / ek,
                                      int((h_out["status"] == 0).sum().item()), dev)
     e2e = {"value": e_conv / (e_ms / 1e3), "unit": UNIT,
@@ -649,6 +660,7 @@ def batch_record(workload: str, dev, steps: int, warmup: int, form: int = 1,
     sampler = ClockSampler(dev.index or 0) if clocks else None
     if sampler:
         sampler.start()
+        sampler.wait_first()
     starts = [ev() for _ in range(steps)]
     ends = [ev() for _ in range(steps)]
     with torch.cuda.stream(stream):
@@ -811,7 +823,7 @@ ADJ_SCATTER_PER_SAMPLE = 16
 
 def adjoint_record(dev, steps: int, warmup: int, n_pairs: int = 8,
                    fp32_peak: float | None = None, atomic_peak: float | None = None,
-                   cpu_pois: int = 256) -> dict:
+                   cpu_pois: int = 4096) -> dict:
     """ZNSSD forward + backward at the imposed shapes over the affine1024x8
     differentiation set (8 pairs, subset 31, step 8: 14161 POIs each)."""
     import numpy as np

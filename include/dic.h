@@ -179,6 +179,45 @@ dic_status dic_num_pois(dic_t h, int *n_pois, int *nx, int *ny);
 dic_status dic_integer_search(dic_t h, int32_t *u0, int32_t *v0, float *zncc0,
                               uint8_t *status);
 
+/* Integer search by particle swarm optimisation (Section 2.1, Eqs. 2-4), or
+ * by the modified swarm whose particles also evaluate the four pixels
+ * around their own every generation and move to the best of the five (the
+ * star search the paper folds into the swarm, Sections 3 and 5), over the
+ * same window [-R, R]^2 as dic_integer_search.  Per POI and generation t:
+ *   t = 0   position R (2u0 - 1, 2u1 - 1), velocity vinit (2u2 - 1, 2u3 - 1)
+ *   t >= 1  v <- ((w v) + (c1 r1)(pbest - p)) + (c2 r2)(gbest - p)  (Eq. 2),
+ *           w = 0.9 - (t - 1) / (2 generations)                     (Eq. 4),
+ *           r1 = (u0, u1), r2 = (u2, u3) per direction; p <- p + v  (Eq. 3),
+ *           clamped to [-R, R] per direction
+ *   Eq. 1 at the nearest pixel floor(p + 1/2) (and the modified swarm's star
+ *   pixels inside the window; ties: centre, +x, -x, +y, -y); pbest takes a
+ *   strictly better pixel; gbest the first strictly better pbest in particle
+ *   order.  Stop after the first generation whose gbest has
+ *   C >= stop_num / stop_den (tested exactly), else after `generations`.
+ * The particle arithmetic is FP64, each product and sum rounded on its own in
+ * that order; Eq. 1 comes from exact integer sums and candidates compare
+ * exactly as in dic_integer_search.  The swarm's random numbers are inputs:
+ *   uniforms      device, [n_pois][generations][particles][4] doubles in
+ *                 [0, 1): generation 0 holds the start draws, generation
+ *                 t >= 1 the r1 (x, y) and r2 (x, y) of the update into t
+ *   particles     1..64 (Section 5 uses 50); generations 1..1000 (5)
+ *   c1, c2, vinit finite (the paper fixes none of them; 2, 2 and R/4 are
+ *                 the values used elsewhere in this library's documentation)
+ *   stop_num/den  0..2^20 / 1..2^20 (995/1000 stops at C >= 0.995)
+ * Outputs (device, n_pois each): u0, v0 = gbest; zncc0 = its Eq. 1 (FP32 from
+ * the exact sums); status OK / ZERO_VAR_REF / ZERO_VAR_DEF (every pixel the
+ * swarm saw has a flat target subset); gens = generations run (0 for a flat
+ * reference); evals = distinct pixels evaluated (each pixel once per POI).
+ * Requires dic_set_pair with an 8-bit pair (else DIC_ERR_STATE /
+ * DIC_ERR_UNSUPPORTED); DIC_ERR_ARG for the ranges above or a null pointer;
+ * DIC_ERR_UNSUPPORTED if the window and the pixel table of one POI exceed
+ * shared memory.  Reuses the handle's box-sum scratch (8 bytes per subset
+ * position of f and of g, allocated on first use). */
+dic_status dic_pso_search(dic_t h, int modified, int particles, int generations, double c1,
+                          double c2, double vinit, int stop_num, int stop_den,
+                          const double *uniforms, int32_t *u0, int32_t *v0, float *zncc0,
+                          uint8_t *status, int32_t *gens, int32_t *evals);
+
 /* Sub-pixel refinement (Section 2.2) of every POI from the integer start
  * (u0, v0, status0), e.g. the outputs of dic_integer_search.  POIs whose
  * status0 is not DIC_POI_OK are passed through with zero gradients.

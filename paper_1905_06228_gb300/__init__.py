@@ -72,6 +72,8 @@ SIGNATURES = {
     "dic_set_batch_shape": (i32, [P, i32, i32]),
     "dic_backward": (i32, [P, P, P, f32, P, P]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
+    "dic_pso_search": (i32, [P, i32, i32, i32, C.c_double, C.c_double, C.c_double, i32, i32,
+                             P, P, P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
     "dic_measure_peak": (i32, [i32, P, C.POINTER(C.c_double)]),
     "dic_subpixel_noalloc": (i32, [P, P, i32, i32, i32, i32, i32, i32, i32, f32, i32, i32,
@@ -134,6 +136,7 @@ def dic_create(subset_size: int, grid_step: int, search_radius: int, shape_order
     h = P()
     _check(lib().dic_create(C.byref(h), subset_size, grid_step, search_radius, shape_order,
                             conv_tol, max_iter))
+    _RADIUS[h.value] = search_radius
     return h
 
 
@@ -255,6 +258,36 @@ def dic_num_pois(h) -> tuple[int, int, int]:
 
 def dic_integer_search(h, u0, v0, zncc0, status) -> None:
     _check(lib().dic_integer_search(h, _ptr(u0), _ptr(v0), _ptr(zncc0), _ptr(status)), h)
+
+
+def dic_pso_search(h, uniforms, u0, v0, zncc0, status, gens, evals, modified: bool = False,
+                   c1: float = 2.0, c2: float = 2.0, vinit: float | None = None,
+                   stop: tuple[int, int] = (995, 1000)) -> None:
+    """Particle swarm integer search (Eqs. 2-4), or the modified swarm with
+    the star search; ``uniforms`` is a float64 device tensor
+    (n_pois, generations, particles, 4).  vinit defaults to radius / 4."""
+    import torch
+    if uniforms.dtype != torch.float64 or uniforms.dim() != 4 or uniforms.shape[3] != 4:
+        raise RuntimeError("uniforms: float64 tensor (n_pois, generations, particles, 4)")
+    n, _, _ = dic_num_pois(h)
+    if uniforms.shape[0] != n:
+        raise RuntimeError("uniforms: one row per POI")
+    if vinit is None:
+        vinit = _handle_radius(h) / 4.0
+    _check(lib().dic_pso_search(h, int(bool(modified)), uniforms.shape[2], uniforms.shape[1],
+                                float(c1), float(c2), float(vinit), int(stop[0]), int(stop[1]),
+                                _ptr(uniforms), _ptr(u0), _ptr(v0), _ptr(zncc0), _ptr(status),
+                                _ptr(gens), _ptr(evals)), h)
+
+
+_RADIUS = {}
+
+
+def _handle_radius(h) -> int:
+    v = _RADIUS.get(h.value if hasattr(h, "value") else int(h))
+    if v is None:
+        raise RuntimeError("vinit needed: handle not created by dic_create of this binding")
+    return v
 
 
 def dic_subpixel(h, method, u0, v0, status0, u, v, ux, uy, vx, vy, zncc, iters, status) -> None:

@@ -1,5 +1,6 @@
 // dic_api.cu -- the C ABI declared in include/dic.h: argument checking, the
 // handle's device scratch, TMA descriptors and kernel launches.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -380,6 +381,101 @@ dic_status dic_num_pois(dic_t h, int* n_pois, int* nx, int* ny) {
   if (n_pois) *n_pois = (int)h->g.n_pois;
   if (nx) *nx = h->g.nx;
   if (ny) *ny = h->g.ny;
+  return DIC_OK;
+}
+
+dic_status dic_pso_search(dic_t h, int modified, int particles, int generations, double c1,
+                          double c2, double vinit, int stop_num, int stop_den,
+                          const double* uniforms, int32_t* u0, int32_t* v0, float* zncc0,
+                          uint8_t* status, int32_t* gens, int32_t* evals) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->ref_f32)
+    return fail(h, DIC_ERR_UNSUPPORTED, "swarm search needs an 8-bit pair (exact sums)");
+  if ((modified != 0 && modified != 1) || particles < 1 || particles > 64 || generations < 1 ||
+      generations > 1000 || stop_num < 0 || stop_num > (1 << 20) || stop_den < 1 ||
+      stop_den > (1 << 20) || !std::isfinite(c1) || !std::isfinite(c2) ||
+      !std::isfinite(vinit))
+    return fail(h, DIC_ERR_ARG,
+                "swarm arguments: modified 0/1, particles 1..64, generations 1..1000, "
+                "0 <= stop_num <= 2^20, 1 <= stop_den <= 2^20, finite coefficients");
+  if (h->g.n_pois == 0) return DIC_OK;
+  if (!uniforms || !u0 || !v0 || !zncc0 || !status || !gens || !evals)
+    return fail(h, DIC_ERR_ARG, "null pointer");
+  int wp = 0;
+  const size_t wsm = dic::pso_warp_smem(h->subset, h->R, particles, &wp);
+  if (wsm == 0)
+    return fail(h, DIC_ERR_UNSUPPORTED, "swarm search: window and table exceed shared memory");
+  // box-sum maps of f and g over every subset top-left a window reaches
+  const int B = h->M + h->R + 2;
+  dic::SearchTcParams t{};
+  t.ref = h->ref;
+  t.def = h->def;
+  t.W = h->g.W;
+  t.H = h->g.H;
+  t.pitch = h->g.pitch;
+  t.S = h->subset;
+  t.xmin = B - h->M - h->R;
+  t.ymin = B - h->M - h->R;
+  const int spanx = (h->g.nx - 1) * h->step + 2 * h->R + 1;
+  const int spany = (h->g.ny - 1) * h->step + 2 * h->R + 1;
+  t.ntx = (spanx + 7) / 8;
+  t.nty = (spany + 15) / 16;
+  const size_t pbe = dic::search_tc_posbox_elems(t);
+  if (pbe > h->tc_posbox_elems) {
+    if (h->tc_posbox) cudaFree(h->tc_posbox);
+    if (h->tc_fbox) cudaFree(h->tc_fbox);
+    h->tc_posbox = nullptr;
+    h->tc_fbox = nullptr;
+    h->tc_posbox_elems = 0;
+    if (cudaMalloc(&h->tc_posbox, pbe * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&h->tc_fbox, pbe * sizeof(int2)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, DIC_ERR_OOM, "cannot allocate swarm search scratch");
+    }
+    h->tc_posbox_elems = pbe;
+  }
+  t.posbox = h->tc_posbox;
+  t.fbox = h->tc_fbox;
+  cudaError_t e = dic::launch_boxmaps(t, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "box-sum map launch");
+  dic::PsoParams p{};
+  p.ref = h->ref;
+  p.def = h->def;
+  p.W = h->g.W;
+  p.H = h->g.H;
+  p.pitch = h->g.pitch;
+  p.S = h->subset;
+  p.M = h->M;
+  p.R = h->R;
+  p.step = h->step;
+  p.nx = h->g.nx;
+  p.n_pois = h->g.n_pois;
+  p.modified = modified;
+  p.particles = particles;
+  p.gmax = generations;
+  p.c1 = c1;
+  p.c2 = c2;
+  p.vinit = vinit;
+  p.stop_num = stop_num;
+  p.stop_den = stop_den;
+  p.rand = uniforms;
+  p.posbox = t.posbox;
+  p.fbox = t.fbox;
+  p.xmin = t.xmin;
+  p.ymin = t.ymin;
+  p.pw = t.ntx * 8;
+  p.wp = wp;
+  p.warp_smem = wsm;
+  p.warps = (int)std::min<size_t>(4, (227 * 1024) / wsm);
+  p.u0 = u0;
+  p.v0 = v0;
+  p.zncc0 = zncc0;
+  p.status = status;
+  p.gens = gens;
+  p.evals = evals;
+  e = dic::launch_pso(p, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "swarm search launch");
   return DIC_OK;
 }
 

@@ -84,6 +84,31 @@ struct SearchTcParams {
   unsigned int* err_flag;
 };
 
+// Parameters of the particle swarm integer search (k_pso.cu).
+struct PsoParams {
+  const uint8_t* ref;
+  const uint8_t* def;
+  int W, H, pitch;
+  int S, M, R, step, nx;
+  int64_t n_pois;
+  int modified, particles, gmax;
+  double c1, c2, vinit;
+  long long stop_num, stop_den;
+  const double* rand;  // [n_pois][gmax][particles][4]
+  const int2* posbox;  // box sums (sum b - 128, sum (b - 128)^2) of g per subset top-left
+  const int2* fbox;    // the same for f
+  int xmin, ymin, pw;  // top-left (x, y) of map entry 0, map row length
+  int wp;              // byte pitch of a warp's window rows in shared memory
+  int warps;           // warps (POIs) per CTA
+  size_t warp_smem;    // shared bytes per warp
+  int32_t* u0;
+  int32_t* v0;
+  float* zncc0;
+  uint8_t* status;
+  int32_t* gens;
+  int32_t* evals;
+};
+
 // Parameters of the sub-pixel kernels.  The reference image is 8-bit
 // (ref) or float (ref_f32 != nullptr); pitch is in elements.
 struct SubpixelParams {
@@ -143,6 +168,13 @@ size_t search_tc_phase_elems(const SearchTcParams& g);  // phase images + templa
 size_t search_tc_gph_elems(const SearchTcParams& g);
 cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
                              const CUtensorMap* tmB, cudaStream_t st);
+// Box-sum maps of f (fbox) and g (posbox) over p.xmin, p.ymin, p.ntx * 8 by
+// p.nty * 16 subset top-left positions (reads p.ref, p.def, W, H, pitch, S).
+cudaError_t launch_boxmaps(const SearchTcParams& p, cudaStream_t st);
+// Shared bytes per warp of the swarm search (window, evaluation table, the
+// generation's box sums); 0 if the geometry is not supported.
+size_t pso_warp_smem(int S, int R, int particles, int* wp);
+cudaError_t launch_pso(const PsoParams& p, cudaStream_t st);
 
 // Persistent multi-pair launchers.  jobs / offsets are device arrays; the
 // POIs of job k are items [offsets[k], offsets[k+1]); counter starts at 0.

@@ -940,6 +940,17 @@ size_t search_tc_posbox_elems(const SearchTcParams& g) {
   return (size_t)g.ntx * 8 * (size_t)g.nty * 16;
 }
 
+cudaError_t launch_boxmaps(const SearchTcParams& p, cudaStream_t st) {
+  const size_t bsm = boxmap_smem(p.S);
+  if (bsm > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(boxmap_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.ntx * 8 + kBoxX - 1) / kBoxX, (p.nty * 16 + kBoxY - 1) / kBoxY, 2);
+  boxmap_kernel<<<grid, 256, bsm, st>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
                              const CUtensorMap* tmB, cudaStream_t st) {
   if (p.n_pois == 0) return cudaSuccess;

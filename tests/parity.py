@@ -102,7 +102,7 @@ def oracle_iterates(f, g, subset, step, radius, start: dict, method: int, ref: d
 def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method: int,
                      tol: float = 1e-3, max_iter: int = 50, idx=None,
                      min_iter_agreement: float = 0.99, min_compared: float = 0.99,
-                     interp: int = 0, label: str = "") -> dict:
+                     interp: int = 0, label: str = "", grad_outliers: float = 0.0) -> dict:
     """Every POI's sub-pixel result against the FP64 oracle (reading P1).
 
     * Statuses agree exactly, POI by POI (a swap between OK and MAX_ITER, the
@@ -121,6 +121,12 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
       reported ZNCC must equal the oracle's Eq. 1 at the GPU's own returned
       shape.  The share of POIs compared inside the tolerance must reach
       ``min_compared``.
+    * ``grad_outliers`` (reading R18b, FA-NR over the bilinear interpolation
+      of Eq. 5 only): that share of the converged POIs may have gradients
+      outside 1e-5 but inside 1e-4, u and v still inside 1e-3 px.  Eq. 5's
+      gradient jumps at cell edges, so a sample that FP32 places on the
+      other side of an edge than FP64 changes the Jacobian and moves the
+      fixed point by a fraction of one sample's jump.
     * ZNCC: a converged POI reports Eq. 1 at the shape its last solve
       sampled (reading R11), compared with the oracle's Eq. 1 at its iterate
       after k - 1 solves; every other POI that ran reports Eq. 1 at its
@@ -140,7 +146,9 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
     assert swap.sum() <= 0.001 * n, ("OK/MAX_ITER swaps", int(swap.sum()))
     np.testing.assert_array_equal(gst[~swap], rst[~swap], err_msg=label + " statuses")
     agree = float((git == rit).mean())
-    assert agree >= min_iter_agreement, (label, "iteration agreement", agree)
+    # small samples: one differing count is always allowed
+    assert (git != rit).sum() <= max(1, int((1 - min_iter_agreement) * n)), (
+        label, "iteration agreement", agree)
 
     want = oracle_iterates(f, g, subset, step, radius, start, method, ref, git, idx, interp)
     err = np.abs(gp - want)
@@ -149,6 +157,14 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
     ran = git >= 1
     conv = ran & (gst == 0)
     wander = ran & (gst != 0)
+    n_grad_outliers = 0
+    if grad_outliers > 0:
+        soft = (conv & over & (err[:, [0, 3]].max(1) < TOL_UV) &
+                (err[:, [1, 2, 4, 5]].max(1) < 10 * TOL_GRAD))
+        n_grad_outliers = int(soft.sum())
+        assert n_grad_outliers <= grad_outliers * conv.sum(), (label, "gradient outliers",
+                                                               n_grad_outliers)
+        over = over & ~soft
     bad = np.nonzero(conv & over)[0]
     assert len(bad) == 0, dict(label=label, poi=bad[:5], gpu=gp[bad[:5]], want=want[bad[:5]],
                                git=git[bad[:5]], rit=rit[bad[:5]])
@@ -182,6 +198,7 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
     st = dict(label=label, n=n, ran=int(ran.sum()), converged=int(conv.sum()),
               not_converged=int(wander.sum()), wandering_outside_tol=n_wander_over,
               compared_within_tol=compared, iter_agreement=agree, ok_maxiter_swaps=int(swap.sum()),
+              gradient_outliers=n_grad_outliers,
               max_err_uv=float(err[ran][:, [0, 3]].max(initial=0)),
               max_err_grad=float(err[ran][:, [1, 2, 4, 5]].max(initial=0)),
               max_err_zncc_converged=zerr_conv, max_err_zncc_other=zerr_other)
