@@ -313,6 +313,40 @@ def run_gpu(args):
     bil_sub_ms = statistics.mean(seb[1])
     dbl.close()
 
+    # the particle swarm integer searches (Section 2.1, Eqs. 2-4; the modified
+    # swarm with the star search) timed beside the dense search on the same
+    # pair, with their agreement with its exact argmax
+    from workloads import swarm
+    rand = torch.from_numpy(swarm.uniforms(1, n)).to(dev)
+    pso = {}
+    ds = make(args.solve_bits, args.form)
+    ds.set_pair(ref_d, def_d)
+    po = {k: torch.empty(n, dtype=dt, device=dev) for k, dt in
+          (("u0", torch.int32), ("v0", torch.int32), ("zncc", torch.float32),
+           ("status", torch.uint8), ("gens", torch.int32), ("evals", torch.int32))}
+    for modified in (False, True):
+        ev_a, ev_b = ev(), ev()
+        reps = max(3, args.steps // 4)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                dic.dic_pso_search(ds.h, rand, po["u0"], po["v0"], po["zncc"], po["status"],
+                                   po["gens"], po["evals"], modified=modified)
+            ev_a.record(stream)
+            for _ in range(reps):
+                dic.dic_pso_search(ds.h, rand, po["u0"], po["v0"], po["zncc"], po["status"],
+                                   po["gens"], po["evals"], modified=modified)
+            ev_b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev_a.elapsed_time(ev_b) / reps
+        agree = ((po["u0"] == s_out["u0"]) & (po["v0"] == s_out["v0"])).float().mean().item()
+        pso["modified_swarm" if modified else "standard_swarm"] = {
+            "ms": ms, "pois_per_s": n / (ms / 1e3), "agrees_with_dense_argmax": agree,
+            "mean_evaluations": po["evals"].float().mean().item(),
+            "mean_generations": po["gens"].float().mean().item(),
+            "dense_search_ms": statistics.mean(search_ms)}
+    ds.close()
+    del rand
+
     # e2e through the public call with host buffers: H2D of both images,
     # the three kernels, D2H of every per-POI output, all inside the events
     h_ref = torch.from_numpy(pair.ref).pin_memory()
@@ -471,7 +505,8 @@ def run_gpu(args):
                                               "solve": f"fp{args.solve_bits}",
                                               "value": bil_value, "subpixel_ms": bil_sub_ms},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
-                                         "value": plain_value}},
+                                         "value": plain_value},
+                          "swarm_searches": pso},
                 "converged_fraction": conv / n, "wall_s_timed": wall,
                 "sub_records": sub_records}
         print(json.dumps(line))

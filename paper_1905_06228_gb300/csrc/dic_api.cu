@@ -166,6 +166,21 @@ void free_batch(dic::BatchState* b) {
   delete b;
 }
 
+void free_stream(dic::StreamState* q) {
+  if (!q) return;
+  if (q->side) cudaStreamSynchronize(q->side);
+  for (int k = 0; k < 3; ++k) {
+    if (q->frame[k]) cudaFree(q->frame[k]);
+    if (q->grad[k]) cudaFree(q->grad[k]);
+    if (q->gimg[k]) cudaFree(q->gimg[k]);
+    if (q->gq[k]) cudaFree(q->gq[k]);
+    if (q->refined[k]) cudaEventDestroy(q->refined[k]);
+  }
+  if (q->searched) cudaEventDestroy(q->searched);
+  if (q->side) cudaStreamDestroy(q->side);
+  delete q;
+}
+
 }  // namespace
 
 extern "C" {
@@ -173,6 +188,7 @@ extern "C" {
 void dic_destroy(dic_t h) {
   if (!h) return;
   free_batch(h->batch);
+  free_stream(h->seq);
   if (h->gimg) cudaFree(h->gimg);
   if (h->grad) cudaFree(h->grad);
   if (h->gq) cudaFree(h->gq);
@@ -377,7 +393,8 @@ dic_status dic_backward(dic_t h, const float* p6, const float* grad_loss, float 
 
 dic_status dic_num_pois(dic_t h, int* n_pois, int* nx, int* ny) {
   if (!h) return DIC_ERR_ARG;
-  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (!h->have_pair && !(h->seq && h->seq->frames > 0))
+    return fail(h, DIC_ERR_STATE, "no image pair set");
   if (n_pois) *n_pois = (int)h->g.n_pois;
   if (nx) *nx = h->g.nx;
   if (ny) *ny = h->g.ny;
@@ -479,14 +496,16 @@ dic_status dic_pso_search(dic_t h, int modified, int particles, int generations,
   return DIC_OK;
 }
 
-dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
-                              uint8_t* status) {
-  if (!h) return DIC_ERR_ARG;
-  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
-  if (h->ref_f32)
-    return fail(h, DIC_ERR_UNSUPPORTED, "integer search needs an 8-bit pair (exact sums)");
-  if (h->g.n_pois == 0) return DIC_OK;
-  if (!u0 || !v0 || !zncc0 || !status) return fail(h, DIC_ERR_ARG, "null output pointer");
+}  // extern "C"
+
+namespace {
+
+// Integer search of the 8-bit images (ref, def) with the handle's geometry
+// (h->g), form and search scratch, on stream st; tma_ok / tm_ref / tm_def
+// describe TMA staging of those images for the FP32 form.
+dic_status search_images(dic_t h, const uint8_t* ref, const uint8_t* def, bool tma_ok,
+                         const CUtensorMap* tm_ref, const CUtensorMap* tm_def, int32_t* u0,
+                         int32_t* v0, float* zncc0, uint8_t* status, cudaStream_t st) {
   if (h->form == DIC_FORM_BF16TC) {
     dic::SearchTcParams t{};
     if (!dic::search_tc_geometry(h->g.W, h->g.H, h->subset, h->step, h->R, h->g.nx, h->g.ny,
@@ -513,8 +532,8 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
       h->tc_pois = (size_t)h->g.n_pois;
       h->tc_slot_elems = slots;
     }
-    t.ref = h->ref;
-    t.def = h->def;
+    t.ref = ref;
+    t.def = def;
     t.W = h->g.W;
     t.H = h->g.H;
     t.pitch = h->g.pitch;
@@ -546,15 +565,15 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
     CUtensorMap tma, tmb;
     if (!encode_tc(&tma, &tmb, t))
       return fail(h, DIC_ERR_UNSUPPORTED, "tensor-core search: tensor map encoding failed");
-    cudaError_t e = dic::launch_search_tc(t, &tma, &tmb, h->stream);
+    cudaError_t e = dic::launch_search_tc(t, &tma, &tmb, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "tensor-core search launch");
     return DIC_OK;
   }
   if (dic::search_smem_bytes(h->subset, h->R) > 227 * 1024)
     return fail(h, DIC_ERR_UNSUPPORTED, "search window too large for shared memory");
   dic::SearchParams p;
-  p.ref = h->ref;
-  p.def = h->def;
+  p.ref = ref;
+  p.def = def;
   p.W = h->g.W;
   p.H = h->g.H;
   p.pitch = h->g.pitch;
@@ -564,16 +583,76 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
   p.step = h->step;
   p.nx = h->g.nx;
   p.n_pois = h->g.n_pois;
-  p.use_tma = h->tma_ok ? 1 : 0;
+  p.use_tma = tma_ok ? 1 : 0;
   p.u0 = u0;
   p.v0 = v0;
   p.zncc0 = zncc0;
   p.status = status;
   p.err_flag = h->err_flag;
-  cudaError_t e = dic::launch_search(p, &h->tm_ref, &h->tm_def, h->stream);
+  cudaError_t e = dic::launch_search(p, tm_ref, tm_def, st);
   if (e != cudaSuccess) return cuda_fail(h, e, "integer search launch");
   return DIC_OK;
 }
+
+// Sub-pixel refinement with the handle's geometry and options: reference
+// image ref (8-bit) with its gradient field grad, deformed image as float
+// gimg and tap quads gq, on stream st.
+dic_status subpixel_images(dic_t h, dic_method method, const uint8_t* ref, const float2* grad,
+                           const float* gimg, const uint2* gq, const int32_t* u0,
+                           const int32_t* v0, const uint8_t* status0, float* u, float* v,
+                           float* ux, float* uy, float* vx, float* vy, float* zncc,
+                           int32_t* iters, uint8_t* status, cudaStream_t st) {
+  dic::SubpixelParams p;
+  p.ref = ref;
+  p.grad = grad;
+  p.gimg = gimg;
+  p.gq = gq;
+  p.W = h->g.W;
+  p.H = h->g.H;
+  p.pitch = h->g.pitch;
+  p.S = h->subset;
+  p.M = h->M;
+  p.R = h->R;
+  p.step = h->step;
+  p.nx = h->g.nx;
+  p.n_pois = h->g.n_pois;
+  p.max_iter = h->max_iter;
+  p.tol = h->tol;
+  p.u0 = u0;
+  p.v0 = v0;
+  p.st0 = status0;
+  p.u = u;
+  p.v = v;
+  p.ux = ux;
+  p.uy = uy;
+  p.vx = vx;
+  p.vy = vy;
+  p.zncc = zncc;
+  p.iters = iters;
+  p.status = status;
+  cudaError_t e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, st,
+                                       h->interp == DIC_INTERP_BILINEAR);
+  if (e != cudaSuccess) return cuda_fail(h, e, "subpixel launch");
+  return DIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
+                              uint8_t* status) {
+  if (!h) return DIC_ERR_ARG;
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->ref_f32)
+    return fail(h, DIC_ERR_UNSUPPORTED, "integer search needs an 8-bit pair (exact sums)");
+  if (h->g.n_pois == 0) return DIC_OK;
+  if (!u0 || !v0 || !zncc0 || !status) return fail(h, DIC_ERR_ARG, "null output pointer");
+  return search_images(h, h->ref, h->def, h->tma_ok, &h->tm_ref, &h->tm_def, u0, v0, zncc0,
+                       status, h->stream);
+}
+
+
 
 dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int32_t* v0,
                         const uint8_t* status0, float* u, float* v, float* ux, float* uy,
@@ -1066,6 +1145,153 @@ dic_status dic_autotune(dic_t h, dic_method method, const dic_batch_out* out, in
     chosen[1] = bm;
   }
   return best < 1e30f ? DIC_OK : fail(h, DIC_ERR_CUDA, "no candidate ran");
+}
+
+
+// ------------------------------------------------------- frame streams
+dic_status dic_stream_push(dic_t h, const uint8_t* frame, int width, int height, int pitch_bytes,
+                           dic_method method, const dic_batch_out* out) {
+  if (!h) return DIC_ERR_ARG;
+  if (!frame) return fail(h, DIC_ERR_ARG, "null frame pointer");
+  if (width < 4 || height < 4 || pitch_bytes < width)
+    return fail(h, DIC_ERR_ARG, "bad frame size %dx%d pitch %d", width, height, pitch_bytes);
+  if (method != DIC_ICGN && method != DIC_FANR) return fail(h, DIC_ERR_ARG, "unknown method");
+  if (!h->seq) {
+    h->seq = new (std::nothrow) dic::StreamState();
+    if (!h->seq) return fail(h, DIC_ERR_OOM, "cannot allocate the stream state");
+  }
+  dic::StreamState* q = h->seq;
+  const long long k = q->frames;
+  if (k > 0 && (width != q->W || height != q->H))
+    return fail(h, DIC_ERR_ARG, "frame %dx%d differs from the sequence's %dx%d", width, height,
+                q->W, q->H);
+  int nx = 0, ny = 0;
+  grid_of(width, height, h->subset, h->step, h->R, &nx, &ny);
+  const int64_t n = (int64_t)nx * ny;
+  if (k > 0 && n > 0 &&
+      (!out || !out->u0 || !out->v0 || !out->zncc0 || !out->status0 || !out->u || !out->v ||
+       !out->ux || !out->uy || !out->vx || !out->vy || !out->zncc || !out->iters ||
+       !out->status))
+    return fail(h, DIC_ERR_ARG, "null output array");
+  if (k == 0) {
+    // a new sequence: (re)allocate the ring for this frame size
+    const int rp = (width + 15) / 16 * 16;
+    const size_t px = (size_t)width * height;
+    if (q->pending && q->side) cudaStreamSynchronize(q->side);
+    q->pending = false;
+    if (rp != q->pitch || height != q->H || px > q->px) {
+      for (int j = 0; j < 3; ++j) {
+        if (q->frame[j]) cudaFree(q->frame[j]);
+        if (q->grad[j]) cudaFree(q->grad[j]);
+        if (q->gimg[j]) cudaFree(q->gimg[j]);
+        if (q->gq[j]) cudaFree(q->gq[j]);
+        q->frame[j] = nullptr;
+        q->grad[j] = nullptr;
+        q->gimg[j] = nullptr;
+        q->gq[j] = nullptr;
+      }
+      q->px = 0;
+      for (int j = 0; j < 3; ++j)
+        if (cudaMalloc(&q->frame[j], (size_t)rp * height) != cudaSuccess ||
+            cudaMalloc(&q->grad[j], px * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc(&q->gimg[j], px * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&q->gq[j], px * sizeof(uint2)) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(h, DIC_ERR_OOM, "cannot allocate the frame ring (%zu bytes)",
+                      3 * ((size_t)rp * height + 20 * px));
+        }
+      q->px = px;
+    }
+    if (!q->side) {
+      if (cudaStreamCreateWithFlags(&q->side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&q->searched, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(h, cudaGetLastError(), "stream set-up");
+      for (int j = 0; j < 3; ++j)
+        if (cudaEventCreateWithFlags(&q->refined[j], cudaEventDisableTiming) != cudaSuccess)
+          return cuda_fail(h, cudaGetLastError(), "stream set-up");
+    }
+    if (!h->err_flag) {
+      if (cudaMalloc(&h->err_flag, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DIC_ERR_OOM, "cannot allocate error flag");
+      }
+      cudaMemsetAsync(h->err_flag, 0, sizeof(unsigned int), h->stream);
+    }
+    q->W = width;
+    q->H = height;
+    q->pitch = rp;
+    // the stream's geometry replaces a bound pair
+    h->have_pair = false;
+    h->g.W = width;
+    h->g.H = height;
+    h->g.pitch = rp;
+    h->g.nx = nx;
+    h->g.ny = ny;
+    h->g.n_pois = n;
+  }
+  const int s = (int)(k % 3);
+  cudaStream_t st = h->stream;
+  cudaError_t e = cudaSuccess;
+  // slot s last served as the reference of pair k-2 (its sub-pixel work on
+  // the second stream) before this frame overwrites it
+  if (k >= 3) e = cudaStreamWaitEvent(st, q->refined[(k - 2) % 3], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(q->frame[s], q->pitch, frame, pitch_bytes, width, height,
+                          cudaMemcpyDeviceToDevice, st);
+  // the frame's precompute, once: gradients (its turn as reference), float
+  // copy and tap quads (its turn as target)
+  if (e == cudaSuccess)
+    e = dic::launch_precompute(q->frame[s], q->frame[s], width, height, q->pitch, q->grad[s],
+                               q->gimg[s], q->gq[s], st);
+  if (e != cudaSuccess) return cuda_fail(h, e, "frame copy / precompute");
+  if (k >= 1 && n > 0) {
+    const int r = (int)((k - 1) % 3);
+    // integer search of pair (k-1, k) on the handle's stream
+    CUtensorMap tmr{}, tmd{};
+    const int span = h->subset + 2 * h->R;
+    const int bwg = dic::tma_box_width(span), bwf = dic::tma_box_width(h->subset);
+    const bool tma = bwg <= 256 && span <= 256 &&
+                     encode_u8(&tmd, q->frame[s], width, height, q->pitch, bwg, span) &&
+                     encode_u8(&tmr, q->frame[r], width, height, q->pitch, bwf, h->subset);
+    dic_status ds = search_images(h, q->frame[r], q->frame[s], tma, &tmr, &tmd, out->u0, out->v0,
+                                  out->zncc0, out->status0, st);
+    if (ds != DIC_OK) return ds;
+    // its sub-pixel refinement on the second stream, overlapping the next
+    // pair's search
+    e = cudaEventRecord(q->searched, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->side, q->searched, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream ordering");
+    ds = subpixel_images(h, method, q->frame[r], q->grad[r], q->gimg[s], q->gq[s], out->u0,
+                         out->v0, out->status0, out->u, out->v, out->ux, out->uy, out->vx,
+                         out->vy, out->zncc, out->iters, out->status, q->side);
+    if (ds != DIC_OK) return ds;
+    e = cudaEventRecord(q->refined[k % 3], q->side);
+    // the previous pair's outputs join the handle's stream (after this
+    // pair's search has been enqueued)
+    if (e == cudaSuccess && q->pending) e = cudaStreamWaitEvent(st, q->refined[(k - 1) % 3], 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream ordering");
+    q->pending = true;
+  }
+  q->frames = k + 1;
+  return DIC_OK;
+}
+
+dic_status dic_stream_flush(dic_t h) {
+  if (!h) return DIC_ERR_ARG;
+  dic::StreamState* q = h->seq;
+  if (!q || !q->pending) return DIC_OK;
+  cudaError_t e = cudaStreamWaitEvent(h->stream, q->refined[(q->frames - 1) % 3], 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream flush");
+  q->pending = false;
+  return DIC_OK;
+}
+
+dic_status dic_stream_reset(dic_t h) {
+  if (!h) return DIC_ERR_ARG;
+  dic_status st = dic_stream_flush(h);
+  if (st != DIC_OK) return st;
+  if (h->seq) h->seq->frames = 0;
+  return DIC_OK;
 }
 
 }  // extern "C"

@@ -247,6 +247,27 @@ struct BatchState {
 };
 }  // namespace dic
 
+namespace dic {
+// State of a consecutive-frame stream (dic_stream_push): a ring of three
+// frame slots, each holding the frame (copied, 16-byte pitch) and its
+// precompute (gradient field for its turn as reference; float copy and tap
+// quads for its turn as target); the sub-pixel launches run on a second
+// stream, ordered by events.
+struct StreamState {
+  int W = 0, H = 0, pitch = 0;  // pitch of the ring's frames (bytes)
+  long long frames = 0;         // frames pushed since the last reset
+  uint8_t* frame[3] = {};
+  float2* grad[3] = {};
+  float* gimg[3] = {};
+  uint2* gq[3] = {};
+  size_t px = 0;                // pixels per slot allocated
+  cudaStream_t side = nullptr;
+  cudaEvent_t searched = nullptr;    // a pair's integer search is done
+  cudaEvent_t refined[3] = {};       // pair k's sub-pixel work is done (k % 3)
+  bool pending = false;              // a pair's sub-pixel work not yet joined
+};
+}  // namespace dic
+
 struct dic_s {
   int subset = 0, M = 0, step = 0, R = 0, shape_order = 1, max_iter = 0;
   float tol = 0.f;
@@ -272,6 +293,7 @@ struct dic_s {
   CUtensorMap tm_ref{}, tm_def{};
 
   dic::BatchState* batch = nullptr;
+  dic::StreamState* seq = nullptr;
 
   // scratch of the tensor-core search form
   uint16_t* tc_phase = nullptr;

@@ -92,8 +92,9 @@ def test_swarm_shapes_and_stop_rules(particles, gens, stop, c, modified):
     ref = oracle.pso_search(f, g, subset, step, radius, rand, modified=modified, c1=c[0],
                             c2=c[1], vinit=1.7, stop=stop)
     compare(gpu, ref)
-    if stop == (0, 1):  # C >= 0 ends the swarm after its first generation
-        assert (gpu["generations"][gpu["zncc"] >= 0] == 1).all()
+    if stop == (0, 1):  # C >= 0 ends the swarm at the generation that reaches it
+        assert (gpu["zncc"][gpu["generations"] < gens] >= 0).all()
+        assert (gpu["generations"][gpu["zncc"] < 0] == gens).all()
 
 
 @pytest.mark.parametrize("subset,step,radius,size", [(5, 3, 2, 30), (41, 12, 6, 120),
