@@ -82,7 +82,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=36100,
                     help="POIs in the oracle's CPU sample (default: the whole pair)")
     ap.add_argument("--workload", default="affine1024",
-                    choices=["affine1024", "sine2048x64", "mixed32", "affine1024x8"],
+                    choices=["affine1024", "sine2048x64", "mixed32", "affine1024x8",
+                             "tensile1024x16"],
                     help="affine1024 is the headline; the others measure the batched form "
                          "and the adjoint")
     ap.add_argument("--pairs", type=int, default=0, help="limit the number of pairs (0 = all)")
@@ -469,6 +470,9 @@ def run_gpu(args):
             "adjoint_affine1024x8": adjoint_record(dev, args.sub_steps, args.sub_warmup,
                                                    fp32_peak=fp32_peak,
                                                    atomic_peak=atomic_peak),
+            "stream_tensile1024x16": stream_record(dev, args.sub_steps, args.sub_warmup,
+                                                   solve_bits=args.solve_bits,
+                                                   fp32_peak=fp32_peak),
             "measured_peaks": {"fp32_fma_tflops": fp32_meas,
                                "smem_atomic_f32_per_s": atomic_peak},
             "wall_s": None}
@@ -940,6 +944,152 @@ def adjoint_record(dev, steps: int, warmup: int, n_pairs: int = 8,
     return rec
 
 
+def stream_record(dev, steps: int, warmup: int, solve_bits: int = 64,
+                  fp32_peak: float | None = None, cpu_pois: int = 1024) -> dict:
+    """The tensile1024x16 frame sequence (17 frames, reference updated every
+    frame) through dic_stream_push: converged POI/s over its 16 consecutive
+    pairs with the frames resident, the same pairs through the single-pair
+    calls, and end to end with every frame copied from pinned host memory
+    inside the timed region (one frame per pair)."""
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    from workloads import configs
+    seq = configs.tensile_sequence()
+    fr, S, st, R = seq["frames"], seq["subset"], seq["step"], seq["radius"]
+    peaks = load_peaks()
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    stream = torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    frames = [torch.from_numpy(f).to(dev) for f in fr]
+    h = dic.dic_create(S, st, R, 1, TOL, MAX_ITER)
+    dic.dic_set_form(h, dic.DIC_FORM_BF16TC)
+    dic.dic_set_solve_precision(h, solve_bits)
+    dic.dic_set_stream(h, stream)
+    with torch.cuda.stream(stream):
+        dic.dic_stream_push(h, frames[0], dic.DIC_ICGN)
+    n, _, _ = dic.dic_num_pois(h)
+    outs = [dic.batch_outputs(n, dev) for _ in range(len(fr) - 1)]
+
+    def run_seq():
+        dic.dic_stream_reset(h)
+        dic.dic_stream_push(h, frames[0], dic.DIC_ICGN)
+        for k in range(1, len(fr)):
+            dic.dic_stream_push(h, frames[k], dic.DIC_ICGN, outs[k - 1])
+        dic.dic_stream_flush(h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            run_seq()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    sampler.wait_first()
+    a, e = ev(), ev()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(steps):
+            run_seq()
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = sampler.stop()
+    ms = a.elapsed_time(e) / steps
+    conv = sum(int((o["status"] == 0).sum()) for o in outs)
+    pairs = len(fr) - 1
+    search_flop = 2.0 * S * S * (2 * R + 1) ** 2 * n * pairs
+    sub_flop = 0.0
+    for o in outs:
+        si, sp = subpixel_work(o["iters"], o["status"], o["status0"], S)
+        sub_flop += FLOP_PER_SAMPLE * si + FLOP_PER_PIXEL_SAMPLE * sp
+    if fp32_peak is None:
+        props = torch.cuda.get_device_properties(dev)
+        fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+    pre_bytes = PRECOMPUTE_BYTES_PER_PX * fr[0].size * pairs
+    t_roof = search_flop / (bf16_peak * 1e12) + sub_flop / (fp32_peak * 1e12) + pre_bytes / hbm
+    # the same pairs through the single-pair calls
+    hs = dic.dic_create(S, st, R, 1, TOL, MAX_ITER)
+    dic.dic_set_form(hs, dic.DIC_FORM_BF16TC)
+    dic.dic_set_solve_precision(hs, solve_bits)
+    dic.dic_set_stream(hs, stream)
+    so = dic.batch_outputs(n, dev)
+
+    def run_pairs():
+        for k in range(1, len(fr)):
+            dic.dic_set_pair(hs, frames[k - 1], frames[k])
+            dic.dic_integer_search(hs, so["u0"], so["v0"], so["zncc0"], so["status0"])
+            dic.dic_subpixel(hs, dic.DIC_ICGN, so["u0"], so["v0"], so["status0"], so["u"],
+                             so["v"], so["ux"], so["uy"], so["vx"], so["vy"], so["zncc"],
+                             so["iters"], so["status"])
+    with torch.cuda.stream(stream):
+        run_pairs()
+        torch.cuda.synchronize(dev)
+        a, e = ev(), ev()
+        a.record(stream)
+        for _ in range(steps):
+            run_pairs()
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_pairs = a.elapsed_time(e) / steps
+    dic.dic_destroy(hs)
+    # end to end: each frame from pinned host memory into one device buffer,
+    # pushed, every pair's outputs read back, all inside the events
+    hfr = [torch.from_numpy(f).pin_memory() for f in fr]
+    hout = [{k: torch.empty_like(v, device="cpu").pin_memory() for k, v in o.items()}
+            for o in outs]
+    dbuf = torch.empty_like(frames[0])
+    with torch.cuda.stream(stream):
+        a, e = ev(), ev()
+        a.record(stream)
+        dic.dic_stream_reset(h)
+        dbuf.copy_(hfr[0], non_blocking=True)
+        dic.dic_stream_push(h, dbuf, dic.DIC_ICGN)
+        for k in range(1, len(fr)):
+            dbuf.copy_(hfr[k], non_blocking=True)
+            dic.dic_stream_push(h, dbuf, dic.DIC_ICGN, outs[k - 1])
+            if k >= 2:  # the previous pair's outputs are complete on this stream now
+                for key in hout[k - 2]:
+                    hout[k - 2][key].copy_(outs[k - 2][key], non_blocking=True)
+        dic.dic_stream_flush(h)
+        for key in hout[-1]:
+            hout[-1][key].copy_(outs[-1][key], non_blocking=True)
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = a.elapsed_time(e)
+    e_conv = sum(int((o["status"] == 0).sum()) for o in hout)
+    dic.dic_destroy(h)
+
+    class _P:
+        pass
+    pl = []
+    for k in (1, pairs // 2, pairs):
+        q = _P()
+        q.ref, q.defm, q.subset, q.step, q.radius = fr[k - 1], fr[k], S, st, R
+        pl.append(q)
+    threads = os.cpu_count() or 1
+    cs = oracle_sample(pl, range(len(pl)), cpu_pois, threads)
+    return {"workload": "tensile1024x16", "frames": len(fr), "pairs": pairs, "pois_per_pair": n,
+            "subset": S, "grid_step": st, "search_radius": R,
+            "form": "dic_stream_push: tensor-core search on the handle's stream, sub-pixel "
+                    "(IC-GN) on a second stream overlapping the next pair's search",
+            "solve": f"fp{solve_bits}", "ms_per_step": ms, "value": conv / (ms / 1e3),
+            "unit": UNIT, "frames_per_s": pairs / (ms / 1e3), "steps": steps, "warmup": warmup,
+            "converged_fraction": conv / (n * pairs),
+            "single_pair_calls": {"ms_per_step": ms_pairs, "value": conv / (ms_pairs / 1e3),
+                                  "stream_gain": ms_pairs / ms},
+            "e2e": {"value": e_conv / (e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(f.size for f in fr)),
+                    "d2h_bytes_per_step": int(sum(v.numel() * v.element_size()
+                                                  for o in hout for v in o.values()))},
+            "roofline_path": {"roofline_ms": t_roof * 1e3, "measured_ms": ms,
+                              "frac": t_roof * 1e3 / ms},
+            "cpu_baseline": {"value": cs["value"], "unit": UNIT, "cores": threads,
+                             "kind": "oracle",
+                             "sample": (f"{cs['pois']} POIs: {cpu_pois} evenly spaced POIs of "
+                                        f"pairs 1, {pairs // 2}, {pairs}, {cs['seconds']:.1f} s")},
+            "clocks": clk}
+
+
 def run_batch_workload(args):
     """One record of the batched forms (sine2048x64, mixed32) or of the
     adjoint (affine1024x8), printed as its own JSON line."""
@@ -950,7 +1100,10 @@ def run_batch_workload(args):
     torch.cuda.set_device(dev)
     dic.build()
     fp32_peak = dic.dic_measure_peak(dic.DIC_PEAK_FP32_FMA) / 1e12
-    if args.workload == "affine1024x8":
+    if args.workload == "tensile1024x16":
+        rec = stream_record(dev, args.steps, args.warmup, solve_bits=args.solve_bits,
+                            fp32_peak=fp32_peak)
+    elif args.workload == "affine1024x8":
         rec = adjoint_record(dev, args.steps, args.warmup, n_pairs=args.pairs or 8,
                              fp32_peak=fp32_peak,
                              atomic_peak=dic.dic_measure_peak(dic.DIC_PEAK_SMEM_ATOMIC_F32))

@@ -299,6 +299,47 @@ dic_status dic_set_batch_shape(dic_t h, int warps_per_cta, int grid_mult);
  * {0, 0} for the overlapped per-pair launches. */
 dic_status dic_autotune(dic_t h, dic_method method, const dic_batch_out *out, int *chosen);
 
+/* ---------------------------------------------------------- frame streams
+ * Consecutive-frame processing as the paper evaluates its image series
+ * (Sections 3 and 5.1): every new frame is the target of one pair whose
+ * reference is the previous frame, so the reference is updated after every
+ * evaluation and consecutive frames differ by small displacements.
+ *
+ * dic_stream_push copies the frame (device pointer; width, height, pitch as
+ * in dic_set_pair) into a ring of three slots inside the library and runs
+ * its precompute once: the gradient field serves the frame's later turn as
+ * reference, the float copy and tap quads its turn as target.  The first
+ * push of a sequence (after dic_create or dic_stream_reset) only stores the
+ * frame; out may be NULL.  Every later push runs the pair (previous frame,
+ * this frame): the integer search in the handle's form on the handle's
+ * stream, then the sub-pixel refinement (method; the handle's solve
+ * precision, interpolation and tolerances) on a second stream of the
+ * library, so that a pair's refinement overlaps the next pair's search.
+ *   out       device arrays of n_pois elements each (dic_num_pois after the
+ *             first push), as in dic_integer_search / dic_subpixel
+ * Ordering: the copy of the frame runs on the handle's stream, so the
+ * caller may reuse its frame buffer once that stream has passed this push.
+ * A pair's outputs are complete for any work enqueued on the handle's stream
+ * after the next push, or after dic_stream_flush; keep each push's out
+ * arrays alive and untouched until then.
+ * The first push fixes the sequence's frame size (later frames of another
+ * size: DIC_ERR_ARG) and the handle's POI grid; it replaces a pair bound by
+ * dic_set_pair (bind one again before dic_integer_search / dic_subpixel).
+ * Allocates the ring on the first push of a size (3 x (pitch x height + 20
+ * bytes per pixel); DIC_ERR_OOM on failure), a stream and four events.
+ * DIC_ERR_ARG for a null frame, bad sizes, an unknown method or a null
+ * output array of a pair; DIC_ERR_CUDA / DIC_ERR_UNSUPPORTED as the
+ * single-pair calls. */
+dic_status dic_stream_push(dic_t h, const uint8_t *frame_dev, int width, int height,
+                           int pitch_bytes, dic_method method, const dic_batch_out *out);
+
+/* Make the last pushed pair's outputs complete for later work on the
+ * handle's stream (an event wait on that stream; no host synchronisation). */
+dic_status dic_stream_flush(dic_t h);
+
+/* End the sequence (after a flush): the next push starts a new one. */
+dic_status dic_stream_reset(dic_t h);
+
 /* Summed ZNSSD of the subsets at given shapes: for POI k,
  *   L_k = sum_i [ (f_i - fbar)/df - (g(W(xi_i; p_k)) - gbar)/dg ]^2 = 2 - 2 C_k,
  * C_k being Eq. 1 at shape p_k with bicubically interpolated g.

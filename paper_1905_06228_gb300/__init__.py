@@ -70,6 +70,9 @@ SIGNATURES = {
     "dic_run_batch": (i32, [P, i32, C.POINTER(dic_batch_out)]),
     "dic_autotune": (i32, [P, i32, C.POINTER(dic_batch_out), C.POINTER(i32)]),
     "dic_set_batch_shape": (i32, [P, i32, i32]),
+    "dic_stream_push": (i32, [P, P, i32, i32, i32, i32, C.POINTER(dic_batch_out)]),
+    "dic_stream_flush": (i32, [P]),
+    "dic_stream_reset": (i32, [P]),
     "dic_backward": (i32, [P, P, P, f32, P, P]),
     "dic_integer_search": (i32, [P, P, P, P, P]),
     "dic_pso_search": (i32, [P, i32, i32, i32, C.c_double, C.c_double, C.c_double, i32, i32,
@@ -238,6 +241,24 @@ def dic_autotune(h, method: int, out: dict) -> tuple[int, int]:
 
 def dic_set_batch_shape(h, warps_per_cta: int, grid_mult: int) -> None:
     _check(lib().dic_set_batch_shape(h, warps_per_cta, grid_mult), h)
+
+
+def dic_stream_push(h, frame, method: int = DIC_ICGN, out: dict | None = None) -> None:
+    """Push the next 8-bit frame of a sequence; from the second frame on,
+    ``out`` (see batch_outputs) receives the pair (previous frame, frame)."""
+    if frame.dtype.itemsize != 1 or frame.is_floating_point():
+        raise RuntimeError("frames must be 8-bit")
+    hgt, wid = frame.shape[-2:]
+    o = C.byref(_batch_out(out)) if out is not None else None
+    _check(lib().dic_stream_push(h, _ptr(frame), wid, hgt, frame.stride(-2), method, o), h)
+
+
+def dic_stream_flush(h) -> None:
+    _check(lib().dic_stream_flush(h), h)
+
+
+def dic_stream_reset(h) -> None:
+    _check(lib().dic_stream_reset(h), h)
 
 
 def batch_outputs(total: int, device):

@@ -153,3 +153,22 @@ def test_measure_peak_argument_checks():
     assert lib.dic_measure_peak(7, None, ctypes.byref(r)) == dic.DIC_ERR_ARG
     assert lib.dic_measure_peak(-1, None, ctypes.byref(r)) == dic.DIC_ERR_ARG
     assert lib.dic_measure_peak(dic.DIC_PEAK_FP32_FMA, None, None) == dic.DIC_ERR_ARG
+
+
+def test_stream_calls_host_side_checks():
+    """Frame-stream entry points refuse null handles and frames and bad sizes
+    before any device work."""
+    lib = dic.lib()
+    assert lib.dic_stream_flush(None) == dic.DIC_ERR_ARG
+    assert lib.dic_stream_reset(None) == dic.DIC_ERR_ARG
+    assert lib.dic_stream_push(None, 16, 64, 64, 64, 0, None) == dic.DIC_ERR_ARG
+    h = dic.dic_create(21, 5, 10)
+    try:
+        assert lib.dic_stream_flush(h) == dic.DIC_OK   # nothing pushed yet
+        assert lib.dic_stream_reset(h) == dic.DIC_OK
+        assert lib.dic_stream_push(h, None, 64, 64, 64, 0, None) == dic.DIC_ERR_ARG
+        assert lib.dic_stream_push(h, 16, 2, 64, 64, 0, None) == dic.DIC_ERR_ARG
+        assert lib.dic_stream_push(h, 16, 64, 64, 32, 0, None) == dic.DIC_ERR_ARG
+        assert lib.dic_stream_push(h, 16, 64, 64, 64, 5, None) == dic.DIC_ERR_ARG
+    finally:
+        dic.dic_destroy(h)

@@ -20,6 +20,12 @@ mixed32                32 pairs: 8 each of 512^2, 1024^2, 2048^2, 4096^2,
                        from {15, 21, 31, 41, 51}, step floor(subset/3)
 affine1024x8           8 pairs as affine1024 (deformation and noise),
                        subset 31, step 8, search +-20 px
+tensile1024x16         17 frames 1024x1024 of one speckle pattern (40000
+                       speckles, noise 2) under a growing tensile load:
+                       frame k has exx = 0.05 % k, eyy = -0.015 % k and a
+                       drift of (0.35, -0.1) px per frame; 16 consecutive
+                       pairs (reference updated every frame); subset 31,
+                       step 5, search +-12 px (a window of 25 pixels)
 =====================  =====================================================
 """
 from __future__ import annotations
@@ -28,11 +34,12 @@ import math
 
 import numpy as np
 
-from .speckle import Affine, Pair, Rigid, Sinusoidal, render_pair
+from .speckle import Affine, Pair, Rigid, Sinusoidal, render_pair, render_sequence
 
 SEED_BASE = 190506228
 
-WORKLOADS = ("rigid256", "affine1024", "sine2048x64", "mixed32", "affine1024x8")
+WORKLOADS = ("rigid256", "affine1024", "sine2048x64", "mixed32", "affine1024x8",
+             "tensile1024x16")
 
 
 def seed_of(workload_index: int, pair: int) -> int:
@@ -100,6 +107,19 @@ def affine1024x8(pair: int) -> Pair:
     d = _affine1024_map()
     f, g = render_pair(seed_of(4, pair), 1024, 1024, 40000, d, 2.0, pad=40.0)
     return Pair(f, g, d, subset=31, step=8, radius=20, meta={"workload": "affine1024x8"})
+
+
+def tensile_sequence(frames: int = 17, size: int = 1024, n_speckles: int = 40000,
+                     noise: float = 2.0, seed_index: int = 5) -> dict:
+    """Frames of the tensile sequence and its analysis parameters; frame k
+    is the pattern under exx = 5e-4 k, eyy = -1.5e-4 k, t = (0.35 k, -0.1 k)
+    about the image centre."""
+    c = (size - 1) / 2.0
+    maps = [None] + [Affine(5e-4 * k, -1.5e-4 * k, 0.0, 0.35 * k, -0.1 * k, c, c)
+                     for k in range(1, frames)]
+    imgs = render_sequence(seed_of(seed_index, 0), size, size, n_speckles, maps, noise,
+                           pad=40.0)
+    return dict(frames=imgs, maps=maps, subset=31, step=5, radius=12)
 
 
 def tiny(seed: int, width: int = 24, height: int = 24, n_speckles: int = 40,

@@ -237,3 +237,22 @@ def render_pair(seed: int, width: int, height: int, n_speckles: int, deformation
         f = f + rng.normal(0.0, noise_sigma, f.shape)
         g = g + rng.normal(0.0, noise_sigma, g.shape)
     return quantise(f), quantise(g)
+
+
+def render_sequence(seed: int, width: int, height: int, n_speckles: int, deformations,
+                    noise_sigma: float = 0.0, pad: float | None = None) -> list[np.ndarray]:
+    """Render a frame sequence of one speckle pattern: frame k is the field
+    seen through ``deformations[k]`` (None = undeformed), with its own
+    noise draw; one PCG64 stream of ``seed`` for speckles and noise."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if pad is None:
+        pad = 4 * 4.0 + 8.0
+    sp = draw_speckles(rng, n_speckles, width, height, pad)
+    ident = (lambda x, y: (x, y))
+    frames = []
+    for d in deformations:
+        img = _render(sp, width, height, d.inverse if d else ident, d.forward if d else ident)
+        if noise_sigma > 0:
+            img = img + rng.normal(0.0, noise_sigma, img.shape)
+        frames.append(quantise(img))
+    return frames
