@@ -945,7 +945,7 @@ def adjoint_record(dev, steps: int, warmup: int, n_pairs: int = 8,
 
 
 def stream_record(dev, steps: int, warmup: int, solve_bits: int = 64,
-                  fp32_peak: float | None = None, cpu_pois: int = 1024) -> dict:
+                  fp32_peak: float | None = None, cpu_pois: int = 8192) -> dict:
     """The tensile1024x16 frame sequence (17 frames, reference updated every
     frame) through dic_stream_push: converged POI/s over its 16 consecutive
     pairs with the frames resident, the same pairs through the single-pair
