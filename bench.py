@@ -44,6 +44,11 @@ FLOP_PER_SAMPLE = 96
 # per sample of a POI's first pass, at the integer start: the samples are
 # pixels (no warp, weights or convolution), only the sums remain
 FLOP_PER_PIXEL_SAMPLE = 19
+# per reference point of the IC-GN precompute, once per POI (Section 2.2:
+# the quantities IC-GN computes once): sum f 1, f - fbar and its square 3,
+# the SD products gx dx, gx dy, gy dx, gy dy 4, the 21 entries of the
+# Hessian sum SD^T SD 42, sum SD 6, sum SD (f - fbar) 12
+FLOP_PER_SETUP_POINT = 68
 # algorithmic bytes per pixel of the precompute kernel: f and g read (1 + 1),
 # gradient (8), float g (4) and BF16 tap quads (8) written
 PRECOMPUTE_BYTES_PER_PX = 22
@@ -395,7 +400,9 @@ def run_gpu(args):
     extra = (p_out["status"] != 0).to(torch.int64)
     pixel_samples = int(ran.sum().item()) * SUBSET * SUBSET
     samples = int(((its - 1) + extra)[ran].sum().item()) * SUBSET * SUBSET
-    sub_flop = FLOP_PER_SAMPLE * samples + FLOP_PER_PIXEL_SAMPLE * pixel_samples
+    setup_points = int((s_out["status0"] == 0).sum().item()) * SUBSET * SUBSET
+    sub_flop = (FLOP_PER_SAMPLE * samples + FLOP_PER_PIXEL_SAMPLE * pixel_samples +
+                FLOP_PER_SETUP_POINT * setup_points)
     sub_avg_s = statistics.mean(sub_ms) / 1e3
     sub_achieved = sub_flop / sub_avg_s / 1e12
     roofline = {"bound": "alu", "achieved": sub_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
@@ -405,7 +412,8 @@ def run_gpu(args):
                 "peak_basis": fp32_basis, "ms": sub_avg_s * 1e3,
                 "work": (f"{FLOP_PER_SAMPLE} flop x {samples} interpolated samples + "
                          f"{FLOP_PER_PIXEL_SAMPLE} flop x {pixel_samples} first-pass pixel "
-                         f"samples per launch")}
+                         f"samples + {FLOP_PER_SETUP_POINT} flop x {setup_points} set-up "
+                         f"points per launch")}
     # the integer search: algorithmic flops 2 N (2R+1)^2 per POI (padded and
     # wasted MACs not counted)
     search_avg_s = statistics.mean(search_ms) / 1e3
@@ -636,17 +644,19 @@ def oracle_sample(pairs, pair_ids, pois_per_pair: int, threads: int) -> dict:
     return {"value": conv / dt, "seconds": dt, "pois": n}
 
 
-def subpixel_work(iters, status, status0, subset: int) -> tuple[int, int]:
+def subpixel_work(iters, status, status0, subset: int) -> tuple[int, int, int]:
     """Interpolated and first-pass pixel samples of one sub-pixel launch: one
     pass per solve (the first at the integer start reads pixels) plus one
     interpolating pass at the returned shape for POIs that did not
-    converge; N = subset^2 samples per pass."""
+    converge; N = subset^2 samples per pass; and the set-up points (N per
+    POI that entered the refinement)."""
     import torch
     its = iters.to(torch.int64)
     ran = (status0 == 0) & (its >= 1)
     extra = (status != 0).to(torch.int64)
     n = subset * subset
-    return (int(((its - 1) + extra)[ran].sum().item()) * n, int(ran.sum().item()) * n)
+    return (int(((its - 1) + extra)[ran].sum().item()) * n, int(ran.sum().item()) * n,
+            int((status0 == 0).sum().item()) * n)
 
 
 def load_peaks() -> dict:
@@ -718,9 +728,9 @@ def batch_record(workload: str, dev, steps: int, warmup: int, form: int = 1,
     for k, p in enumerate(pairs):
         a, b = offs[k], offs[k + 1]
         search_flop += 2.0 * p.subset ** 2 * (2 * p.radius + 1) ** 2 * (b - a)
-        si, sp = subpixel_work(out["iters"][a:b], out["status"][a:b], out["status0"][a:b],
-                               p.subset)
-        sub_flop += FLOP_PER_SAMPLE * si + FLOP_PER_PIXEL_SAMPLE * sp
+        si, sp, su = subpixel_work(out["iters"][a:b], out["status"][a:b],
+                                   out["status0"][a:b], p.subset)
+        sub_flop += FLOP_PER_SAMPLE * si + FLOP_PER_PIXEL_SAMPLE * sp + FLOP_PER_SETUP_POINT * su
         pre_bytes += PRECOMPUTE_BYTES_PER_PX * p.ref.size
     t_roof = search_flop / (bf16_peak * 1e12) + sub_flop / (fp32_peak * 1e12) + pre_bytes / hbm
     # the same pairs through the single-pair calls, one after the other, with
@@ -1000,8 +1010,8 @@ def stream_record(dev, steps: int, warmup: int, solve_bits: int = 64,
     search_flop = 2.0 * S * S * (2 * R + 1) ** 2 * n * pairs
     sub_flop = 0.0
     for o in outs:
-        si, sp = subpixel_work(o["iters"], o["status"], o["status0"], S)
-        sub_flop += FLOP_PER_SAMPLE * si + FLOP_PER_PIXEL_SAMPLE * sp
+        si, sp, su = subpixel_work(o["iters"], o["status"], o["status0"], S)
+        sub_flop += FLOP_PER_SAMPLE * si + FLOP_PER_PIXEL_SAMPLE * sp + FLOP_PER_SETUP_POINT * su
     if fp32_peak is None:
         props = torch.cuda.get_device_properties(dev)
         fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12

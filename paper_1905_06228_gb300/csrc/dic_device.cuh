@@ -171,7 +171,10 @@ struct WarpAffine {
         xm(x0 - kMagicBits),
         ym(y0 - kMagicBits) {}
   __device__ __forceinline__ size_t locate(float2 DX, float2 DY, int W, int H, float2& t) const {
-    const float2 l = __ffma2_rn(b, DY, __ffma2_rn(a, DX, o));
+    return locate_l(__ffma2_rn(b, DY, __ffma2_rn(a, DX, o)), W, H, t);
+  }
+  // the same from the local displacement l itself
+  __device__ __forceinline__ size_t locate_l(float2 l, int W, int H, float2& t) const {
     const float2 r = __fadd2_rd(l, dup2(kMagic));
     const float2 fl = __fadd2_rn(r, dup2(-kMagic));
     t = __ffma2_rn(fl, dup2(-1.f), l);  // l - floor(l), one rounding as in locate

@@ -182,6 +182,29 @@ __device__ __forceinline__ bool invert_to_smem(float mine, int lane, TS* hinv) {
   return true;
 }
 
+// Row a of H^-1 (shared memory, solve precision) times rhs, for a = 0..5,
+// on every lane.  Lanes 0..17 each form two products of row lane/3
+// (columns 2 (lane % 3) and + 1); the three partial sums of a row meet on
+// lane 3a by two shuffles, so the solve precision's work is two conversions,
+// a multiply, a multiply-add and two adds per warp instead of six
+// conversions and six multiply-adds.
+template <typename TS>
+__device__ __forceinline__ void apply_hinv(const TS* hinv, const float (&rhs)[6], int lane,
+                                           float (&out)[6]) {
+  const int r = min(lane / 3, 5), j = 2 * (lane % 3);
+  float b0 = rhs[0], b1 = rhs[1];
+  if (j == 2) b0 = rhs[2], b1 = rhs[3];
+  if (j == 4) b0 = rhs[4], b1 = rhs[5];
+  const TS* hr = hinv + r * 6 + j;
+  TS acc = hr[0] * (TS)b0;
+  acc = fma(hr[1], (TS)b1, acc);
+  const TS a1 = __shfl_down_sync(0xffffffffu, acc, 1);
+  const TS a2 = __shfl_down_sync(0xffffffffu, acc, 2);
+  const float mine = (float)((acc + a1) + a2);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) out[a] = __shfl_sync(0xffffffffu, mine, 3 * a);
+}
+
 // 8-bit pixel as float without a conversion instruction: its bits OR'd into
 // the mantissa of 2^23, minus 2^23 (exact).
 __device__ __forceinline__ float pixel_value(uint8_t b) {
@@ -265,11 +288,268 @@ __host__ __device__ inline size_t warp_smem_bytes(int N, size_t point_bytes) {
   return ((size_t)N * point_bytes + 15) / 16 * 16 + 36 * sizeof(double) + 12 * sizeof(float);
 }
 
+// IC-GN of one POI of an 8-bit pair with bicubic interpolation when the
+// subset width is 31 or 15 (LPR = 32 or 16 lanes per subset row): lane c of
+// each group of LPR lanes owns column dx = c - M of every (32 / LPR)-th row
+// (the last lane of a group idles), so dx is constant per lane.  The
+// arithmetic is the generic path's; what changes is where the work lands:
+//  - the set-up keeps per-lane sums of g_a g_b, g_a g_b dy, g_a g_b dy^2,
+//    g_a, g_a dy, g_a (f - fbar) and g_a (f - fbar) dy (a, b in {x, y}) and
+//    multiplies by the lane's dx (and dx^2) once, instead of every product
+//    of the SD vector per point;
+//  - a sample's local displacement is one multiply-add from the lane's
+//    column term (u + (1+ux) dx, v + vx dx) and dy -- the same two
+//    roundings as the generic walk, so the same sample positions -- and the
+//    walk is a row step;
+//  - sum SD_1 (g - c) and sum SD_4 (g - c) are dx times the lane's
+//    sum SD_0 (g - c) and sum SD_3 (g - c), formed once per pass;
+//  - the point records hold f - fbar instead of f.
+template <typename TS, int LPR>
+__device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t poi, int lane,
+                                             unsigned char* wsm) {
+  using PS = PointStore<uint8_t>;
+  using G = PS::T;
+  constexpr int S = LPR - 1, M = S / 2, N = S * S, RPP = 32 / LPR;
+  const int x0 = M + p.R + 2 + (int)(poi % p.nx) * p.step;
+  const int y0 = M + p.R + 2 + (int)(poi / p.nx) * p.step;
+  const int W = p.W, H = p.H;
+  G* spt = reinterpret_cast<G*>(wsm);
+  TS* hinv = reinterpret_cast<TS*>(wsm + ((size_t)N * sizeof(G) + 15) / 16 * 16);
+  float* ssd = reinterpret_cast<float*>(hinv + 36);  // sum SD
+  float* sbf = ssd + 6;                              // sum SD (f - fbar)
+  const int col = lane % LPR, row0 = lane / LPR;
+  const bool act = col < S;
+  const float fdx = (float)(col - M);
+
+  const uint8_t st0 = p.st0[poi];
+  float prm[6] = {(float)p.u0[poi], 0.f, 0.f, (float)p.v0[poi], 0.f, 0.f};
+  auto write_out = [&](float zn, int it, uint8_t st) {
+    if (lane == 0) {
+      p.u[poi] = prm[0];
+      p.ux[poi] = prm[1];
+      p.uy[poi] = prm[2];
+      p.v[poi] = prm[3];
+      p.vx[poi] = prm[4];
+      p.vy[poi] = prm[5];
+      p.zncc[poi] = zn;
+      p.iters[poi] = it;
+      p.status[poi] = st;
+    }
+  };
+  if (st0 != kOk) {
+    write_out(0.f, 0, st0);
+    return;
+  }
+
+  // ---- reference subset into shared memory, sum of f (exact)
+  float fsum = 0.f;
+  if (act) {
+#pragma unroll 4
+    for (int r = row0; r < S; r += RPP) {
+      const float f = pixel_value(p.ref[(size_t)(y0 + r - M) * p.pitch + (x0 + col - M)]);
+      fsum += f;
+      spt[r * S + col] = PS::pack(p.grad[(size_t)(y0 + r - M) * W + (x0 + col - M)], f);
+    }
+  }
+  fsum = warp_sum(fsum);
+  const float fbar = fsum / (float)N;
+  // ---- per-lane sums (each lane reads back only the records it wrote)
+  float2 g0 = dup2(0.f), g1 = dup2(0.f), g2 = dup2(0.f);   // sum g_a^2 (dy^0,1,2)
+  float2 s0 = dup2(0.f), s1 = dup2(0.f);                    // sum g_a (dy^0,1)
+  float2 fs0 = dup2(0.f), fs1 = dup2(0.f);                  // sum g_a fc (dy^0,1)
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f, q = 0.f;              // sum gx gy (dy^0,1,2)
+  if (act) {
+#pragma unroll 2
+    for (int r = row0; r < S; r += RPP) {
+      const int i = r * S + col;
+      float2 gr;
+      float f;
+      PS::unpack(spt[i], gr, f);
+      const float fc = f - fbar;
+      spt[i].f = __float_as_uint(fc);
+      q = fmaf(fc, fc, q);
+      const float dy = (float)(r - M);
+      const float2 dy2 = dup2(dy);
+      const float2 t = __fmul2_rn(gr, gr), tdy = __fmul2_rn(t, dy2);
+      g0 = __fadd2_rn(g0, t);
+      g1 = __fadd2_rn(g1, tdy);
+      g2 = __ffma2_rn(tdy, dy2, g2);
+      const float c = gr.x * gr.y, cdy = c * dy;
+      c0 += c;
+      c1 += cdy;
+      c2 = fmaf(cdy, dy, c2);
+      s0 = __fadd2_rn(s0, gr);
+      s1 = __ffma2_rn(gr, dy2, s1);
+      const float2 gfc = __fmul2_rn(gr, dup2(fc));
+      fs0 = __fadd2_rn(fs0, gfc);
+      fs1 = __ffma2_rn(gfc, dy2, fs1);
+    }
+  }
+  // the lane's share of the 33 sums, in the order of the generic path: H
+  // (packed lower triangle of SD = (gx e, gy e), e = (1, dx, dy)), sum SD,
+  // sum SD (f - fbar)
+  float v[32];
+  {
+    const float dx = act ? fdx : 0.f, dxx = dx * dx;
+    // xx block: (0,0) (1,0) (1,1) (2,0) (2,1) (2,2)
+    v[0] = g0.x; v[1] = dx * g0.x; v[2] = dxx * g0.x;
+    v[3] = g1.x; v[4] = dx * g1.x; v[5] = g2.x;
+    // row 3 (gy e0): xy block then yy (3,3)
+    v[6] = c0; v[7] = dx * c0; v[8] = c1; v[9] = g0.y;
+    // row 4 (gy e1): xy, then yy (4,3) (4,4)
+    v[10] = dx * c0; v[11] = dxx * c0; v[12] = dx * c1; v[13] = dx * g0.y; v[14] = dxx * g0.y;
+    // row 5 (gy e2): xy, then yy (5,3) (5,4) (5,5)
+    v[15] = c1; v[16] = dx * c1; v[17] = c2; v[18] = g1.y; v[19] = dx * g1.y; v[20] = g2.y;
+    v[21] = s0.x; v[22] = dx * s0.x; v[23] = s1.x;
+    v[24] = s0.y; v[25] = dx * s0.y; v[26] = s1.y;
+    v[27] = fs0.x; v[28] = dx * fs0.x; v[29] = fs1.x;
+    v[30] = fs0.y; v[31] = dx * fs0.y;
+  }
+  const float last = warp_sum(fs1.y);  // sum SD_5 (f - fbar)
+  const float mine = reduce_scatter32(v, lane);
+  q = warp_sum(q);
+  const float df = sqrtf(q);
+  if (!(df > 0.f)) {
+    write_out(0.f, 0, kZeroVarRef);
+    return;
+  }
+  if (lane >= 21 && lane < 27) ssd[lane - 21] = mine;
+  if (lane >= 27) sbf[lane - 27] = mine;
+  if (lane == 0) sbf[5] = last;
+  if (!invert_to_smem<TS>(mine, lane, hinv)) {
+    write_out(0.f, 0, kSingular);
+    return;
+  }
+  if (!corners_in(prm, x0, y0, M, W, H)) {
+    write_out(0.f, 0, kOutOfBounds);
+    return;
+  }
+
+  const float c = fbar;
+  const float invN = 1.f / (float)N;
+  const float m2 = (float)M * (float)M;
+  uint8_t st = kMaxIter;
+  int it_done = 0;
+  float zn = 0.f;
+  bool have_zn = false;
+  for (int it = 1; it <= p.max_iter; ++it) {
+    float s0s = 0.f, s1s = 0.f, sfd = 0.f;
+    float2 a03 = dup2(0.f), a25 = dup2(0.f);
+    auto absorb = [&](int i, float g, float dy) {
+      const float d = g - c;
+      s0s += d;
+      s1s = fmaf(d, d, s1s);
+      float2 gr;
+      float fc;
+      PS::unpack(spt[i], gr, fc);
+      sfd = fmaf(fc, d, sfd);
+      const float2 ab = __fmul2_rn(gr, dup2(d));
+      a03 = __fadd2_rn(a03, ab);
+      a25 = __ffma2_rn(ab, dup2(dy), a25);
+    };
+    if (act) {
+      if (it == 1) {
+        // integer start: every sample is a pixel (see the generic path)
+        const float* gb =
+            p.gimg + (size_t)(y0 + (int)prm[3] - M) * W + (x0 + (int)prm[0] + col - M);
+#pragma unroll 4
+        for (int r = row0; r < S; r += RPP)
+          absorb(r * S + col, __ldg(gb + (size_t)r * W), (float)(r - M));
+      } else {
+        const WarpAffine wa(prm, x0, y0);
+        const float2 la = __ffma2_rn(wa.a, dup2(fdx), wa.o);
+#pragma unroll 2
+        for (int r = row0; r < S; r += RPP) {
+          const float dy = (float)(r - M);
+          float2 t;
+          const size_t cell = wa.locate_l(__ffma2_rn(wa.b, dup2(dy), la), W, H, t);
+          absorb(r * S + col, bicubic_q(p.gq, W, cell, t), dy);
+        }
+      }
+    }
+    const float2 a14 = __fmul2_rn(a03, dup2(act ? fdx : 0.f));
+    float acc[6] = {a03.x, a14.x, a25.x, a03.y, a14.y, a25.y};
+    s0s = warp_sum(s0s);
+    s1s = warp_sum(s1s);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
+    const float gm = s0s * invN;  // gbar - c
+    const float var = s1s - s0s * gm;
+    const float dg = sqrtf(fmaxf(var, 0.f));
+    if (!(dg > 0.f) || !isfinite(dg)) {
+      st = kNonFinite;
+      break;
+    }
+    float dp[6], rhs[6];
+    const float ratio = df / dg;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) rhs[a] = sbf[a] - ratio * (acc[a] - gm * ssd[a]);
+    apply_hinv<TS>(hinv, rhs, lane, dp);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) dp[a] = -dp[a];
+    it_done = it;
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) fin = fin && isfinite(dp[a]);
+    if (!fin) {
+      st = kNonFinite;
+      break;
+    }
+    float pn[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) pn[a] = prm[a];
+    compose_inverse(pn, dp);
+    if (!corners_in(pn, x0, y0, M, W, H)) {
+      st = kOutOfBounds;
+      break;
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) prm[a] = pn[a];
+    const float nrm = sqrtf(dp[0] * dp[0] + dp[3] * dp[3] +
+                            m2 * (dp[1] * dp[1] + dp[2] * dp[2] + dp[4] * dp[4] + dp[5] * dp[5]));
+    if (nrm < p.tol) {
+      zn = warp_sum(sfd) / (df * dg);
+      have_zn = true;
+      st = kOk;
+      break;
+    }
+  }
+  // ---- Eq. 1 at the returned shape (POIs that did not converge)
+  if (!have_zn) {
+    float s0s = 0.f, s1s = 0.f, sfg = 0.f;
+    if (act) {
+      for (int r = row0; r < S; r += RPP) {
+        float tx, ty, gx, gy;
+        const size_t cell = locate(prm, col - M, r - M, x0, y0, W, H, tx, ty);
+        const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
+        float2 gr;
+        float fc;
+        PS::unpack(spt[r * S + col], gr, fc);
+        s0s += d;
+        s1s = fmaf(d, d, s1s);
+        sfg = fmaf(fc, d, sfg);
+      }
+    }
+    s0s = warp_sum(s0s);
+    s1s = warp_sum(s1s);
+    sfg = warp_sum(sfg);
+    const float var = s1s - s0s * s0s * invN;
+    const float dgf = sqrtf(fmaxf(var, 0.f));
+    zn = dgf > 0.f ? sfg / (df * dgf) : 0.f;
+  }
+  write_out(zn, it_done, st);
+}
+
 // Refinement of one POI by one warp; wsm is the warp's shared block.  BIL:
 // bilinear interpolation of g (Eq. 5) instead of bicubic.
 template <bool FANR, typename TS, typename TP, bool BIL = false>
 __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t poi, int lane,
                                              unsigned char* wsm) {
+  if constexpr (!FANR && !BIL && sizeof(TP) == 1) {
+    // subset widths whose rows fill a warp (or half of one): column layout
+    if (p.S == 31) return icgn_col_poi<TS, 32>(p, poi, lane, wsm);
+    if (p.S == 15) return icgn_col_poi<TS, 16>(p, poi, lane, wsm);
+  }
   using PS = PointStore<TP>;
   using G = typename PS::T;
   const int S = p.S, M = p.M, N = S * S;
@@ -559,13 +839,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       const float ratio = df / dg;
 #pragma unroll
       for (int a = 0; a < 6; ++a) rhs[a] = sbf[a] - ratio * (acc[a] - gm * ssd[a]);
-      TS acc6 = TS(0);
-      const TS* hr = hinv + (lane < 6 ? lane : 0) * 6;
+      apply_hinv<TS>(hinv, rhs, lane, dp);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) acc6 += hr[a] * (TS)rhs[a];
-      const float mine = (float)(-acc6);
-#pragma unroll
-      for (int a = 0; a < 6; ++a) dp[a] = __shfl_sync(0xffffffffu, mine, a);
+      for (int a = 0; a < 6; ++a) dp[a] = -dp[a];
       ok = true;
     } else {
       // rhs_a = ratio sum J_a (f - fbar) - (sum J_a (g - c) - gm sum J_a),
@@ -590,13 +866,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
         st = kSingular;
         break;
       }
-      TS acc6 = TS(0);
-      const TS* hr = hinv + (lane < 6 ? lane : 0) * 6;
-#pragma unroll
-      for (int a = 0; a < 6; ++a) acc6 += hr[a] * (TS)rhs[a];
-      const float mine = (float)acc6;
-#pragma unroll
-      for (int a = 0; a < 6; ++a) dp[a] = __shfl_sync(0xffffffffu, mine, a);
+      apply_hinv<TS>(hinv, rhs, lane, dp);
     }
     it_done = it;
     bool fin = true;

@@ -132,6 +132,8 @@ def test_smallest_subset_search():
 @pytest.mark.parametrize("subset,step,radius,size", [
     (5, 2, 3, 28),      # ragged: N = 25 < 32 lanes
     (9, 4, 0, 40),      # R = 0: a single candidate
+    (15, 6, 4, 80),     # column layout, two subset rows per warp
+    (31, 9, 5, 110),    # column layout, one subset row per warp
     (33, 9, 4, 96),     # N = 1089 > 1024: FP32 blocks flushed to int32
     (41, 12, 6, 120),
     (51, 20, 5, 140),
