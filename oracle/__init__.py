@@ -12,6 +12,7 @@ follows the paper's method as stated in the C file's header:
                          a first-order warp and Keys bicubic interpolation.
 * ``znssd``           -- summed ZNSSD and its hand-derived FP64 gradient.
 * ``zncc_at``         -- Eq. 1 at given shapes (interpolated target subset).
+* ``subpixel2``       -- both methods with a second-order (12-parameter) shape.
 * ``bicubic``         -- the bicubic interpolant itself (Section 2.2).
 * ``pso_search``      -- particle swarm integer search (Section 2.1, Eqs. 2-4)
                          and the modified swarm with the star search folded in.
@@ -73,6 +74,13 @@ def _load():
             lib.dico_bicubic.restype = dbl
             lib.dico_znssd.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, P, P, P, P]
             lib.dico_znssd.restype = i32
+            lib.dico_subpixel2.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, dbl, i32,
+                                           P, i64, P, P, P, i32, P, P, P, P, P]
+            lib.dico_subpixel2.restype = i32
+            lib.dico_compose2.argtypes = [P, P, P]
+            lib.dico_compose2.restype = i32
+            lib.dico_warp2_matrix.argtypes = [P, P]
+            lib.dico_warp2_matrix.restype = None
             lib.dico_zncc_at.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, P, i64, P,
                                          i32, P]
             lib.dico_zncc_at.restype = i32
@@ -160,6 +168,59 @@ def subpixel(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
                zncc=zn, iters=it, status=st, nx=nx, ny=ny)
     if trajectory:
         out["traj"] = traj
+    return out
+
+
+NAMES2 = ("u", "ux", "uy", "uxx", "uxy", "uyy", "v", "vx", "vy", "vxx", "vxy", "vyy")
+
+
+def subpixel2(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, u0, v0,
+              status0, method: int = ICGN, tol: float = 1e-3, max_iter: int = 50,
+              poi_idx=None, threads: int | None = None, trajectory: bool = False) -> dict:
+    """Sub-pixel refinement with the second-order (12-parameter) shape
+    function, p = (u, ux, uy, uxx, uxy, uyy, v, vx, vy, vxx, vxy, vyy)."""
+    f = np.ascontiguousarray(f, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    H, W = f.shape
+    nx, ny = grid(W, H, subset, step, radius)
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        n = nx * ny
+    u0 = np.ascontiguousarray(u0, np.int32)
+    v0 = np.ascontiguousarray(v0, np.int32)
+    status0 = np.ascontiguousarray(status0, np.uint8)
+    p = np.zeros((n, 12), np.float64)
+    zn = np.zeros(n, np.float64)
+    it = np.zeros(n, np.int32)
+    st = np.zeros(n, np.uint8)
+    traj = np.zeros((n, max_iter + 1, 12), np.float64) if trajectory else None
+    rc = _load().dico_subpixel2(_ptr(f), _ptr(g), W, H, W, subset, step, radius, method, tol,
+                                max_iter, _ptr(idx), n if idx is not None else -1, _ptr(u0),
+                                _ptr(v0), _ptr(status0), threads or default_threads(), _ptr(p),
+                                _ptr(zn), _ptr(it), _ptr(st), _ptr(traj))
+    if rc:
+        raise ValueError("oracle subpixel2 failed")
+    out = dict(p=p, zncc=zn, iters=it, status=st, nx=nx, ny=ny)
+    out.update({k: p[:, j] for j, k in enumerate(NAMES2)})
+    if trajectory:
+        out["traj"] = traj
+    return out
+
+
+def warp2_matrix(p) -> np.ndarray:
+    p = np.ascontiguousarray(p, np.float64)
+    out = np.zeros(36, np.float64)
+    _load().dico_warp2_matrix(_ptr(p), _ptr(out))
+    return out.reshape(6, 6)
+
+
+def compose2(p, dp) -> np.ndarray:
+    """W(p) W(dp)^-1 of two second-order shapes (the IC-GN update)."""
+    p = np.ascontiguousarray(p, np.float64)
+    dp = np.ascontiguousarray(dp, np.float64)
+    out = np.zeros(12, np.float64)
+    if _load().dico_compose2(_ptr(p), _ptr(dp), _ptr(out)):
+        raise ValueError("singular update")
     return out
 
 

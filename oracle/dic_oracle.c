@@ -28,6 +28,8 @@
  *  - The summed ZNSSD of every subset at given shape parameters and its
  *    gradient with respect to the deformed-image pixels and the parameters
  *    (hand-derived adjoint, FP64).
+ *  - Sub-pixel refinement with a second-order (12-parameter) subset shape
+ *    function, by both methods (an extension; readings at that section).
  *  - Integer search by particle swarm optimisation (Section 2.1, Eqs. 2-4)
  *    and by the modified swarm with one star-search step per generation
  *    (Sections 3, 5); the swarm's random numbers are inputs.  Readings are
@@ -521,6 +523,341 @@ int dico_subpixel_interp(const double *f, const double *g, int W, int H, int pit
     subpixel_one(f, g, W, H, pitch, x0, y0, M, method, mode, tol, max_iter, u0[k], v0[k],
                  st0[k], &p_out[k * 6], &zncc[k], &iters[k], &status[k],
                  traj ? &traj[k * (int64_t)(max_iter + 1) * 6] : NULL);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------ second-order shape */
+/* Second-order subset shape function, p = (u, ux, uy, uxx, uxy, uyy,
+ * v, vx, vy, vxx, vxy, vyy):
+ *   x = x0 + dx + u + ux dx + uy dy + uxx dx^2/2 + uxy dx dy + uyy dy^2/2
+ * (and y with the v terms), i.e. p . (1, dx, dy, dx^2/2, dx dy, dy^2/2) per
+ * direction.  The paper uses first-order shapes only; this extension keeps
+ * the first-order readings and adds:
+ *   - IC-GN: SD_i = [fx e_i, fy e_i] with e = (1, dx, dy, dx^2/2, dx dy,
+ *     dy^2/2), H = sum SD^T SD (12x12, Cholesky), dp = -H^-1 sum SD^T r;
+ *     W(p) <- W(p) W(dp)^-1 in the 6x6 representation of a quadratic warp
+ *     acting on w = (xi^2, xi eta, eta^2, xi, eta, 1), whose rows are the
+ *     warped (xi'^2, xi' eta', eta'^2, xi', eta', 1) with terms above second
+ *     order dropped; the new p is read from rows 4 and 5 of the product;
+ *   - FA-NR: J = [gx e, gy e], dp = (J^T J)^-1 J^T r, p <- p + dp;
+ *   - stop: |dp|^2 = du^2 + dv^2 + M^2 (first derivatives^2) + (M^2/2)^2
+ *     (dxx^2 + dyy^2 terms) + M^4 (dxy^2 terms): each term weighted by the
+ *     largest change of the displacement it causes over the subset;
+ *   - bounds: every warped subset point must stay inside [1, W-2) x
+ *     [1, H-2) (a quadratic warp need not reach its extremes at corners). */
+static void basis2(int dx, int dy, double e[6]) {
+  e[0] = 1.0; e[1] = dx; e[2] = dy;
+  e[3] = 0.5 * dx * dx; e[4] = (double)dx * dy; e[5] = 0.5 * dy * dy;
+}
+
+static void warp2_pt(const double p[12], int x0, int y0, int dx, int dy, double *x, double *y) {
+  double e[6];
+  basis2(dx, dy, e);
+  double lx = 0, ly = 0;
+  for (int k = 0; k < 6; ++k) {
+    lx += p[k] * e[k];
+    ly += p[6 + k] * e[k];
+  }
+  *x = x0 + dx + lx;
+  *y = y0 + dy + ly;
+}
+
+static int in_bounds2(const double p[12], int x0, int y0, int M, int W, int H) {
+  for (int dy = -M; dy <= M; ++dy)
+    for (int dx = -M; dx <= M; ++dx) {
+      double x, y;
+      warp2_pt(p, x0, y0, dx, dy, &x, &y);
+      if (!(x >= 1.0 && x < W - 2.0 && y >= 1.0 && y < H - 2.0)) return 0;
+    }
+  return 1;
+}
+
+/* 6x6 representation of the quadratic warp p (rows: xi'^2, xi' eta',
+ * eta'^2, xi', eta', 1 over the columns xi^2, xi eta, eta^2, xi, eta, 1). */
+void dico_warp2_matrix(const double p[12], double Mx[36]) {
+  const double A1 = 0.5 * p[3], A2 = p[4], A3 = 0.5 * p[5], A4 = 1.0 + p[1], A5 = p[2],
+               A6 = p[0];
+  const double B1 = 0.5 * p[9], B2 = p[10], B3 = 0.5 * p[11], B4 = p[7], B5 = 1.0 + p[8],
+               B6 = p[6];
+  const double r[36] = {
+      A4 * A4 + 2 * A1 * A6, 2 * A4 * A5 + 2 * A2 * A6, A5 * A5 + 2 * A3 * A6, 2 * A4 * A6,
+      2 * A5 * A6, A6 * A6,
+      A4 * B4 + A1 * B6 + A6 * B1, A4 * B5 + A5 * B4 + A2 * B6 + A6 * B2,
+      A5 * B5 + A3 * B6 + A6 * B3, A4 * B6 + A6 * B4, A5 * B6 + A6 * B5, A6 * B6,
+      B4 * B4 + 2 * B1 * B6, 2 * B4 * B5 + 2 * B2 * B6, B5 * B5 + 2 * B3 * B6, 2 * B4 * B6,
+      2 * B5 * B6, B6 * B6,
+      A1, A2, A3, A4, A5, A6,
+      B1, B2, B3, B4, B5, B6,
+      0, 0, 0, 0, 0, 1};
+  memcpy(Mx, r, sizeof r);
+}
+
+/* Inverse of a 6x6 matrix by Gauss-Jordan elimination with partial
+ * pivoting; -1 if singular. */
+static int inv6(const double A[36], double X[36]) {
+  double a[6][12];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 12; ++j) a[i][j] = j < 6 ? A[i * 6 + j] : (j - 6 == i ? 1.0 : 0.0);
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < 6; ++i)
+      if (fabs(a[i][c]) > fabs(a[piv][c])) piv = i;
+    if (!(fabs(a[piv][c]) > 0.0)) return -1;
+    if (piv != c)
+      for (int j = 0; j < 12; ++j) {
+        double t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t;
+      }
+    double d = a[c][c];
+    for (int j = 0; j < 12; ++j) a[c][j] /= d;
+    for (int i = 0; i < 6; ++i)
+      if (i != c) {
+        double m = a[i][c];
+        for (int j = 0; j < 12; ++j) a[i][j] -= m * a[c][j];
+      }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) X[i * 6 + j] = a[i][6 + j];
+  return 0;
+}
+
+/* W(p) <- W(p) W(dp)^-1 for quadratic warps (see above); -1 if W(dp)'s
+ * matrix is singular. */
+int dico_compose2(const double p[12], const double dp[12], double out[12]) {
+  double Mp[36], Md[36], Mi[36], P[36];
+  dico_warp2_matrix(p, Mp);
+  dico_warp2_matrix(dp, Md);
+  if (inv6(Md, Mi)) return -1;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double s = 0;
+      for (int k = 0; k < 6; ++k) s += Mp[i * 6 + k] * Mi[k * 6 + j];
+      P[i * 6 + j] = s;
+    }
+  out[3] = 2.0 * P[18]; out[4] = P[19]; out[5] = 2.0 * P[20];
+  out[1] = P[21] - 1.0; out[2] = P[22]; out[0] = P[23];
+  out[9] = 2.0 * P[24]; out[10] = P[25]; out[11] = 2.0 * P[26];
+  out[7] = P[27]; out[8] = P[28] - 1.0; out[6] = P[29];
+  return 0;
+}
+
+static double dp_norm2(const double dp[12], int M) {
+  const double m2 = (double)M * M, q2 = 0.25 * m2 * m2, m4 = m2 * m2;
+  return sqrt(dp[0] * dp[0] + dp[6] * dp[6] +
+              m2 * (dp[1] * dp[1] + dp[2] * dp[2] + dp[7] * dp[7] + dp[8] * dp[8]) +
+              q2 * (dp[3] * dp[3] + dp[5] * dp[5] + dp[9] * dp[9] + dp[11] * dp[11]) +
+              m4 * (dp[4] * dp[4] + dp[10] * dp[10]));
+}
+
+/* Cholesky of a symmetric n x n matrix in place (lower), n <= 12. */
+static int choln(double *A, int n) {
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[j * n + k] * A[j * n + k];
+    if (!(d > 0.0) || !isfinite(d)) return -1;
+    d = sqrt(d);
+    A[j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = s / d;
+    }
+  }
+  return 0;
+}
+static void choln_solve(const double *L, int n, const double *b, double *x) {
+  double y[12];
+  for (int i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+}
+
+/* g at every warped point of a quadratic shape (bicubic), mean and spread. */
+static void sample_subset2(const double *g, int pitch, const double p[12], int x0, int y0,
+                           int M, double *gv, double *gxv, double *gyv, double *gbar,
+                           double *dg) {
+  int S = 2 * M + 1, N = S * S;
+  double s = 0;
+  for (int i = 0; i < N; ++i) {
+    int dx = i % S - M, dy = i / S - M;
+    double x, y;
+    warp2_pt(p, x0, y0, dx, dy, &x, &y);
+    gv[i] = interp(g, pitch, x, y, gxv ? &gxv[i] : NULL, gyv ? &gyv[i] : NULL);
+    s += gv[i];
+  }
+  double m = s / N, q = 0;
+  for (int i = 0; i < N; ++i) q += (gv[i] - m) * (gv[i] - m);
+  *gbar = m;
+  *dg = sqrt(q);
+}
+
+static void subpixel2_one(const double *f, const double *g, int W, int H, int pitch, int x0,
+                          int y0, int M, int method, double tol, int max_iter, int32_t iu0,
+                          int32_t iv0, uint8_t st0, double *pout, double *zncc,
+                          int32_t *iters, uint8_t *status, double *traj) {
+  const int S = 2 * M + 1, N = S * S;
+  double p[12] = {0};
+  p[0] = iu0;
+  p[6] = iv0;
+  memcpy(pout, p, sizeof p);
+  *iters = 0;
+  if (traj) {
+    for (int k = 0; k < (max_iter + 1) * 12; ++k) traj[k] = NAN;
+    memcpy(traj, p, sizeof p);
+  }
+  if (st0 != ST_OK) {
+    *zncc = 0.0;
+    *status = st0;
+    return;
+  }
+  double *fc = malloc(sizeof(double) * N * 6);
+  double *fx = fc + N, *fy = fx + N, *gv = fy + N, *gxv = gv + N, *gyv = gxv + N;
+  double fs = 0;
+  for (int i = 0; i < N; ++i) {
+    int dx = i % S - M, dy = i / S - M;
+    int64_t o = (int64_t)(y0 + dy) * pitch + (x0 + dx);
+    fc[i] = f[o];
+    fx[i] = 0.5 * (f[o + 1] - f[o - 1]);
+    fy[i] = 0.5 * (f[o + pitch] - f[o - pitch]);
+    fs += fc[i];
+  }
+  double fbar = fs / N, q = 0;
+  for (int i = 0; i < N; ++i) {
+    fc[i] -= fbar;
+    q += fc[i] * fc[i];
+  }
+  const double df = sqrt(q);
+  uint8_t st = ST_MAX_ITER;
+  int it_done = 0;
+  double Hm[144];
+  if (df == 0.0) {
+    st = ST_ZERO_VAR_REF;
+    goto final2;
+  }
+  if (method == 0) {
+    memset(Hm, 0, sizeof Hm);
+    for (int i = 0; i < N; ++i) {
+      double e[6], sd[12];
+      basis2(i % S - M, i / S - M, e);
+      for (int k = 0; k < 6; ++k) { sd[k] = fx[i] * e[k]; sd[6 + k] = fy[i] * e[k]; }
+      for (int a = 0; a < 12; ++a)
+        for (int b = 0; b < 12; ++b) Hm[a * 12 + b] += sd[a] * sd[b];
+    }
+    if (choln(Hm, 12)) {
+      st = ST_SINGULAR;
+      goto final2;
+    }
+  }
+  for (int it = 1; it <= max_iter; ++it) {
+    double gbar, dg;
+    sample_subset2(g, pitch, p, x0, y0, M, gv, method ? gxv : NULL, method ? gyv : NULL, &gbar,
+                   &dg);
+    if (!(dg > 0.0) || !isfinite(dg)) {
+      st = ST_NONFINITE;
+      break;
+    }
+    double b[12] = {0}, dp[12];
+    if (method == 0) {
+      for (int i = 0; i < N; ++i) {
+        double e[6];
+        basis2(i % S - M, i / S - M, e);
+        double r = fc[i] - (df / dg) * (gv[i] - gbar);
+        for (int k = 0; k < 6; ++k) {
+          b[k] += fx[i] * e[k] * r;
+          b[6 + k] += fy[i] * e[k] * r;
+        }
+      }
+      choln_solve(Hm, 12, b, dp);
+      for (int a = 0; a < 12; ++a) dp[a] = -dp[a];
+    } else {
+      memset(Hm, 0, sizeof Hm);
+      for (int i = 0; i < N; ++i) {
+        double e[6], J[12];
+        basis2(i % S - M, i / S - M, e);
+        for (int k = 0; k < 6; ++k) { J[k] = gxv[i] * e[k]; J[6 + k] = gyv[i] * e[k]; }
+        double r = (dg / df) * fc[i] - (gv[i] - gbar);
+        for (int a = 0; a < 12; ++a) {
+          b[a] += J[a] * r;
+          for (int c = 0; c < 12; ++c) Hm[a * 12 + c] += J[a] * J[c];
+        }
+      }
+      it_done = it;
+      if (choln(Hm, 12)) {
+        st = ST_SINGULAR;
+        break;
+      }
+      choln_solve(Hm, 12, b, dp);
+    }
+    it_done = it;
+    int fin = 1;
+    for (int a = 0; a < 12; ++a) fin &= isfinite(dp[a]);
+    if (!fin) {
+      st = ST_NONFINITE;
+      break;
+    }
+    double pn[12];
+    if (method == 0) {
+      if (dico_compose2(p, dp, pn)) {
+        st = ST_NONFINITE;
+        break;
+      }
+    } else {
+      for (int a = 0; a < 12; ++a) pn[a] = p[a] + dp[a];
+    }
+    if (!in_bounds2(pn, x0, y0, M, W, H)) {
+      st = ST_OUT_OF_BOUNDS;
+      break;
+    }
+    memcpy(p, pn, sizeof p);
+    if (traj) memcpy(traj + it * 12, p, sizeof p);
+    if (dp_norm2(dp, M) < tol) {
+      st = ST_OK;
+      break;
+    }
+  }
+final2:
+  memcpy(pout, p, sizeof p);
+  *iters = it_done;
+  *status = st;
+  if (st == ST_ZERO_VAR_REF) {
+    *zncc = 0.0;
+  } else {
+    double gbar, dg;
+    sample_subset2(g, pitch, p, x0, y0, M, gv, NULL, NULL, &gbar, &dg);
+    double s2 = 0;
+    for (int i = 0; i < N; ++i) s2 += fc[i] * (gv[i] - gbar);
+    *zncc = (dg > 0.0) ? s2 / (df * dg) : 0.0;
+  }
+  free(fc);
+}
+
+int dico_subpixel2(const double *f, const double *g, int W, int H, int pitch, int subset,
+                   int step, int R, int method, double tol, int max_iter,
+                   const int64_t *poi_idx, int64_t n_idx, const int32_t *u0, const int32_t *v0,
+                   const uint8_t *st0, int nthreads, double *p_out, double *zncc,
+                   int32_t *iters, uint8_t *status, double *traj) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  if (method != 0 && method != 1) return -1;
+  if (max_iter < 1) return -1;
+  const int M = subset / 2;
+  const int64_t n = poi_idx ? n_idx : (int64_t)nx * ny;
+  if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads)
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t poi = poi_idx ? poi_idx[k] : k;
+    int x0, y0;
+    poi_centre(poi, nx, M, R, step, &x0, &y0);
+    subpixel2_one(f, g, W, H, pitch, x0, y0, M, method, tol, max_iter, u0[k], v0[k], st0[k],
+                  &p_out[k * 12], &zncc[k], &iters[k], &status[k],
+                  traj ? &traj[k * (int64_t)(max_iter + 1) * 12] : NULL);
   }
   return 0;
 }

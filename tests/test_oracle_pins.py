@@ -646,3 +646,128 @@ def test_zncc_at_non_integer_shape_written_out(interp):
     a, b = np.array(a) - np.mean(a), np.array(b) - np.mean(b)
     lit = (a * b).sum() / math.sqrt((a * a).sum() * (b * b).sum())
     assert abs(c - lit) < 1e-12
+
+
+# --------------------------------------------- second-order shape function
+def test_warp2_matrix_rows_are_the_warped_monomials_to_second_order():
+    """Rows 4-6 of the 6x6 representation give xi', eta', 1 exactly; rows
+    1-3 give xi'^2, xi' eta', eta'^2 up to terms of third and higher order
+    (the difference shrinks eightfold when (xi, eta) halves)."""
+    # every coefficient well away from zero, so each product term of the
+    # matrix matters
+    p = np.array([1.3, 0.04, -0.03, 0.02, -0.015, 0.01, -0.9, 0.025, 0.035, -0.012, 0.018,
+                  0.02])
+    Mx = oracle.warp2_matrix(p)
+
+    def exact(xi, eta):
+        e = np.array([1, xi, eta, 0.5 * xi * xi, xi * eta, 0.5 * eta * eta])
+        xs = xi + p[:6] @ e
+        ys = eta + p[6:] @ e
+        return np.array([xs * xs, xs * ys, ys * ys, xs, ys, 1.0])
+
+    def lifted(xi, eta):
+        return Mx @ np.array([xi * xi, xi * eta, eta * eta, xi, eta, 1.0])
+
+    for a, b in ((0.07, -0.04), (-0.03, 0.09)):
+        d1 = exact(a, b) - lifted(a, b)
+        d2 = exact(a / 2, b / 2) - lifted(a / 2, b / 2)
+        assert np.abs(d1[3:]).max() < 1e-13 and np.abs(d2[3:]).max() < 1e-13
+        # rows 1-3: the dropped terms are cubic (and quartic) in (xi, eta),
+        # so near the origin the remainder shrinks eightfold when (xi, eta)
+        # halves; a missing or wrong second-order term would shrink it
+        # only fourfold
+        ratio = np.abs(d2[:3]) / np.abs(d1[:3])
+        assert ((ratio > 0.11) & (ratio < 0.14)).all(), ratio
+
+
+def test_compose2_identity_and_first_order_case():
+    """W(p) W(0)^-1 = W(p); for first-order p and dp the update is the 3x3
+    affine composition P D^-1 (written out here)."""
+    rng = np.random.default_rng(8)
+    p = rng.normal(0, [1, 0.02, 0.02, 0.001, 0.001, 0.001, 1, 0.02, 0.02, 0.001, 0.001, 0.001])
+    assert np.abs(oracle.compose2(p, np.zeros(12)) - p).max() < 1e-14
+    p1 = np.zeros(12)
+    d1 = np.zeros(12)
+    p1[[0, 1, 2, 6, 7, 8]] = [2.3, 0.01, -0.02, -1.1, 0.015, 0.004]
+    d1[[0, 1, 2, 6, 7, 8]] = [0.05, 0.001, 0.002, -0.03, -0.0015, 0.001]
+
+    def aff(q):
+        return np.array([[1 + q[1], q[2], q[0]], [q[7], 1 + q[8], q[6]], [0, 0, 1]])
+    want = aff(p1) @ np.linalg.inv(aff(d1))
+    got = oracle.compose2(p1, d1)
+    assert np.abs(got[[3, 4, 5, 9, 10, 11]]).max() < 1e-15
+    np.testing.assert_allclose([got[1] + 1, got[2], got[0], got[7], got[8] + 1, got[6]],
+                               [want[0, 0], want[0, 1], want[0, 2], want[1, 0], want[1, 1],
+                                want[1, 2]], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_subpixel2_integer_shift_fixed_point(method):
+    big, _ = configs.tiny(21, 120, 120, 500)
+    f = np.ascontiguousarray(big[10:110, 10:110])
+    g = np.ascontiguousarray(big[10 - 2:110 - 2, 10 - 3:110 - 3])  # shift (3, 2)
+    s = oracle.integer_search(f, g, 21, 10, 6)
+    u0 = s["u0"] - 1
+    v0 = s["v0"] + 1
+    r = oracle.subpixel2(f, g, 21, 10, 6, u0, v0, s["status"], method=method, tol=1e-10)
+    ok = r["status"] == 0
+    assert ok.mean() > 0.9
+    want = np.zeros(12)
+    want[0], want[6] = 3, 2
+    assert np.abs(r["p"][ok] - want).max() < 1e-8
+    assert np.abs(r["zncc"][ok] - 1).max() < 1e-12
+
+
+def _quadratic_pair(noise=0.0):
+    from workloads.speckle import Quadratic, render_pair
+    d = Quadratic(cu=(1.6, 0.004, -0.003, 8e-4, -5e-4, 6e-4),
+                  cv=(-0.9, 0.002, 0.005, -6e-4, 7e-4, 5e-4), cx=127.5, cy=127.5)
+    f, g = render_pair(411, 256, 256, 3200, d, noise, pad=30.0)
+    return f, g, d
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_subpixel2_recovers_an_imposed_quadratic_field(method):
+    """Noise-free speckles under a quadratic field: the second-order shape
+    recovers u, v and all ten derivatives at every POI (the first-order
+    shape cannot follow the curvature and misses it)."""
+    f, g, d = _quadratic_pair()
+    subset, step, r = 31, 16, 12
+    s = oracle.integer_search(f, g, subset, step, r)
+    res = oracle.subpixel2(f, g, subset, step, r, s["u0"], s["v0"], s["status"], method=method)
+    nx = s["nx"]
+    b = subset // 2 + r + 2
+    k = np.arange(len(s["u0"]))
+    x0 = (b + (k % nx) * step).astype(float)
+    y0 = (b + (k // nx) * step).astype(float)
+    truth = np.stack(d.displacement2(x0, y0), 1)
+    ok = res["status"] == 0
+    assert ok.mean() > 0.95
+    e = np.abs(res["p"] - truth)[ok]
+    assert e[:, [0, 6]].max() < 0.02 and e[:, [0, 6]].mean() < 0.005
+    assert e[:, [1, 2, 7, 8]].mean() < 5e-4
+    assert e[:, [3, 4, 5, 9, 10, 11]].mean() < 1e-4
+    first = oracle.subpixel(f, g, subset, step, r, s["u0"], s["v0"], s["status"], method=method)
+    e1 = np.abs(first["p"] - truth[:, [0, 1, 2, 6, 7, 8]])[first["status"] == 0]
+    assert e[:, [1, 2, 7, 8]].mean() < 0.5 * e1[:, [1, 2, 4, 5]].mean()
+
+
+@pytest.mark.parametrize("method", [oracle.ICGN, oracle.FANR])
+def test_subpixel2_on_an_affine_field(affine1024, method):
+    """Where the field is affine (noise sigma 2) the second-order terms come
+    out near zero and u, v stay within the paper's usual 0.05 px of the
+    imposed field, as the first-order refinement's do."""
+    p = affine1024
+    idx = np.arange(0, 36100, 97)
+    s = oracle.integer_search(p.ref, p.defm, p.subset, p.step, p.radius, poi_idx=idx)
+    r2 = oracle.subpixel2(p.ref, p.defm, p.subset, p.step, p.radius, s["u0"], s["v0"],
+                          s["status"], method=method, poi_idx=idx)
+    ok = r2["status"] == 0
+    assert ok.mean() > 0.98
+    b = p.subset // 2 + p.radius + 2
+    x0 = (b + (idx % 190) * p.step).astype(float)
+    y0 = (b + (idx // 190) * p.step).astype(float)
+    gt = np.stack(p.deformation.displacement(x0, y0), 1)
+    assert np.abs(r2["p"][ok][:, [0, 6]] - gt[ok][:, [0, 3]]).max() < 0.05
+    assert np.abs(r2["p"][ok][:, [1, 2, 7, 8]] - gt[ok][:, [1, 2, 4, 5]]).mean() < 2e-3
+    assert np.abs(r2["p"][ok][:, [3, 4, 5, 9, 10, 11]]).mean() < 5e-4

@@ -138,6 +138,47 @@ class Sinusoidal:
 
 
 @dataclass
+class Quadratic:
+    """x' = x + u, y' = y + v with u, v quadratic in (X, Y) = (x - cx, y - cy):
+    u = cu[0] + cu[1] X + cu[2] Y + cu[3] X^2/2 + cu[4] X Y + cu[5] Y^2/2
+    (v likewise with cv), the field a second-order subset shape reproduces."""
+    cu: tuple
+    cv: tuple
+    cx: float
+    cy: float
+
+    @staticmethod
+    def _q(c, X, Y):
+        return c[0] + c[1] * X + c[2] * Y + 0.5 * c[3] * X * X + c[4] * X * Y + 0.5 * c[5] * Y * Y
+
+    def forward(self, x, y):
+        X, Y = x - self.cx, y - self.cy
+        return x + self._q(self.cu, X, Y), y + self._q(self.cv, X, Y)
+
+    def inverse(self, xp, yp, iters: int = 60):
+        # fixed point x = x' - u(x); the map's Jacobian stays well below 1 on
+        # the images it is used for
+        x, y = xp, yp
+        for _ in range(iters):
+            X, Y = x - self.cx, y - self.cy
+            x = xp - self._q(self.cu, X, Y)
+            y = yp - self._q(self.cv, X, Y)
+        return x, y
+
+    def displacement2(self, x, y):
+        """The 12 second-order shape parameters at reference points (x, y):
+        (u, ux, uy, uxx, uxy, uyy, v, vx, vy, vxx, vxy, vyy)."""
+        x = np.asarray(x, np.float64)
+        y = np.asarray(y, np.float64)
+        X, Y = x - self.cx, y - self.cy
+        out = []
+        for c in (self.cu, self.cv):
+            out += [self._q(c, X, Y), c[1] + c[3] * X + c[4] * Y, c[2] + c[4] * X + c[5] * Y,
+                    c[3] + 0 * X, c[4] + 0 * X, c[5] + 0 * X]
+        return tuple(out)
+
+
+@dataclass
 class SpeckleSet:
     cx: np.ndarray
     cy: np.ndarray
