@@ -319,6 +319,41 @@ def run_gpu(args):
     bil_sub_ms = statistics.mean(seb[1])
     dbl.close()
 
+    # the second-order (12-parameter) shape function, IC-GN, same search and
+    # solve precision, same rules
+    h2 = dic.dic_create(SUBSET, STEP, RADIUS, 2, TOL, MAX_ITER)
+    dic.dic_set_solve_precision(h2, args.solve_bits)
+    if args.form == "tc":
+        dic.dic_set_form(h2, dic.DIC_FORM_BF16TC)
+    dic.dic_set_stream(h2, stream)
+    p12 = torch.empty((n, 12), dtype=torch.float32, device=dev)
+    o2 = {k: torch.empty(n, dtype=dt, device=dev) for k, dt in
+          (("zncc", torch.float32), ("iters", torch.int32), ("status", torch.uint8))}
+
+    def step2():
+        dic.dic_set_pair(h2, ref_d, def_d)
+        dic.dic_integer_search(h2, s_out["u0"], s_out["v0"], s_out["zncc0"], s_out["status0"])
+        dic.dic_subpixel2(h2, dic.DIC_ICGN, s_out["u0"], s_out["v0"], s_out["status0"], p12,
+                          o2["zncc"], o2["iters"], o2["status"])
+    k2 = max(5, args.steps // 4)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            flush.zero_()
+            step2()
+        ev2 = [(ev(), ev()) for _ in range(k2)]
+        for a_, b_ in ev2:
+            flush.zero_()
+            a_.record(stream)
+            step2()
+            b_.record(stream)
+    torch.cuda.synchronize(dev)
+    ms2 = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev2)
+    conv2 = int((o2["status"] == 0).sum().item())
+    second_order = {"shape": "second order (12 parameters)", "method": "IC-GN",
+                    "solve": f"fp{args.solve_bits}", "ms_per_step": ms2,
+                    "value": conv2 / (ms2 / 1e3), "converged_fraction": conv2 / n}
+    dic.dic_destroy(h2)
+
     # the particle swarm integer searches (Section 2.1, Eqs. 2-4; the modified
     # swarm with the star search) timed beside the dense search on the same
     # pair, with their agreement with its exact argmax
@@ -518,7 +553,8 @@ def run_gpu(args):
                                               "value": bil_value, "subpixel_ms": bil_sub_ms},
                           "plain_fp32": {"search": "fp32-exact", "solve": "fp32",
                                          "value": plain_value},
-                          "swarm_searches": pso},
+                          "swarm_searches": pso,
+                          "second_order_shape": second_order},
                 "converged_fraction": conv / n, "wall_s_timed": wall,
                 "sub_records": sub_records}
         print(json.dumps(line))

@@ -93,8 +93,10 @@ int dic_version(void);
  *   grid_step      POI spacing in pixels, >= 1
  *   search_radius  R >= 0: offsets [-R, R]^2 are searched (Section 2.1 uses a
  *                  fixed window around the reference position)
- *   shape_order    1 = first-order 6-parameter warp (the only order built;
- *                  anything else returns DIC_ERR_UNSUPPORTED)
+ *   shape_order    1 = first-order 6-parameter warp (dic_subpixel), or
+ *                  2 = second-order 12-parameter warp (dic_subpixel2, an
+ *                  extension: the paper's refinement is first-order);
+ *                  anything else returns DIC_ERR_UNSUPPORTED
  *   conv_tol       stop when |dp| < conv_tol, with
  *                  |dp| = sqrt(du^2 + dv^2 + M^2 (dux^2+duy^2+dvx^2+dvy^2))
  *   max_iter       maximum Gauss-Newton solves per POI, >= 1
@@ -230,6 +232,29 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t *u0, const int
                         const uint8_t *status0, float *u, float *v, float *ux, float *uy,
                         float *vx, float *vy, float *zncc, int32_t *iters,
                         uint8_t *status);
+
+/* Sub-pixel refinement with the second-order subset shape function
+ * (handles created with shape_order 2; an extension of Section 2.2's
+ * first-order warp):
+ *   p = (u, ux, uy, uxx, uxy, uyy, v, vx, vy, vxx, vxy, vyy), point (dx, dy)
+ *   -> (x0 + dx + p[0..5] . e, y0 + dy + p[6..11] . e),
+ *   e = (1, dx, dy, dx^2/2, dx dy, dy^2/2).
+ * IC-GN: SD = [fx e, fy e], H = sum SD^T SD (12 x 12, inverted once per POI
+ * in the handle's solve precision), dp = -H^-1 sum SD r, and
+ * W(p) <- W(p) W(dp)^-1 composed in the 6 x 6 representation of a
+ * quadratic warp acting on (dx^2, dx dy, dy^2, dx, dy, 1), terms above
+ * second order dropped.  Stop when |dp| < conv_tol with
+ * |dp|^2 = du^2 + dv^2 + M^2 (first derivatives)^2 + (M^2/2)^2 (uxx, uyy,
+ * vxx, vyy)^2 + M^4 (uxy, vxy)^2; an update that moves any warped subset
+ * point outside [1, W-2) x [1, H-2) is rejected (DIC_POI_OUT_OF_BOUNDS).
+ *   p12  device [n_pois][12], row-major, in the order above
+ * Other arguments and outputs as dic_subpixel.  DIC_ERR_STATE for a handle of
+ * shape order 1 or without a pair; DIC_ERR_UNSUPPORTED for DIC_FANR or
+ * bilinear interpolation (the device path is IC-GN over bicubic
+ * interpolation); DIC_ERR_ARG for a null pointer. */
+dic_status dic_subpixel2(dic_t h, dic_method method, const int32_t *u0, const int32_t *v0,
+                         const uint8_t *status0, float *p12, float *zncc, int32_t *iters,
+                         uint8_t *status);
 
 /* ---------------------------------------------------------------- batches
  * Many image pairs of uneven size in one go -- the GPU form of the paper's

@@ -77,6 +77,8 @@ def _load():
             lib.dico_subpixel2.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, dbl, i32,
                                            P, i64, P, P, P, i32, P, P, P, P, P]
             lib.dico_subpixel2.restype = i32
+            lib.dico_zncc_at2.argtypes = [P, P, i32, i32, i32, i32, i32, i32, P, i64, P, i32, P]
+            lib.dico_zncc_at2.restype = i32
             lib.dico_compose2.argtypes = [P, P, P]
             lib.dico_compose2.restype = i32
             lib.dico_warp2_matrix.argtypes = [P, P]
@@ -204,6 +206,26 @@ def subpixel2(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int,
     out.update({k: p[:, j] for j, k in enumerate(NAMES2)})
     if trajectory:
         out["traj"] = traj
+    return out
+
+
+def zncc_at2(f: np.ndarray, g: np.ndarray, subset: int, step: int, radius: int, p: np.ndarray,
+             poi_idx=None, threads: int | None = None) -> np.ndarray:
+    """Eq. 1 at second-order shapes p (n x 12), bicubic; NaN where the warped
+    subset leaves the image or a subset is flat."""
+    f = np.ascontiguousarray(f, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    H, W = f.shape
+    idx, n = _idx(poi_idx)
+    if idx is None:
+        nx, ny = grid(W, H, subset, step, radius)
+        n = nx * ny
+    p = np.ascontiguousarray(p, np.float64).reshape(n, 12)
+    out = np.zeros(n, np.float64)
+    if _load().dico_zncc_at2(_ptr(f), _ptr(g), W, H, W, subset, step, radius, _ptr(idx),
+                             n if idx is not None else -1, _ptr(p), threads or default_threads(),
+                             _ptr(out)):
+        raise ValueError("oracle zncc_at2 failed")
     return out
 
 

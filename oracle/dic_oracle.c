@@ -838,6 +838,51 @@ final2:
   free(fc);
 }
 
+/* Eq. 1 at given second-order shapes p[k][12] (bicubic); NAN where a warped
+ * point leaves [1, W-2) x [1, H-2) or a subset is flat. */
+int dico_zncc_at2(const double *f, const double *g, int W, int H, int pitch, int subset,
+                  int step, int R, const int64_t *poi_idx, int64_t n_idx, const double *p,
+                  int nthreads, double *zncc) {
+  int nx, ny;
+  if (dico_grid(W, H, subset, step, R, &nx, &ny)) return -1;
+  const int M = subset / 2, S = subset, N = S * S;
+  const int64_t n = poi_idx ? n_idx : (int64_t)nx * ny;
+  if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel num_threads(nthreads)
+  {
+    double *fc = malloc(sizeof(double) * N * 2);
+    double *gv = fc + N;
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n; ++k) {
+      int64_t poi = poi_idx ? poi_idx[k] : k;
+      int x0, y0;
+      poi_centre(poi, nx, M, R, step, &x0, &y0);
+      const double *pk = &p[k * 12];
+      zncc[k] = NAN;
+      if (!in_bounds2(pk, x0, y0, M, W, H)) continue;
+      double fs = 0;
+      for (int i = 0; i < N; ++i) {
+        int dx = i % S - M, dy = i / S - M;
+        fc[i] = f[(int64_t)(y0 + dy) * pitch + (x0 + dx)];
+        fs += fc[i];
+      }
+      double fbar = fs / N, q = 0;
+      for (int i = 0; i < N; ++i) {
+        fc[i] -= fbar;
+        q += fc[i] * fc[i];
+      }
+      double df = sqrt(q), gbar, dg;
+      sample_subset2(g, pitch, pk, x0, y0, M, gv, NULL, NULL, &gbar, &dg);
+      if (!(df > 0.0) || !(dg > 0.0)) continue;
+      double c = 0;
+      for (int i = 0; i < N; ++i) c += fc[i] * (gv[i] - gbar);
+      zncc[k] = c / (df * dg);
+    }
+    free(fc);
+  }
+  return 0;
+}
+
 int dico_subpixel2(const double *f, const double *g, int W, int H, int pitch, int subset,
                    int step, int R, int method, double tol, int max_iter,
                    const int64_t *poi_idx, int64_t n_idx, const int32_t *u0, const int32_t *v0,

@@ -78,6 +78,7 @@ SIGNATURES = {
     "dic_pso_search": (i32, [P, i32, i32, i32, C.c_double, C.c_double, C.c_double, i32, i32,
                              P, P, P, P, P, P, P]),
     "dic_subpixel": (i32, [P, i32, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "dic_subpixel2": (i32, [P, i32, P, P, P, P, P, P, P]),
     "dic_measure_peak": (i32, [i32, P, C.POINTER(C.c_double)]),
     "dic_subpixel_noalloc": (i32, [P, P, i32, i32, i32, i32, i32, i32, i32, f32, i32, i32,
                                    P, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -279,6 +280,13 @@ def dic_num_pois(h) -> tuple[int, int, int]:
 
 def dic_integer_search(h, u0, v0, zncc0, status) -> None:
     _check(lib().dic_integer_search(h, _ptr(u0), _ptr(v0), _ptr(zncc0), _ptr(status)), h)
+
+
+def dic_subpixel2(h, method, u0, v0, status0, p12, zncc, iters, status) -> None:
+    """Second-order refinement (handle of shape order 2); p12 is a float32
+    device tensor (n_pois, 12)."""
+    _check(lib().dic_subpixel2(h, method, _ptr(u0), _ptr(v0), _ptr(status0), _ptr(p12),
+                               _ptr(zncc), _ptr(iters), _ptr(status)), h)
 
 
 def dic_pso_search(h, uniforms, u0, v0, zncc0, status, gens, evals, modified: bool = False,

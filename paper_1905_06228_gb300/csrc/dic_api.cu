@@ -125,7 +125,7 @@ dic_status dic_create(dic_t* out, int subset_size, int grid_step, int search_rad
       grid_step < 1 || search_radius < 0 || search_radius > 1000 || !(conv_tol > 0.f) ||
       max_iter < 1)
     return DIC_ERR_ARG;
-  if (shape_order != 1) return DIC_ERR_UNSUPPORTED;
+  if (shape_order != 1 && shape_order != 2) return DIC_ERR_UNSUPPORTED;
   dic_t h = new (std::nothrow) dic_s;
   if (!h) return DIC_ERR_OOM;
   h->subset = subset_size;
@@ -654,11 +654,56 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
 
 
 
+dic_status dic_subpixel2(dic_t h, dic_method method, const int32_t* u0, const int32_t* v0,
+                         const uint8_t* status0, float* p12, float* zncc, int32_t* iters,
+                         uint8_t* status) {
+  if (!h) return DIC_ERR_ARG;
+  if (method != DIC_ICGN && method != DIC_FANR) return fail(h, DIC_ERR_ARG, "unknown method");
+  if (h->shape_order != 2)
+    return fail(h, DIC_ERR_STATE, "second-order refinement needs a handle of shape order 2");
+  if (method != DIC_ICGN)
+    return fail(h, DIC_ERR_UNSUPPORTED, "second-order shape: IC-GN only on the device");
+  if (h->interp != DIC_INTERP_BICUBIC)
+    return fail(h, DIC_ERR_UNSUPPORTED, "second-order shape: bicubic interpolation only");
+  if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
+  if (h->g.n_pois == 0) return DIC_OK;
+  if (!u0 || !v0 || !status0 || !p12 || !zncc || !iters || !status)
+    return fail(h, DIC_ERR_ARG, "null pointer");
+  dic::SubpixelParams p;
+  p.ref = h->ref;
+  p.ref_f32 = h->ref_f32;
+  p.grad = h->grad;
+  p.gimg = h->gimg;
+  p.gq = h->ref ? h->gq : nullptr;
+  p.W = h->g.W;
+  p.H = h->g.H;
+  p.pitch = h->g.pitch;
+  p.S = h->subset;
+  p.M = h->M;
+  p.R = h->R;
+  p.step = h->step;
+  p.nx = h->g.nx;
+  p.n_pois = h->g.n_pois;
+  p.max_iter = h->max_iter;
+  p.tol = h->tol;
+  p.u0 = u0;
+  p.v0 = v0;
+  p.st0 = status0;
+  p.zncc = zncc;
+  p.iters = iters;
+  p.status = status;
+  cudaError_t e = dic::launch_subpixel2(p, h->solve_bits == 64, p12, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "second-order subpixel launch");
+  return DIC_OK;
+}
+
 dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int32_t* v0,
                         const uint8_t* status0, float* u, float* v, float* ux, float* uy,
                         float* vx, float* vy, float* zncc, int32_t* iters, uint8_t* status) {
   if (!h) return DIC_ERR_ARG;
   if (method != DIC_ICGN && method != DIC_FANR) return fail(h, DIC_ERR_ARG, "unknown method");
+  if (h->shape_order != 1)
+    return fail(h, DIC_ERR_STATE, "a handle of shape order 2 refines with dic_subpixel2");
   if (!h->have_pair) return fail(h, DIC_ERR_STATE, "no image pair set");
   if (h->g.n_pois == 0) return DIC_OK;
   if (!u0 || !v0 || !status0 || !u || !v || !ux || !uy || !vx || !vy || !zncc || !iters ||

@@ -14,6 +14,22 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sum over the warp of 32 values per lane, scattered: lane l returns the
+// sum of every lane's v[l] (five halving exchanges, 31 shuffles in all).
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool up = lane & h;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = up ? v[k] : v[k + h];
+      const float keep = up ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  return v[0];
+}
+
 // Keys (a = -1/2) weights of the taps -1, 0, 1, 2 at fractional offset t.
 __device__ __forceinline__ void keys_weights(float t, float w[4]) {
   const float t2 = t * t, t3 = t2 * t;

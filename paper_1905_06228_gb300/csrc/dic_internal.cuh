@@ -188,6 +188,9 @@ cudaError_t launch_subpixel_batch(const SubpixelParams* jobs, const int64_t* off
                                   unsigned long long* counter, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchParams& p, const CUtensorMap* tm_ref,
                           const CUtensorMap* tm_def, cudaStream_t st);
+// IC-GN with the second-order shape function; p12 receives [n_pois][12]
+cudaError_t launch_subpixel2(const SubpixelParams& p, int solve_fp64, float* p12,
+                             cudaStream_t st);
 // bilinear: 1 for the bilinear interpolation of Eq. 5, 0 for bicubic (Keys)
 cudaError_t launch_subpixel(const SubpixelParams& p, int method, int solve_fp64,
                             cudaStream_t st, int bilinear = 0);

@@ -130,22 +130,6 @@ __device__ __forceinline__ bool sweep_inverse6(float h, int i, int j, T& out) {
   return ok;
 }
 
-// Sum over the warp of 32 values per lane, scattered: lane l returns the
-// sum of every lane's v[l] (five halving exchanges, 31 shuffles in all).
-__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool up = lane & h;
-#pragma unroll
-    for (int k = 0; k < h; ++k) {
-      const float send = up ? v[k] : v[k + h];
-      const float keep = up ? v[k + h] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, h);
-    }
-  }
-  return v[0];
-}
-
 // H^-1 into shared memory (36 solve-precision values, row-major) from the 21
 // entries of a symmetric positive definite H held one per lane (lane l < 21:
 // packed entry l, see packed_entry): H is first scaled symmetrically to a

@@ -204,3 +204,103 @@ def compare_subpixel(gpu: dict, f, g, subset, step, radius, start: dict, method:
               max_err_zncc_converged=zerr_conv, max_err_zncc_other=zerr_other)
     print("parity", st)
     return st
+
+
+# ------------------------------------------------ second-order shape function
+NAMES2 = ("u", "ux", "uy", "uxx", "uxy", "uyy", "v", "vx", "vy", "vxx", "vxy", "vyy")
+
+
+def run_gpu2(f, g, subset, step, radius, solve_bits=64, form=1, device="cuda:0"):
+    """Integer search and second-order IC-GN through the C ABI."""
+    import torch
+
+    import paper_1905_06228_gb300 as dic
+    tf = torch.from_numpy(np.ascontiguousarray(f)).to(device)
+    tg = torch.from_numpy(np.ascontiguousarray(g)).to(device)
+    h = dic.dic_create(subset, step, radius, 2)
+    try:
+        dic.dic_set_solve_precision(h, solve_bits)
+        dic.dic_set_form(h, form)
+        dic.dic_set_pair(h, tf, tg)
+        n, nx, ny = dic.dic_num_pois(h)
+        t = lambda dt: torch.empty(n, dtype=dt, device=device)
+        u0, v0, z0, s0 = t(torch.int32), t(torch.int32), t(torch.float32), t(torch.uint8)
+        dic.dic_integer_search(h, u0, v0, z0, s0)
+        p12 = torch.empty((n, 12), dtype=torch.float32, device=device)
+        zn, it, st = t(torch.float32), t(torch.int32), t(torch.uint8)
+        dic.dic_subpixel2(h, 0, u0, v0, s0, p12, zn, it, st)
+        torch.cuda.synchronize()
+        out = dict(n=n, nx=nx, ny=ny, u0=u0, v0=v0, zncc0=z0, status0=s0, p=p12, zncc=zn,
+                   iters=it, status=st)
+        return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+    finally:
+        dic.dic_destroy(h)
+
+
+def compare_subpixel2(gpu, f, g, subset, step, radius, start, tol=1e-3, max_iter=50,
+                      idx=None, min_compared=0.99, label="") -> dict:
+    """Second-order IC-GN against the oracle under the rules of
+    compare_subpixel (statuses exact, shapes at the GPU's iteration count,
+    converged POIs all inside the tolerance, ZNCC at the sampled iterate);
+    idx selects grid POIs (start holds the oracle's search at those POIs).
+    Tolerances: u, v 1e-3 px; first derivatives 1e-5; second derivatives
+    2e-5 / M -- the same displacement at the subset edge (M px from the
+    centre, where a second-derivative term moves a point by up to M^2 times
+    it) as the first-derivative tolerance."""
+    sel = np.arange(len(gpu["iters"])) if idx is None else np.asarray(idx)
+    ref = oracle.subpixel2(f, g, subset, step, radius, start["u0"], start["v0"],
+                           start["status"], tol=tol, max_iter=max_iter, poi_idx=idx,
+                           trajectory=True)
+    M = subset // 2
+    tol2 = 2 * TOL_GRAD / M
+    gp, git, gst = gpu["p"][sel].astype(np.float64), gpu["iters"][sel], gpu["status"][sel]
+    rit, rst = ref["iters"], ref["status"]
+    n = len(gst)
+    swap = (gst != rst) & np.isin(gst, (0, 3)) & np.isin(rst, (0, 3))
+    assert swap.sum() <= 0.001 * n, (label, "OK/MAX_ITER swaps", int(swap.sum()))
+    np.testing.assert_array_equal(gst[~swap], rst[~swap], err_msg=label + " statuses")
+    assert (git != rit).sum() <= max(1, int(0.01 * n)), (label, "iteration agreement")
+
+    def iterate(k):
+        out = np.full((n, 12), np.nan)
+        have = k <= rit
+        rows = np.nonzero(have)[0]
+        out[rows] = ref["traj"][rows, k[rows]]
+        rej = rows[np.isnan(out[rows]).any(1) & (k[rows] >= 1)]
+        out[rej] = ref["traj"][rej, k[rej] - 1]
+        for kk in np.unique(k[~have]):
+            rows = np.nonzero(~have & (k == kk))[0]
+            sub = oracle.subpixel2(f, g, subset, step, radius, start["u0"][rows],
+                                   start["v0"][rows], start["status"][rows], tol=1e-300,
+                                   max_iter=int(kk), poi_idx=sel[rows])
+            out[rows] = sub["p"]
+        return out
+
+    want = iterate(git)
+    err = np.abs(gp - want)
+    e_uv = err[:, [0, 6]].max(1)
+    e_g1 = err[:, [1, 2, 7, 8]].max(1)
+    e_g2 = err[:, [3, 4, 5, 9, 10, 11]].max(1)
+    over = ~(e_uv < TOL_UV) | ~(e_g1 < TOL_GRAD) | ~(e_g2 < tol2)
+    ran = git >= 1
+    conv = ran & (gst == 0)
+    bad = np.nonzero(conv & over)[0]
+    assert len(bad) == 0, dict(label=label, poi=bad[:5], gpu=gp[bad[:3]], want=want[bad[:3]],
+                               e=(e_uv[bad[:5]], e_g1[bad[:5]], e_g2[bad[:5]]))
+    wander = ran & (gst != 0)
+    n_w = int((wander & over).sum())
+    assert int(ran.sum()) - n_w >= min_compared * ran.sum(), (label, "compared")
+    zc = np.nonzero(conv)[0]
+    zerr = 0.0
+    if len(zc):
+        before = iterate(np.where(conv, git - 1, 0))[zc]
+        c = oracle.zncc_at2(f, g, subset, step, radius, before, poi_idx=sel[zc])
+        zerr = float(np.abs(gpu["zncc"][sel][zc] - c).max())
+        assert zerr < TOL_ZNCC, (label, "zncc", zerr)
+    st = dict(label=label, n=n, converged=int(conv.sum()), wandering_outside_tol=n_w,
+              max_err_uv=float(e_uv[ran].max(initial=0)),
+              max_err_grad=float(e_g1[ran].max(initial=0)),
+              max_err_grad2=float(e_g2[ran].max(initial=0)), tol_grad2=tol2,
+              max_err_zncc=zerr)
+    print("parity2", st)
+    return st

@@ -57,10 +57,24 @@ def test_create_rejects_bad_tolerance_and_iterations():
             dic.dic_create(21, 5, 10, 1, tol, it)
 
 
-def test_unsupported_shape_order():
-    with pytest.raises(dic.DICError) as e:
-        dic.dic_create(21, 5, 10, 2)
-    assert e.value.code == dic.DIC_ERR_UNSUPPORTED
+def test_shape_orders():
+    """Orders 1 and 2 are built; each refines through its own call (the
+    other returns DIC_ERR_STATE before any device work); others are refused."""
+    for order in (0, 3):
+        with pytest.raises(dic.DICError) as e:
+            dic.dic_create(21, 5, 10, order)
+        assert e.value.code == dic.DIC_ERR_UNSUPPORTED
+    lib = dic.lib()
+    h1 = dic.dic_create(21, 5, 10, 1)
+    h2 = dic.dic_create(21, 5, 10, 2)
+    try:
+        assert lib.dic_subpixel2(h1, 0, *[16] * 7) == dic.DIC_ERR_STATE
+        assert lib.dic_subpixel(h2, 0, *[16] * 12) == dic.DIC_ERR_STATE
+        assert lib.dic_subpixel2(h2, 1, *[16] * 7) == dic.DIC_ERR_UNSUPPORTED
+        assert lib.dic_subpixel2(h2, 0, *[16] * 7) == dic.DIC_ERR_STATE  # no pair
+    finally:
+        dic.dic_destroy(h1)
+        dic.dic_destroy(h2)
 
 
 def test_state_errors_before_set_pair():

@@ -771,3 +771,26 @@ def test_subpixel2_on_an_affine_field(affine1024, method):
     assert np.abs(r2["p"][ok][:, [0, 6]] - gt[ok][:, [0, 3]]).max() < 0.05
     assert np.abs(r2["p"][ok][:, [1, 2, 7, 8]] - gt[ok][:, [1, 2, 4, 5]]).mean() < 2e-3
     assert np.abs(r2["p"][ok][:, [3, 4, 5, 9, 10, 11]]).mean() < 5e-4
+
+
+def test_zncc_at2_reduces_to_first_order_and_is_invariant():
+    """Eq. 1 at a second-order shape with zero second derivatives is Eq. 1 at
+    the first-order shape (independent sampling code), and it is invariant
+    under g -> a g + b."""
+    f, g = configs.tiny(34, 70, 70, 200, Rigid(0.4, 0.7), noise=1.0)
+    nx, ny = oracle.grid(70, 70, 11, 7, 3)
+    n = nx * ny
+    rng = np.random.default_rng(6)
+    p1 = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-0.02, 0.02, n),
+                          rng.uniform(-0.02, 0.02, n), rng.uniform(-1, 1, n),
+                          rng.uniform(-0.02, 0.02, n), rng.uniform(-0.02, 0.02, n)])
+    p2 = np.zeros((n, 12))
+    p2[:, [0, 1, 2, 6, 7, 8]] = p1
+    c1 = oracle.zncc_at(f, g, 11, 7, 3, p1)
+    c2 = oracle.zncc_at2(f, g, 11, 7, 3, p2)
+    assert np.abs(c1 - c2).max() < 1e-12
+    p2[:, [3, 4, 5, 9, 10, 11]] = rng.uniform(-3e-3, 3e-3, (n, 6))
+    c3 = oracle.zncc_at2(f, g, 11, 7, 3, p2)
+    c4 = oracle.zncc_at2(f, 1.7 * g.astype(np.float64) + 13.0, 11, 7, 3, p2)
+    assert np.isfinite(c3).all() and np.abs(c3 - c4).max() < 1e-12
+    assert np.abs(c3 - c2).max() > 1e-6  # the second-order terms move the samples
