@@ -1163,7 +1163,58 @@ def run_batch_workload(args):
     print(json.dumps(rec))
 
 
+def traffic_record(csv_path: str, kernel_regex: str, sources: list[str], out: str,
+                   command: str, workload: str) -> dict:
+    """DRAM bytes per launch of the kernels matching kernel_regex in an ncu
+    CSV (--metrics dram__bytes_read.sum,dram__bytes_write.sum --csv), with
+    the SHA-256 of the given sources as they are when this runs -- run it in
+    the same command as the capture, so the hashes are those of the code
+    that was captured."""
+    import csv
+    import hashlib
+    import re
+    per_id: dict[str, float] = {}
+    names: dict[str, str] = {}
+    with open(csv_path, newline="") as fh:
+        rows = [ln for ln in fh if ln.startswith('"')]
+    for row in csv.DictReader(rows):
+        name = row.get("Kernel Name", "")
+        metric = row.get("Metric Name", "")
+        if not re.search(kernel_regex, name) or metric not in ("dram__bytes_read.sum",
+                                                               "dram__bytes_write.sum"):
+            continue
+        unit = row.get("Metric Unit", "byte").lower()
+        scale = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}.get(unit, 1)
+        val = float(row["Metric Value"].replace(",", "")) * scale
+        per_id[row["ID"]] = per_id.get(row["ID"], 0.0) + val
+        names[row["ID"]] = name
+    if not per_id:
+        raise SystemExit(f"no launch of {kernel_regex} in {csv_path}")
+    rec = {"kernel": sorted(set(names.values()))[0][:160], "workload": workload,
+           "launches": len(per_id),
+           "bytes_per_launch": int(round(statistics.mean(per_id.values()))),
+           "counters": "dram__bytes_read.sum + dram__bytes_write.sum",
+           "command": command,
+           "sources": {rel: hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read())
+                       .hexdigest() for rel in sources}}
+    with open(out, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    return rec
+
+
 def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--traffic-record":
+        ap = argparse.ArgumentParser()
+        ap.add_argument("--traffic-record", required=True, help="ncu CSV")
+        ap.add_argument("--kernel", required=True)
+        ap.add_argument("--sources", required=True, help="comma-separated repo paths")
+        ap.add_argument("--out", required=True)
+        ap.add_argument("--command", required=True)
+        ap.add_argument("--workload", default=WORKLOAD)
+        a = ap.parse_args()
+        print(json.dumps(traffic_record(a.traffic_record, a.kernel, a.sources.split(","), a.out,
+                                        a.command, a.workload)))
+        return
     args = parse()
     if args.impl == "reference":
         run_reference(args)

@@ -40,3 +40,34 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_traffic_record_from_ncu_csv(tmp_path):
+    """bench.py --traffic-record sums dram read + write per captured launch of
+    the matching kernel and stores the sources' hashes as they are when it
+    runs (in the capture's own command)."""
+    import hashlib
+    import json
+    import subprocess
+    import sys
+    csv = tmp_path / "t.csv"
+    hdr = '"ID","Process ID","Kernel Name","Metric Name","Metric Unit","Metric Value"\n'
+    rows = [
+        '"0","1","subpixel_kernel<false>(dic::SubpixelParams)","dram__bytes_read.sum","Mbyte","20.50"\n',
+        '"0","1","subpixel_kernel<false>(dic::SubpixelParams)","dram__bytes_write.sum","byte","1,000"\n',
+        '"1","1","tile_kernel(dic::SearchTcParams)","dram__bytes_read.sum","Mbyte","99.00"\n',
+        '"2","1","subpixel_kernel<false>(dic::SubpixelParams)","dram__bytes_read.sum","Mbyte","20.70"\n',
+        '"2","1","subpixel_kernel<false>(dic::SubpixelParams)","dram__bytes_write.sum","byte","3,000"\n',
+    ]
+    csv.write_text("==PROF== noise line\n" + hdr + "".join(rows))
+    out = tmp_path / "rec.json"
+    src = "paper_1905_06228_gb300/csrc/k_subpixel.cu"
+    subprocess.check_call([sys.executable, os.path.join(ROOT, "bench.py"), "--traffic-record",
+                           str(csv), "--kernel", "subpixel_kernel", "--sources", src,
+                           "--out", str(out), "--command", "ncu ..."], cwd=ROOT,
+                          stdout=subprocess.DEVNULL)
+    rec = json.loads(out.read_text())
+    assert rec["launches"] == 2
+    assert rec["bytes_per_launch"] == int(round((20.5e6 + 1000 + 20.7e6 + 3000) / 2))
+    want = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+    assert rec["sources"][src] == want
