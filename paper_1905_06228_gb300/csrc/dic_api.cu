@@ -68,12 +68,28 @@ bool encode_u8(CUtensorMap* tm, const uint8_t* base, int W, int H, int pitch, in
   return r == CUDA_SUCCESS;
 }
 
-// Tensor maps of the tensor-core search (BF16).  A box lands as 8-row
-// groups of operand rows of TWK taps (2*TWK bytes, the swizzle width):
+// Tensor maps of the tensor-core search (BF16).
 //  A: 3-D over the eight phase images [8][phh][phw]: (column, phase r,
-//     image row), box (TWK, 8, tile rows): image row = group, r = row;
-//  B: 4-D over the template bank [ny][S][nx][twk]: (tap, POI column, POI
-//     row, template row), box (TWK, ncols, nrows, 1): a tile's POI block.
+//     image row), box (TWK, 8, tile rows): image row = 8-row group, r = row,
+//     swizzle of the row width (2*TWK bytes);
+//  B: 4-D over the template bank [bank_rows][nx][64]: (tap, POI column, POI
+//     row, operand row j), box (64, ncols, nrows, 1): one stage of a tile's
+//     POI block, 128-byte swizzle.  Bank row of (kr, j): kr*step + SUB*j by
+//     image row (overlapping strides), kr*sj + j stacked.
+bool encode_bank_map(CUtensorMap* tmb, void* bank, int nx, int ny, int sj, cuuint64_t kr_rows,
+                     cuuint64_t j_rows, int ncols, int nrows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t row = (cuuint64_t)nx * 128;  // bytes per bank row
+  cuuint64_t dims[4] = {64, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)sj};
+  cuuint64_t str[3] = {128, row * kr_rows, row * j_rows};
+  cuuint32_t box[4] = {64, (cuuint32_t)ncols, (cuuint32_t)nrows, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(tmb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, bank, dims, str, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_tc(CUtensorMap* tma, CUtensorMap* tmb, const dic::SearchTcParams& t) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
@@ -90,17 +106,30 @@ bool encode_tc(CUtensorMap* tma, CUtensorMap* tmb, const dic::SearchTcParams& t)
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
-  {
-    const cuuint64_t row = (cuuint64_t)t.nx * t.twk * 2;  // bytes per template row
-    cuuint64_t dims[4] = {(cuuint64_t)t.twk, (cuuint64_t)t.nx, (cuuint64_t)t.ny, (cuuint64_t)t.S};
-    cuuint64_t str[3] = {(cuuint64_t)t.twk * 2, row * t.S, row};
-    cuuint32_t box[4] = {(cuuint32_t)t.twk, (cuuint32_t)t.ncols_max, (cuuint32_t)t.nrows_max, 1};
-    cuuint32_t es[4] = {1, 1, 1, 1};
-    if (fn(tmb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, t.bank, dims, str, box, es,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return false;
+  const cuuint64_t kr_rows = t.bank_overlap ? (cuuint64_t)t.step : (cuuint64_t)t.sj;
+  const cuuint64_t j_rows = t.bank_overlap ? (cuuint64_t)t.sub : 1;
+  return encode_bank_map(tmb, t.bank, t.nx, t.ny, t.sj, kr_rows, j_rows, t.ncols_max,
+                         t.nrows_max);
+}
+
+// Whether the tensor map encoder takes the bank by image row (strides of
+// the POI-row and operand-row dimensions that overlap).  Asked once, with a
+// map that is never used; no memory is accessed.
+bool bank_overlap_ok() {
+  static int ok = -1;
+  if (ok < 0) {
+    alignas(128) static unsigned char probe[128];
+    CUtensorMap tm;
+    ok = encode_bank_map(&tm, probe, 20, 20, 16, 5, 2, 10, 12) ? 1 : 0;
   }
+  return ok == 1;
+}
+
+// Geometry of the tensor-core search, with the bank's row order the
+// encoder accepts.
+bool tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, dic::SearchTcParams* t) {
+  if (!dic::search_tc_geometry(W, H, S, step, R, nx, ny, t)) return false;
+  if (t->bank_overlap && !bank_overlap_ok()) return dic::search_tc_bank_order(t, 0);
   return true;
 }
 
@@ -216,7 +245,9 @@ dic_status dic_check(dic_t h) {
   if (e != cudaSuccess) return cuda_fail(h, e, "error-flag reset");
   return fail(h, DIC_ERR_TIMEOUT,
               "a bounded device wait gave up (flag 0x%x: 1 FP32 search staging, 2 tensor-core "
-              "tile pipeline); the affected integer-search results are incomplete",
+              "tile pipeline, with 0x10 A free, 0x20 B stage free, 0x40 accumulator read, "
+              "0x80 A landed, 0x100 B landed, 0x200 accumulator complete, 0x400 last MMAs); "
+              "the affected integer-search results are incomplete",
               flag);
 }
 
@@ -508,7 +539,7 @@ dic_status search_images(dic_t h, const uint8_t* ref, const uint8_t* def, bool t
                          int32_t* v0, float* zncc0, uint8_t* status, cudaStream_t st) {
   if (h->form == DIC_FORM_BF16TC) {
     dic::SearchTcParams t{};
-    if (!dic::search_tc_geometry(h->g.W, h->g.H, h->subset, h->step, h->R, h->g.nx, h->g.ny,
+    if (!tc_geometry(h->g.W, h->g.H, h->subset, h->step, h->R, h->g.nx, h->g.ny,
                                  &t) ||
         dic::search_tc_smem(t) > 227 * 1024)
       return fail(h, DIC_ERR_UNSUPPORTED,
@@ -1019,7 +1050,7 @@ dic_status dic_set_pairs(dic_t h, int n_pairs, const dic_pair_desc* descs) {
     }
     grid_of(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, &bp.nx, &bp.ny);
     bp.fp32_ok = dic::search_smem_bytes(bp.S, bp.R) <= 227 * 1024;
-    bp.tc_ok = dic::search_tc_geometry(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, bp.nx,
+    bp.tc_ok = tc_geometry(bp.d.width, bp.d.height, bp.S, bp.step, bp.R, bp.nx,
                                        bp.ny, &bp.tc) &&
                dic::search_tc_smem(bp.tc) <= 227 * 1024;
     if (!bp.fp32_ok && !bp.tc_ok && bp.nx > 0 && bp.ny > 0) {

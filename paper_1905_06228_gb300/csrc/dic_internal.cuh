@@ -61,17 +61,23 @@ struct SearchTcParams {
   int W, H, pitch;
   int S, M, R, step, nx, ny;
   int64_t n_pois;
-  int twk;           // template row width padded to 16 taps
+  int twk;           // template row width padded to 16 taps (taps per A operand row)
+  int sub;           // template rows per B operand row of 64 taps: 64 / twk
+  int sj;            // B operand rows per template: ceil(S / sub)
+  int bank_overlap;  // 1: bank rows by image row, 0: [ny][sj] (see bank_kernel)
+  int bank_rows;
   int npad;          // N of the MMA (POIs per tile block, padded to 16)
   int ncols_max, nrows_max;  // POI block of a tile's CTA (columns, rows of one chunk)
   int nchunk;                // CTAs per tile, each taking nrows_max rows of POIs
   int arows;                 // image rows of a tile's A buffer
   int rows_per_acc;  // template rows per exact FP32 accumulator
   int tmem_cols;
-  int stages;        // template-row stages of the tile kernel's ring
+  int accbufs;       // TMEM accumulator buffers of the tile kernel (1 or 2)
+  int abufs;         // A buffers of the tile kernel (1 or 2)
+  int stages;        // B stages of the tile kernel's ring
   int xmin, ymin, ntx, nty;
   int slots_x, slots_y, nslots;
-  uint16_t* bank;    // [ny][S][nx][twk] centred BF16 subsets of f (POI-major rows)
+  uint16_t* bank;    // [bank_rows][nx][64] centred BF16 subsets of f (see bank_kernel)
   uint16_t* gph;     // [8][phh][phw] centred BF16 copies of g shifted by 0..7
   int phh, phw;
   int2* fbox;        // like posbox, for the reference image (POI sums)
@@ -166,6 +172,9 @@ size_t search_tc_smem(const SearchTcParams& g);
 size_t search_tc_posbox_elems(const SearchTcParams& g);
 size_t search_tc_phase_elems(const SearchTcParams& g);  // phase images + template bank
 size_t search_tc_gph_elems(const SearchTcParams& g);
+// Sets the bank's row order (1: by image row, 0: stacked) and its row
+// count; false if that order exceeds the bank's limits.
+bool search_tc_bank_order(SearchTcParams* g, int overlap);
 cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
                              const CUtensorMap* tmB, cudaStream_t st);
 // Box-sum maps of f (fbox) and g (posbox) over p.xmin, p.ymin, p.ntx * 8 by

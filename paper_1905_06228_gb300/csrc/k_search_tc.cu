@@ -9,19 +9,26 @@
 //
 //   D[m][n] = sum_ty sum_tx  G[Y0+q+ty][X0+r+tx] * T_n[ty][tx],   m = 8q + r
 //
-// Operands are K-major with rows of TWK taps (16, 32 or 64; 2*TWK bytes, the
-// swizzle width of both the TMA boxes and the MMA descriptors):
-//  A (M = 128 positions): row (q, r) at image row Y0+q+ty holds
+// Operands are K-major.  A template row is padded to TWK taps (16, 32 or 64).
+//  A (M = 128 positions): rows of TWK taps (2*TWK bytes, the swizzle width
+//    of its TMA box and descriptor); row (q, r) at image row Y0+q+ty holds
 //    g[Y0+q+ty][X0+r ..] - 128, i.e. row Y0+q+ty of the phase image r (the
 //    copy of g shifted by r columns).  One 3-D TMA box loads all tile rows
 //    once; an 8-row group is one image row, so the step ty -> ty+1 is a
 //    descriptor offset of one group.
-//  B (N = POI block): row n holds template row ty of POI n from the
-//    template bank (every subset of f, POI-major rows); one 4-D TMA box per
-//    template row loads the whole block, streamed through a ring of stages.
-// One thread issues the TMA loads, one thread the MMAs (tcgen05.mma
-// kind::f16, BF16 x BF16 -> FP32, M=128, K=16 per instruction), paired by
-// full/empty mbarriers; the accumulator lives in TMEM.
+//  B (N = POI block): rows of 64 taps (128 bytes, 128-byte swizzle), each
+//    holding SUB = 64 / TWK consecutive template rows of one POI from the
+//    template bank; one 4-D TMA box per operand row j loads the template
+//    rows SUB*j .. SUB*j + SUB-1 of the whole block, streamed through a
+//    ring of stages.  The four K = 16 MMAs of a stage each take their A
+//    descriptor at the image row of their template row; MMAs of template
+//    rows at or beyond S are not issued.
+//
+// The tile kernel is persistent and warp-specialised: one lane streams A
+// and B by TMA, one lane issues the MMAs (tcgen05.mma kind::f16, BF16 x BF16
+// -> FP32, M=128, K=16 per instruction) into one of two TMEM accumulator
+// buffers, and eight epilogue warps score the other buffer, all paired by
+// mbarriers.
 //
 // Exactness: a = f-128 and b = g-128 are integers in [-128, 127], exact in
 // BF16; |ab| <= 2^14, so any sum of at most 1024 products is an integer of
@@ -34,12 +41,13 @@
 //
 // Epilogue: each warp reads one lane quarter of TMEM (32 positions) x 16
 // POIs, scores sign(num) num^2 / Dg in FP32 (errors bounded, see
-// score_block) and keeps each POI's best two through a warp reduce-scatter;
-// a POI's float winner is its exact tile winner when it clears the second
-// by 5e-4, otherwise one warp compares the near-tied positions exactly.
-// Each (tile, POI) winner goes to a slot; a final kernel reduces a POI's
-// slots exactly (lowest linear index on ties), so the integer result is
-// bit-identical to the FP32 form and to the oracle.
+// score_block) and keeps each POI's best two, and the exact sum at the best,
+// through a warp reduce-scatter; a POI's float winner is its exact tile
+// winner when it clears the second by 5e-4, otherwise the warps of the four
+// lane quarters compare the near-tied positions exactly from the sums in
+// TMEM.  Each (tile, POI) winner goes to a slot; a final kernel reduces a
+// POI's slots exactly (lowest linear index on ties), so the integer result
+// is bit-identical to the FP32 form and to the oracle.
 #include <algorithm>
 
 #include "dic_device.cuh"
@@ -48,7 +56,6 @@
 namespace dic {
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kMaxSlots = 1024;  // tiles met by one POI window (10-bit index)
 constexpr int kTileQ = 16;  // position rows per tile
 constexpr int kTileR = 8;   // position columns per tile
@@ -161,33 +168,44 @@ __global__ void phase_kernel(const SearchTcParams p) {
 }
 
 // ------------------------------------------------------------ template bank
-// Every POI's subset of f, centred BF16, rows padded to TWK taps with zeros:
-//   bank[((kr*S + ty)*nx + kc)*TWK + tx] = f[yl+ty][xl+tx] - 128  (tx < S)
-// with (xl, yl) the subset's top-left.  Row ty of the POIs of one grid row
-// is contiguous, so a tile's template rows stream as runs of 16-byte chunks.
-// One thread per 16-byte chunk.
+// B operand rows of every POI's subset of f, centred BF16: a bank row holds,
+// for each POI column kc, 64 taps = SUB template rows of TWK taps,
+//   bank[(b*nx + kc)*64 + s*TWK + tx] = f[y(b) + s][xl(kc) + tx] - 128
+// (tx < S, else 0), xl(kc) the subsets' left edge.  Two row orders:
+//  - by image row (bank_overlap = 1): y(b) = top row of the first POI row +
+//    b, so operand row j of POI row kr is bank row kr*step + SUB*j, and the
+//    tensor map's POI-row and operand-row strides overlap (step and SUB
+//    bank rows); an image row is stored SUB times instead of S/step times;
+//  - stacked (bank_overlap = 0): b = kr*sj + j, y(b) = top row of POI row kr
+//    + SUB*j, template rows at or beyond S stored as zeros.
+// One thread per 16-byte chunk (8 taps, never across two template rows).
 __global__ void bank_kernel(const SearchTcParams p) {
-  // blockIdx.y = kr * S + ty (one bank row); threads over (kc, kb)
-  const int KB = p.twk / 8;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.nx * KB) return;
-  const int kc = t / KB, kb = t - kc * KB;
-  const int kr = blockIdx.y / p.S, ty = blockIdx.y - kr * p.S;
-  const int B = p.M + p.R + 2;
-  const int xl = B + kc * p.step - p.M, yl = B + kr * p.step - p.M;
-  const uint8_t* src = p.ref + (size_t)(yl + ty) * p.pitch + xl;
+  if (t >= p.nx * 8) return;
+  const int kc = t >> 3, kb = t & 7;
+  const int b = blockIdx.y, B = p.M + p.R + 2;
+  int ytop = B - p.M + b, ty_lim = INT_MAX;  // image row of sub-row 0, template rows left
+  if (!p.bank_overlap) {
+    const int kr = b / p.sj, j = b - kr * p.sj;
+    ytop = B - p.M + kr * p.step + p.sub * j;
+    ty_lim = p.S - p.sub * j;
+  }
+  const int s = (8 * kb) / p.twk, tx0 = 8 * kb - s * p.twk;
+  const int y = ytop + s;
+  const bool row_ok = s < ty_lim && y < p.H;
+  const uint8_t* src = p.ref + (size_t)(row_ok ? y : 0) * p.pitch + (B + kc * p.step - p.M);
   uint32_t w[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     uint32_t h2[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int tx = 8 * kb + 2 * e + k;
-      h2[k] = tx < p.S ? centred_bf16(src[tx]) : 0u;
+      const int tx = tx0 + 2 * e + k;
+      h2[k] = (row_ok && tx < p.S) ? centred_bf16(src[tx]) : 0u;
     }
     w[e] = h2[0] | (h2[1] << 16);
   }
-  *reinterpret_cast<uint4*>(p.bank + ((size_t)blockIdx.y * p.nx * KB + t) * 8) =
+  *reinterpret_cast<uint4*>(p.bank + ((size_t)b * p.nx + kc) * 64 + 8 * kb) =
       make_uint4(w[0], w[1], w[2], w[3]);
 }
 
@@ -277,49 +295,74 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
 }
 
 // ------------------------------------------------------------ tile kernel
-// Roles.  Thread 0 streams the template rows B(ty) into a ring of p.stages
-// shared-memory stages with TMA (one box per 8-POI group, arriving on
-// full[ty]); thread 32 issues the MMAs of row ty once full[ty] completes and
-// commits them to empty[ty], which lets the producer refill that stage.  The
-// other threads wait at the block barrier before the epilogue.
-constexpr int kMaxStages = 12;
+// A work item is one tile of positions with one chunk of its POI block.  The
+// kernel is persistent (one CTA per SM, CTA c takes the items c, c + grid,
+// ...) and warp-specialised:
+//  - warp 0 (one lane) streams, per item, the A rows into one of p.abufs A
+//    buffers and the B stages into a ring of p.stages that runs on across
+//    items, with TMA;
+//  - warp 1 (one lane) issues the item's MMAs into one of p.accbufs TMEM
+//    accumulator buffers and commits them to the item's barriers;
+//  - kEpiWarps epilogue warps score a finished buffer while the MMAs of the
+//    next item run in the other.
+// Barriers: a_full/a_empty per A buffer, b_full/b_empty per stage,
+// acc_full/acc_empty per accumulator buffer.  Every wait is bounded: a wait
+// that gives up sets the abort word and err_flag, and each role then leaves
+// its loop (the epilogue warps decide together, at a barrier).
+constexpr int kMaxStages = 16;
+constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 64 + kEpiThreads;
+constexpr int kEpiGroups = kEpiWarps / 4;         // warps per lane quarter
 constexpr int kWaitLimit = 1 << 17;  // try_wait calls before giving up (~1.3 s)
+// err_flag bits of the tile kernel: 2 | the wait that gave up
+constexpr unsigned kGaveUpAEmpty = 1u << 4;    // producer: A buffer free
+constexpr unsigned kGaveUpBEmpty = 1u << 5;    // producer: B stage free
+constexpr unsigned kGaveUpAccEmpty = 1u << 6;  // MMA: accumulator buffer read
+constexpr unsigned kGaveUpAFull = 1u << 7;     // MMA: A rows landed
+constexpr unsigned kGaveUpBFull = 1u << 8;     // MMA: B stage landed
+constexpr unsigned kGaveUpAccFull = 1u << 9;   // epilogue: accumulator complete
+constexpr unsigned kGaveUpDone = 1u << 10;     // MMA: last MMAs complete
+
+constexpr int kRowB = 128;  // bytes of a B operand row (64 taps): its swizzle width
+constexpr int kPos = kTileQ * kTileR;  // positions per tile (the MMA's M)
 
 struct TileLayout {
   int rows;    // image rows of the tile: kTileQ + S - 1
-  int RB;      // bytes of one operand row (TWK taps): the swizzle width
-  int grp;     // bytes of an 8-row group: 8 * RB (one image row of A)
-  int stageB;  // bytes per template-row stage: Npad * RB
-  size_t off_bar, off_tmem, off_pos, off_poi, off_red, off_tie, off_a, off_b, off_d, total;
+  int RB;      // bytes of one A operand row (TWK taps): its swizzle width
+  int grp;     // bytes of an 8-row group of A: 8 * RB (one image row)
+  int abytes;  // bytes of one A buffer, rounded to 1024
+  int stageB;  // bytes per B stage: Npad * kRowB
+  size_t off_bar, off_misc, off_pos, off_poi, off_red, off_tie, off_tc, off_a, off_b, total;
 };
 
 __host__ __device__ inline size_t al(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-constexpr int kPos = kTileQ * kTileR;  // positions per tile (the MMA's M)
-constexpr int kDs = kPos + 1;          // row stride of the transposed sums
+// Best candidate of one quarter of a tie's positions (exact sums).
+struct TieCand {
+  long long num, dg;
+  int l, pad;
+};
 
-__host__ __device__ inline TileLayout tile_layout(int S, int TWK, int npad, int stages) {
+__host__ __device__ inline TileLayout tile_layout(int S, int TWK, int npad, int stages,
+                                                  int abufs) {
   TileLayout L;
   L.rows = kTileQ + S - 1;
   L.RB = 2 * TWK;
   L.grp = 8 * L.RB;
-  L.stageB = npad * L.RB;
+  L.abytes = (int)al((size_t)L.rows * L.grp, 1024);
+  L.stageB = npad * kRowB;
   size_t o = 0;
-  L.off_bar = o;  o += 8 * (2 * kMaxStages + 2);
-  L.off_tmem = o; o += 8;
+  L.off_bar = o;  o += 8 * (2 * kMaxStages + 9);
+  L.off_misc = o; o += 16;                                   // TMEM base, abort, tie count
   o = al(o, 16);  L.off_pos = o;  o += (size_t)kPos * 16;    // dg, sb, 1/dg
   L.off_poi = o;  o += (size_t)npad * 16;                    // per-POI window and sums
-  L.off_red = o;  o += (size_t)4 * npad * 8;                 // per-quarter best two
-  L.off_tie = o;  o += (size_t)npad * 8 + 16;                // near-tie list + count
+  L.off_red = o;  o += (size_t)4 * npad * 16;                // per-quarter best two + sum
+  L.off_tie = o;  o += (size_t)npad * 8;                     // near-tie list
+  L.off_tc = o;   o += (size_t)4 * npad * sizeof(TieCand);   // per-quarter tie winners
   o = al(o, 1024);  // swizzle atoms of the operands start on 1024-byte boundaries
-  // A buffer and B stages; the transposed sums reuse this region once the
-  // last MMA has completed
-  const size_t ab = (size_t)L.rows * L.grp + (size_t)stages * L.stageB;
-  const size_t dd = (size_t)npad * kDs * 4;
-  L.off_a = o;
-  L.off_b = o + (size_t)L.rows * L.grp;
-  L.off_d = o;
-  o += ab > dd ? ab : dd;
+  L.off_a = o;    o += (size_t)abufs * L.abytes;
+  L.off_b = o;    o += (size_t)stages * L.stageB;
   L.total = o;
   return L;
 }
@@ -366,34 +409,17 @@ __device__ __forceinline__ void bfly(int (&mx)[8], int (&sc)[8], bool up, int o)
   }
 }
 
-// Scores of one (quarter, 16-column) block of the accumulator and their
-// per-POI best two over the quarter's 32 positions.
-//
-// Position m = 32*quarter + lane (row q = m/8, column r = m%8 of the tile)
-// holds the sums of POIs c0..c0+15.  The score sign(num) num^2 / Dg orders a
-// POI's candidates like its ZNCC.  Without wide sums (one accumulator,
-// |Sab| < 2^24 exact in FP32) num is formed in FP32 from exact operands:
-// Sa*Sb as an exact two-float product, N*Sab - hi in one FMA, then - lo;
-// its error is at most 2^-23 |num| + 2^-14.  With wide sums num is exact in
-// 64-bit integers and only the final conversion rounds.  Either way a
-// score's relative error, including the position index packed into the
-// low 7 bits of its key, stays below 1.5e-4 for num != 0, and |score| <
-// 4e-9 when num = 0; the winner test in the tile kernel relies on this.
+// Sums of the accumulator for lane quarter `quarter`, columns c .. c+15 of
+// every accumulator of a buffer (one accumulator: the exact FP32 sums as
+// bits; several: their int32 total).
 template <bool kWide>
-__device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tmem, int nacc,
-                                            int quarter, int lane, int c0, int rr, int q,
-                                            float sbf, int sb, float pinv_m, const PoiInfo* poi,
-                                            int* dsm, int2* red) {
-  const int NP = p.npad, R2 = 2 * p.R, m = quarter * 32 + lane;
-  const long long N = (long long)p.S * p.S;
-  const float Nf = (float)N;
-  // val: the exact FP32 sums (one accumulator) or int32 sums (several)
-  uint32_t val[16];
+__device__ __forceinline__ void load_sums(uint32_t tmem, int nacc, int np, int quarter, int c,
+                                          uint32_t (&val)[16]) {
 #pragma unroll
   for (int k = 0; k < 16; ++k) val[k] = 0;
   for (int a = 0; a < nacc; ++a) {
     uint32_t v[16];
-    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * NP + c0);
+    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * np + c);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -406,11 +432,36 @@ __device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tm
     for (int k = 0; k < 16; ++k)
       val[k] = kWide ? (uint32_t)((int)val[k] + __float2int_rn(__uint_as_float(v[k]))) : v[k];
   }
+}
+
+// Scores of one (quarter, 16-column) block of an accumulator buffer and
+// their per-POI best two over the quarter's 32 positions, with the sum at
+// the best.
+//
+// Position m = 32*quarter + lane (row q = m/8, column r = m%8 of the tile)
+// holds the sums of POIs c0..c0+15.  The score sign(num) num^2 / Dg orders a
+// POI's candidates like its ZNCC.  Without wide sums (one accumulator,
+// |Sab| < 2^24 exact in FP32) num is formed in FP32 from exact operands:
+// Sa*Sb as an exact two-float product, N*Sab - hi in one FMA, then - lo;
+// its error is at most 2^-23 |num| + 2^-14.  With wide sums num is exact in
+// 64-bit integers and only the final conversion rounds.  Either way a
+// score's relative error, including the position index packed into the
+// low 7 bits of its key, stays below 1.5e-4 for num != 0, and |score| <
+// 4e-9 when num = 0; the winner test relies on this.
+template <bool kWide>
+__device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tmem, int nacc,
+                                            int quarter, int lane, int c0, int rr, int q,
+                                            float sbf, int sb, float pinv_m, const PoiInfo* poi,
+                                            int4* red) {
+  const int NP = p.npad, R2 = 2 * p.R, m = quarter * 32 + lane;
+  const long long N = (long long)p.S * p.S;
+  const float Nf = (float)N;
+  uint32_t val[16];
+  load_sums<kWide>(tmem, nacc, NP, quarter, c0, val);
   int mx[8], sc[8];
   int key[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    dsm[(c0 + k) * kDs + m] = (int)val[k];
     const PoiInfo pi = poi[c0 + k];
     const bool in = (unsigned)(rr - pi.cx) <= (unsigned)R2 && (unsigned)(q - pi.cy) <= (unsigned)R2;
     float nf;
@@ -444,11 +495,18 @@ __device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tm
     const int rsc = __shfl_xor_sync(0xffffffffu, sc[0], 1);
     merge2(mx[0], sc[0], rmx, rsc);
   }
-  if ((lane & 1) == 0) {
-    const int j = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                  ((lane >> 1) & 1);
-    red[quarter * NP + c0 + j] = make_int2(mx[0], sc[0]);
+  // lanes l and l^1 now hold the best two of POI c0 + j; the sum at the
+  // best position sits in register val[j] of lane (best & 31)
+  const int j = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
+                ((lane >> 1) & 1);
+  const int src = mx[0] == INT_MIN ? lane : (mx[0] & 31);
+  int vbest = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int v = __shfl_sync(0xffffffffu, (int)val[k], src);
+    if (j == k) vbest = v;
   }
+  if ((lane & 1) == 0) red[quarter * NP + c0 + j] = make_int4(mx[0], sc[0], vbest, 0);
 }
 
 // POI n of a tile's block (row-major over ncols_max x nrows_max): operand
@@ -458,320 +516,533 @@ __device__ __forceinline__ void block_poi(const SearchTcParams& p, int n, int& b
   bj = n % p.ncols_max;
 }
 
-__global__ void __launch_bounds__(kThreads, 3)
+// Tile origin (absolute positions; X0 a multiple of 8) and POI block of a
+// work item; false if the item meets no POI (a chunk past the block's last
+// row, or a tile in a gap between windows when the grid step exceeds
+// 2R + 8): every role skips such items alike.
+struct TileItem {
+  int X0, Y0, kc0, kr0, nbr, nbc;
+};
+
+__device__ __forceinline__ bool tile_item(const SearchTcParams& p, int item, TileItem& t) {
+  const int tile = item / p.nchunk, chunk = item - tile * p.nchunk;
+  const int M = p.M, R = p.R, B = M + R + 2;
+  t.X0 = p.xmin + (tile % p.ntx) * kTileR;
+  t.Y0 = p.ymin + (tile / p.ntx) * kTileQ;
+  // POI column k is met iff x_k - M - R <= X0 + 7 and x_k - M + R >= X0
+  auto ceil_div = [](int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); };
+  auto floor_div = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
+  t.kc0 = max(0, ceil_div(t.X0 + M - R - B, p.step));
+  t.kr0 = max(0, ceil_div(t.Y0 + M - R - B, p.step)) + chunk * p.nrows_max;
+  const int kc1 = min(p.nx - 1, floor_div(t.X0 + kTileR - 1 + M + R - B, p.step));
+  const int kr1 = min(p.ny - 1, floor_div(t.Y0 + kTileQ - 1 + M + R - B, p.step));
+  t.nbr = min(kr1 - t.kr0 + 1, p.nrows_max);
+  t.nbc = kc1 - t.kc0 + 1;
+  return t.nbr > 0 && t.nbc > 0;
+}
+
+__device__ __forceinline__ void epi_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
+}
+// true on every epilogue thread if v is true on any
+__device__ __forceinline__ bool epi_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.or.pred q, 1, %2, p; "
+      "selp.u32 %0, 1, 0, q; }"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kEpiThreads)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Issue helpers for a converged warp: elect.sync picks one lane (the same
+// lowest active lane every time), which issues the operation.
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "{ .reg .b32 r; .reg .pred e; elect.sync r|e, 0xffffffff; "
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0]; }" ::"r"(
+          bar)
+      : "memory");
+}
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{ .reg .b32 r; .reg .pred e, p; elect.sync r|e, 0xffffffff; setp.ne.b32 p, %4, 0; "
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void tma_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile(
+      "{ .reg .b32 r; .reg .pred e; elect.sync r|e, 0xffffffff; "
+      "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1; }" ::"r"(bar),
+      "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "{ .reg .b32 r; .reg .pred e; elect.sync r|e, 0xffffffff; "
+      "@e cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5]; }" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "{ .reg .b32 r; .reg .pred e; elect.sync r|e, 0xffffffff; "
+      "@e cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6]; }" ::"r"(dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+// The MMAs of one B stage: SUB template rows of 64 / SUB taps, KPR = 4 / SUB
+// MMAs of 16 taps each, straight-line with constant descriptor offsets.
+// (ty, rin, dcol, ad_row): the next template row, its row within the
+// current accumulator, that accumulator's TMEM column, its A descriptor.
+template <int SUB>
+__device__ __forceinline__ void issue_stage(uint32_t& dcol, uint64_t& ad_row, uint64_t bd, int& ty,
+                                            int& rin, int S, int rows_per_acc, uint32_t a_step,
+                                            uint32_t np, uint32_t idesc) {
+  constexpr int KPR = 4 / SUB;
+#pragma unroll
+  for (int sr = 0; sr < SUB; ++sr) {
+    if (ty < S) {
+#pragma unroll
+      for (int kk = 0; kk < KPR; ++kk)
+        umma_f16(dcol, ad_row + (uint64_t)(2 * kk), bd + (uint64_t)(2 * (sr * KPR + kk)), idesc,
+                 (rin == 0 && kk == 0) ? 0u : 1u);
+      ++ty;
+      ad_row += a_step;
+      if (++rin == rows_per_acc) {
+        rin = 0;
+        dcol += np;
+      }
+    }
+  }
+}
+
+// A wait of the whole warp, decided by lane 0's observation (uniform).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int limit) {
+  const int ok = mbar_wait(bar, parity, limit) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
     tile_kernel(const SearchTcParams p, const __grid_constant__ CUtensorMap tmA,
                 const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = p.S, M = p.M, R = p.R, TWK = p.twk, NP = p.npad, NST = p.stages;
-  const TileLayout L = tile_layout(S, TWK, NP, NST);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bar);
-  uint64_t* empty = full + kMaxStages;
-  uint64_t* done = empty + kMaxStages;
-  uint64_t* abar = done + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.off_tmem);
+  const int S = p.S, R = p.R, TWK = p.twk, NP = p.npad, NST = p.stages;
+  const int NAB = p.abufs, NACB = p.accbufs;
+  const TileLayout L = tile_layout(S, TWK, NP, NST, NAB);
+  uint64_t* b_full = reinterpret_cast<uint64_t*>(smem + L.off_bar);
+  uint64_t* b_empty = b_full + kMaxStages;
+  uint64_t* a_full = b_empty + kMaxStages;  // [2]
+  uint64_t* a_empty = a_full + 2;           // [2]
+  uint64_t* acc_full = a_empty + 2;         // [2]
+  uint64_t* acc_empty = acc_full + 2;       // [2]
+  uint64_t* done = acc_empty + 2;           // every MMA of the CTA completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.off_misc);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* nties = reinterpret_cast<int*>(tmem_slot + 2);
   long long* pdg = reinterpret_cast<long long*>(smem + L.off_pos);  // Dg per position
   int* psb = reinterpret_cast<int*>(pdg + kPos);                     // Sb per position
   float* pinv = reinterpret_cast<float*>(psb + kPos);                // 1 / Dg
   PoiInfo* poi = reinterpret_cast<PoiInfo*>(smem + L.off_poi);
-  int2* red = reinterpret_cast<int2*>(smem + L.off_red);
+  int4* red = reinterpret_cast<int4*>(smem + L.off_red);
   int2* ties = reinterpret_cast<int2*>(smem + L.off_tie);  // (POI n, threshold bits)
-  int* nties = reinterpret_cast<int*>(ties + NP);
+  TieCand* tcand = reinterpret_cast<TieCand*>(smem + L.off_tc);
   unsigned char* abuf = smem + L.off_a;
   unsigned char* bbuf = smem + L.off_b;
-  int* dsm = reinterpret_cast<int*>(smem + L.off_d);
 
-  // tile origin (absolute positions; X0 is a multiple of 8) and its POI block
-  const int tile = blockIdx.x;
-  const int X0 = p.xmin + (tile % p.ntx) * kTileR;
-  const int Y0 = p.ymin + (tile / p.ntx) * kTileQ;
-  const int B = M + R + 2;
-  // POI column k is met iff x_k - M - R <= X0 + 7 and x_k - M + R >= X0
-  auto ceil_div = [](int a, int b) { return a >= 0 ? (a + b - 1) / b : -((-a) / b); };
-  auto floor_div = [](int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); };
-  // blockIdx.y selects a chunk of nrows_max POI rows of the block (several
-  // chunks when the whole block would exceed N = 256 or the TMEM columns)
-  const int kc0 = max(0, ceil_div(X0 + M - R - B, p.step));
-  const int kr0 = max(0, ceil_div(Y0 + M - R - B, p.step)) + (int)blockIdx.y * p.nrows_max;
-  const int kc1 = min(p.nx - 1, floor_div(X0 + kTileR - 1 + M + R - B, p.step));
-  const int kr1 = min(p.ny - 1, floor_div(Y0 + kTileQ - 1 + M + R - B, p.step));
-  const int nbr = kr1 - kr0 + 1, nbc = kc1 - kc0 + 1;
-  // a chunk past the block's last row, or a tile in a gap between windows
-  // (grid step > 2R + 8): no POI, nothing to compute (uniform over the CTA)
-  if (nbr <= 0 || nbc <= 0) return;
+  const int nitems = p.ntx * p.nty * p.nchunk;
   const long long N = (long long)S * S;
-  const int nblock = p.ncols_max * p.nrows_max;  // POIs (operand rows) loaded per row
-  const uint32_t row_bytes = (uint32_t)(nblock * L.RB);
+  const int nblock = p.ncols_max * p.nrows_max;  // POIs (operand rows) loaded per stage
+  const int rows_per_acc = p.rows_per_acc;
+  const int nacc = (S + rows_per_acc - 1) / rows_per_acc;
+  const uint32_t bufcols = (uint32_t)(nacc * NP);  // TMEM columns of one accumulator buffer
 
-  // ---- setup: barriers and the A buffer (one TMA: for image rows Y0 ..
-  // Y0+rows-1 and positions r = 0..7 of the tile's row, the TWK taps from
-  // column X0 + r, i.e. row r of phase image r; 8-row group = image row):
-  //   A row (row, r), tap k = g[Y0+row][X0 + r + k] - 128  (0 beyond the
-  // phase images; taps at or beyond S meet zero template taps),
-  // then TMEM allocation (warp 0)
-  const uint32_t ncols = p.tmem_cols;
   if (tid == 0) {
-    *nties = 0;
+    *abort_flag = 0;
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
     for (int i = 0; i < NST; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&b_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&b_empty[i])));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&a_empty[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_empty[i])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(abar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(abar)),
-                 "r"((uint32_t)(L.rows * L.grp))
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(abuf)),
-        "l"(&tmA), "r"(X0), "r"(0), "r"(Y0), "r"(smem_u32(abar))
-        : "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(ncols)
+                 "r"((uint32_t)p.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  // ---- per-position box statistics (from the map)
-  if (tid < kPos) {
-    const int q = tid / kTileR, r = tid % kTileR;
-    const int2 bx = p.posbox[(size_t)(Y0 - p.ymin + q) * (p.ntx * 8) + (X0 - p.xmin + r)];
-    const long long dg = N * (long long)bx.y - (long long)bx.x * bx.x;
-    pdg[tid] = dg;
-    psb[tid] = bx.x;
-    pinv[tid] = dg ? 1.0f / ll_to_float(dg) : 0.f;
-  }
-  // ---- per-POI window and reference sums
-  for (int n = tid; n < NP; n += kThreads) {
-    int bi, bj;
-    block_poi(p, n, bi, bj);
-    PoiInfo pi{kNoPoi, kNoPoi, 0.f, 0};
-    if (n < nblock && bi < nbr && bj < nbc) {
-      const int xl = B + (kc0 + bj) * p.step - M, yl = B + (kr0 + bi) * p.step - M;
-      const int2 fb = p.fbox[(size_t)(yl - p.ymin) * (p.ntx * 8) + (xl - p.xmin)];
-      // a POI without reference variance is decided by the reduce kernel
-      if (N * (long long)fb.y - (long long)fb.x * fb.x != 0)
-        pi = PoiInfo{xl - X0 - R, yl - Y0 - R, (float)fb.x, fb.x};
-    }
-    poi[n] = pi;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  auto give_up = [&](unsigned site) {
+    *abort_flag = 1;
+    atomicOr(p.err_flag, 2u | site);
+  };
 
-  const int rows_per_acc = p.rows_per_acc;
-  int failed = 0, issued = 0;
-  if (tid == 0) {
-    // ---- producer: template row ty of every POI of the block into stage
-    // ty % NST with one TMA: the ncols_max x nrows_max patch of the bank
-    // lands as operand rows n = bi * ncols_max + bj of TWK taps (swizzled)
-    const uint32_t bbase = smem_u32(bbuf);
+  if (warp == 0) {
+    // ---- producer: the whole warp runs the loop (uniform control flow and
+    // operands), one elected lane issues each copy
+    int i = 0, gs = 0;  // items and B stages issued
     int st = 0;
-    uint32_t eparity = 0;  // parity of the empty phase awaited on this lap
-    for (int ty = 0; ty < S; ++ty, ++issued) {
-      if (ty >= NST && !mbar_wait(smem_u32(&empty[st]), eparity, kWaitLimit)) {
-        failed = 1;
+    uint32_t ephase = 0;  // parity of the b_empty phase awaited on this lap of the ring
+    unsigned failed = 0;
+    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+      TileItem t;
+      if (!tile_item(p, item, t)) continue;
+      if (*abort_flag) break;
+      // A buffer ab is free once the MMAs of its previous item completed
+      const int ab = NAB == 2 ? (i & 1) : 0, ua = NAB == 2 ? (i >> 1) : i;
+      if (ua > 0 && !mbar_wait_warp(smem_u32(&a_empty[ab]), (uint32_t)((ua - 1) & 1), kWaitLimit)) {
+        failed = kGaveUpAEmpty;
         break;
       }
-      const uint32_t fb = smem_u32(&full[st]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                   "r"(row_bytes)
-                   : "memory");
-      asm volatile(
-          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-          "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(bbase + (uint32_t)(st * L.stageB)),
-          "l"(&tmB), "r"(0), "r"(kc0), "r"(kr0), "r"(ty), "r"(fb)
-          : "memory");
-      if (++st == NST) {
-        st = 0;
-        if (ty >= NST) eparity ^= 1u;  // the first lap waits on nothing
+      // A rows Y0 .. Y0+rows-1, positions r = 0..7 of the tile's row: the
+      // TWK taps from column X0 + r, i.e. row r of phase image r (an 8-row
+      // group is one image row)
+      tma_expect(smem_u32(&a_full[ab]), (uint32_t)(L.rows * L.grp));
+      tma_load_3d(smem_u32(abuf + (size_t)ab * L.abytes), &tmA, t.X0, 0, t.Y0,
+                  smem_u32(&a_full[ab]));
+      ++i;
+      // B stages: operand row j (template rows SUB*j ..) of every POI of
+      // the block, the ncols_max x nrows_max patch of the bank landing as
+      // operand rows n = bi * ncols_max + bj of 64 taps
+      for (int j = 0; j < p.sj; ++j) {
+        if (gs >= NST && !mbar_wait_warp(smem_u32(&b_empty[st]), ephase, kWaitLimit)) {
+          failed = kGaveUpBEmpty;
+          break;
+        }
+        const uint32_t fb = smem_u32(&b_full[st]);
+        tma_expect(fb, (uint32_t)(nblock * kRowB));
+        tma_load_4d(smem_u32(bbuf + (size_t)st * L.stageB), &tmB, 0, t.kc0, t.kr0, j, fb);
+        ++gs;
+        if (++st == NST) {
+          st = 0;
+          if (gs > NST) ephase ^= 1u;  // the first lap waits on nothing
+        }
       }
     }
-  } else if (tid == 32) {
-    // ---- MMA issuer.  Descriptors are built once and advanced by adding
-    // (byte offset >> 4) to their start-address field; stage, phase and
-    // accumulator indices advance incrementally (no divisions in the loop).
+    if (failed && lane == 0) give_up(failed);
+    __syncwarp();
+    if (*abort_flag) {
+      // let the copies still in flight land (bounded) before the CTA leaves
+      for (int g = max(0, gs - NST); g < gs; ++g)
+        mbar_wait_warp(smem_u32(&b_full[g % NST]), (uint32_t)((g / NST) & 1), kWaitLimit / 16);
+      for (int k = max(0, i - NAB); k < i; ++k) {
+        const int ab = NAB == 2 ? (k & 1) : 0, ua = NAB == 2 ? (k >> 1) : k;
+        mbar_wait_warp(smem_u32(&a_full[ab]), (uint32_t)(ua & 1), kWaitLimit / 16);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: the whole warp runs the loop, one elected lane issues
+    // each MMA and commit.  Descriptors are advanced by adding (byte offset
+    // >> 4) to their start-address field.  MMA k of a stage covers taps
+    // 16k .. 16k+15 of the B row: template row ty = SUB*j + k / KPR, taps
+    // 16 (k % KPR) .. of A's image row Y0 + q + ty; the MMAs of template rows
+    // at or beyond S are not issued.
     const uint32_t idesc = make_idesc(128, NP);
-    const uint64_t ad0 = make_desc(smem_u32(abuf), L.RB);
-    const uint64_t bd0 = make_desc(smem_u32(bbuf), L.RB);
+    const uint64_t bd0 = make_desc(smem_u32(bbuf), kRowB);
     const uint32_t a_step = (uint32_t)L.grp >> 4, b_step = (uint32_t)L.stageB >> 4;
-    if (!mbar_wait(smem_u32(abar), 0, kWaitLimit)) failed = 1;
-    int st = 0, rin = 0;
-    uint32_t fparity = 0, dcol = tmem;
-    uint64_t ad_row = ad0, bd_st = bd0;
-    for (int ty = 0; ty < S && !failed; ++ty) {
-      if (!mbar_wait(smem_u32(&full[st]), fparity, kWaitLimit)) {
-        failed = 1;
+    const int SUB = p.sub;
+    int i = 0, st = 0;
+    uint32_t fphase = 0;
+    uint64_t bd_st = bd0;
+    unsigned failed = 0;
+    for (int item = blockIdx.x; item < nitems && !failed; item += gridDim.x) {
+      TileItem t;
+      if (!tile_item(p, item, t)) continue;
+      if (*abort_flag) break;
+      const int b = NACB == 2 ? (i & 1) : 0, ub = NACB == 2 ? (i >> 1) : i;
+      const int ab = NAB == 2 ? (i & 1) : 0, ua = NAB == 2 ? (i >> 1) : i;
+      // the epilogue has read this accumulator buffer's previous item
+      if (ub > 0 &&
+          !mbar_wait_warp(smem_u32(&acc_empty[b]), (uint32_t)((ub - 1) & 1), kWaitLimit)) {
+        failed = kGaveUpAccEmpty;
+        break;
+      }
+      if (!mbar_wait_warp(smem_u32(&a_full[ab]), (uint32_t)(ua & 1), kWaitLimit)) {
+        failed = kGaveUpAFull;
+        break;
+      }
+      const uint64_t ad0 = make_desc(smem_u32(abuf + (size_t)ab * L.abytes), L.RB);
+      const uint32_t dbase = tmem + (uint32_t)b * bufcols;
+      // template row ty, its accumulator (dcol) and row within it (rin),
+      // advanced by counters (no divisions on the issue path)
+      int ty = 0, rin = 0;
+      uint32_t dcol = dbase;
+      uint64_t ad_row = ad0;
+      for (int j = 0; j < p.sj; ++j) {
+        if (!mbar_wait_warp(smem_u32(&b_full[st]), fphase, kWaitLimit)) {
+          failed = kGaveUpBFull;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (SUB == 4)
+          issue_stage<4>(dcol, ad_row, bd_st, ty, rin, S, rows_per_acc, a_step, (uint32_t)NP, idesc);
+        else if (SUB == 2)
+          issue_stage<2>(dcol, ad_row, bd_st, ty, rin, S, rows_per_acc, a_step, (uint32_t)NP, idesc);
+        else
+          issue_stage<1>(dcol, ad_row, bd_st, ty, rin, S, rows_per_acc, a_step, (uint32_t)NP, idesc);
+        umma_commit(smem_u32(&b_empty[st]));  // the stage is free once these complete
+        if (++st == NST) {
+          st = 0;
+          fphase ^= 1u;
+          bd_st = bd0;
+        } else {
+          bd_st += b_step;
+        }
+      }
+      if (failed) break;
+      umma_commit(smem_u32(&a_empty[ab]));
+      umma_commit(smem_u32(&acc_full[b]));
+      ++i;
+    }
+    if (failed && lane == 0) give_up(failed);
+    // every MMA issued so far has completed before the CTA leaves
+    umma_commit(smem_u32(done));
+    if (!mbar_wait_warp(smem_u32(done), 0, kWaitLimit) && lane == 0) give_up(kGaveUpDone);
+  } else {
+    // ---- epilogue warps
+    const int et = tid - 64;                       // 0 .. kEpiThreads-1
+    const int quarter = warp & 3;                  // TMEM lane quarter of this warp
+    const int grp = (warp - 2) >> 2;               // 0 .. kEpiGroups-1
+    const int wide = nacc > 1;
+    const int ow = 2 * R + 1;
+    const float Nf = (float)N;
+    const int B = p.M + R + 2;
+    // box sums of an item's positions (thread et < kPos) and of its POI et
+    // (et < NP; kEpiThreads >= 256 >= NP), loaded one item ahead
+    static_assert(kEpiThreads >= 256, "one POI of a block per epilogue thread");
+    auto next_item = [&](int item, TileItem& t) {
+      while (item < nitems && !tile_item(p, item, t)) item += gridDim.x;
+      return item;
+    };
+    auto load_sums_of = [&](const TileItem& t, int2& pb, int2& fb) {
+      pb = make_int2(0, 0);
+      fb = make_int2(0, 0);
+      if (et < kPos)
+        pb = p.posbox[(size_t)(t.Y0 - p.ymin + et / kTileR) * (p.ntx * 8) +
+                      (t.X0 - p.xmin + et % kTileR)];
+      int bi, bj;
+      block_poi(p, et, bi, bj);
+      if (et < nblock && bi < t.nbr && bj < t.nbc) {
+        const int xl = B + (t.kc0 + bj) * p.step - p.M, yl = B + (t.kr0 + bi) * p.step - p.M;
+        fb = p.fbox[(size_t)(yl - p.ymin) * (p.ntx * 8) + (xl - p.xmin)];
+      }
+    };
+    int i = 0;
+    TileItem t;
+    int item = next_item(blockIdx.x, t);
+    int2 pb_next, fb_next;
+    if (item < nitems) load_sums_of(t, pb_next, fb_next);
+    while (item < nitems) {
+      const int X0 = t.X0, Y0 = t.Y0, kc0 = t.kc0, kr0 = t.kr0;
+      const int b = NACB == 2 ? (i & 1) : 0, ub = NACB == 2 ? (i >> 1) : i;
+      // ---- per-position box statistics and per-POI window / sums
+      if (et < kPos) {
+        const int2 bx = pb_next;
+        const long long dg = N * (long long)bx.y - (long long)bx.x * bx.x;
+        pdg[et] = dg;
+        psb[et] = bx.x;
+        pinv[et] = dg ? 1.0f / ll_to_float(dg) : 0.f;
+      }
+      if (et < NP) {
+        int bi, bj;
+        block_poi(p, et, bi, bj);
+        PoiInfo pi{kNoPoi, kNoPoi, 0.f, 0};
+        const int2 fb = fb_next;
+        // a POI without reference variance is decided by the reduce kernel
+        if (et < nblock && bi < t.nbr && bj < t.nbc &&
+            N * (long long)fb.y - (long long)fb.x * fb.x != 0) {
+          const int xl = B + (kc0 + bj) * p.step - p.M, yl = B + (kr0 + bi) * p.step - p.M;
+          pi = PoiInfo{xl - X0 - R, yl - Y0 - R, (float)fb.x, fb.x};
+        }
+        poi[et] = pi;
+      }
+      const int item_next = next_item(item + gridDim.x, t);
+      if (item_next < nitems) load_sums_of(t, pb_next, fb_next);
+      if (et == 0) *nties = 0;
+      // ---- the accumulator of this item
+      const bool got = mbar_wait(smem_u32(&acc_full[b]), (uint32_t)(ub & 1), kWaitLimit);
+      if (epi_any(!got || *abort_flag)) {  // also the barrier before the scores
+        if (!got) give_up(kGaveUpAccFull);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 4
-      for (int j = 0; j < TWK / 16; ++j) {  // 16 taps (32 bytes) per MMA
-        const uint64_t ad = ad_row + (uint64_t)(2 * j), bd = bd_st + (uint64_t)(2 * j);
-        const uint32_t accum = (rin == 0 && j == 0) ? 0u : 1u;
-        asm volatile(
-            "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(dcol),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-            : "memory");
+      const uint32_t tbuf = tmem + (uint32_t)b * bufcols;
+      // ---- scores: each warp takes its lane quarter (32 positions) and
+      // every kEpiGroups-th 16-column block of POIs
+      __syncwarp();
+      {
+        const int m = quarter * 32 + lane, q = m / kTileR, r = m % kTileR;
+        const int rr = pdg[m] != 0 ? r : r + (1 << 21);  // Dg = 0: in no window
+        const float pinv_m = pinv[m];
+        const int sb = psb[m];
+        const float sbf = (float)sb;
+        for (int c0 = grp * 16; c0 < NP; c0 += kEpiGroups * 16) {
+          if (wide)
+            score_block<true>(p, tbuf, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, red);
+          else
+            score_block<false>(p, tbuf, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, red);
+        }
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&empty[st]))
-          : "memory");
-      ad_row += a_step;
-      if (++st == NST) {
-        st = 0;
-        fparity ^= 1u;
-        bd_st = bd0;
-      } else {
-        bd_st += b_step;
+      epi_sync();
+      // ---- per-POI winner of the tile: merge the four quarters' best two.
+      // The float winner is the exact winner if its magnitude exceeds 1e-8
+      // and it clears the second by 5e-4 of that magnitude: float scores err
+      // by less than 1.5e-4 (relative) where num != 0, and by less than 4e-9
+      // where num = 0, so the exact order of the two cannot differ.
+      // Otherwise (a near tie) the POI's positions whose float score is
+      // within 5e-4 (+1e-8) of the best are compared exactly, lowest linear
+      // index on ties; no position outside that band can be the tile's
+      // maximum.
+      auto cand_at = [&](const PoiInfo& pi, int raw, int m) {
+        const int sab = wide ? raw : __float2int_rn(__int_as_float(raw));
+        return Cand{N * (long long)sab - (long long)pi.sa * psb[m], pdg[m],
+                    (m / kTileR - pi.cy) * ow + (m % kTileR - pi.cx)};
+      };
+      auto write_slot = [&](const PoiInfo& pi, int n, const Cand& best) {
+        int bi, bj;
+        block_poi(p, n, bi, bj);
+        const int64_t poi_k = (int64_t)(kr0 + bi) * p.nx + (kc0 + bj);
+        const int xl = pi.cx + X0 + R, yl = pi.cy + Y0 + R;
+        // slot of this tile among the POI's tiles
+        const int tx_first = (xl - R - p.xmin) / kTileR, ty_first = (yl - R - p.ymin) / kTileQ;
+        const int slot = ((Y0 - p.ymin) / kTileQ - ty_first) * p.slots_x +
+                         ((X0 - p.xmin) / kTileR - tx_first);
+        SlotCand* s = p.slots + (size_t)poi_k * p.nslots + slot;
+        s->num = best.num;
+        s->dg = best.dg;
+        s->l = best.l;
+      };
+      for (int n = et; n < NP; n += kEpiThreads) {
+        const PoiInfo pi = poi[n];
+        if (pi.cx == kNoPoi) continue;
+        int4 r0 = red[n];
+        int mx = r0.x, sc = r0.y, v = r0.z;
+#pragma unroll
+        for (int qq = 1; qq < 4; ++qq) {
+          const int4 rq = red[qq * NP + n];
+          sc = max(max(sc, rq.y), min(mx, rq.x));
+          if (rq.x > mx) {
+            mx = rq.x;
+            v = rq.z;
+          }
+        }
+        if (mx == INT_MIN) {
+          write_slot(pi, n, Cand{0, 1, INT_MAX});
+          continue;
+        }
+        const float fm = key2f(mx);
+        if (fabsf(fm) > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 5e-4f * fabsf(fm))) {
+          write_slot(pi, n, cand_at(pi, v, mx & 127));
+        } else {
+          const int k = atomicAdd(nties, 1);
+          ties[k] = make_int2(n, __float_as_int(fm - 5e-4f * fabsf(fm) - 1e-8f));
+        }
       }
-      if (++rin == rows_per_acc) {
-        rin = 0;
-        dcol += (uint32_t)NP;
+      epi_sync();
+      // ---- near ties: the warps of lane group grp take every kEpiGroups-th
+      // tie, each warp its quarter's positions, reading the sums of the
+      // tie's column back from TMEM
+      const int ntie = *nties;
+      __syncwarp();
+      for (int k = grp; k < ntie; k += kEpiGroups) {
+        const int n = ties[k].x;
+        const float thr = __int_as_float(ties[k].y);
+        const PoiInfo pi = poi[n];
+        int raw = 0;
+        for (int a = 0; a < nacc; ++a) {
+          uint32_t v;
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                       : "=r"(v)
+                       : "r"(tbuf + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * NP + n)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          raw = wide ? raw + __float2int_rn(__uint_as_float(v)) : (int)v;
+        }
+        const int m = quarter * 32 + lane, q = m / kTileR, r = m % kTileR;
+        Cand best{0, 1, INT_MAX};
+        if ((unsigned)(r - pi.cx) <= (unsigned)(2 * R) && (unsigned)(q - pi.cy) <= (unsigned)(2 * R) &&
+            pdg[m] != 0) {
+          float nf;
+          if (wide) {
+            nf = ll_to_float(N * (long long)raw - (long long)pi.sa * psb[m]);
+          } else {
+            const float sbf = (float)psb[m], hi = pi.saf * sbf, lo = fmaf(pi.saf, sbf, -hi);
+            nf = fmaf(Nf, __int_as_float(raw), -hi) - lo;
+          }
+          if (nf * fabsf(nf) * pinv[m] >= thr) best = cand_at(pi, raw, m);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          Cand d;
+          d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
+          d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
+          d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
+          if (cand_better(d, best)) best = d;
+        }
+        if (lane == 0) tcand[k * 4 + quarter] = TieCand{best.num, best.dg, best.l, 0};
       }
-    }
-    // every MMA issued so far (all of them, or those before a failure)
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(done))
-        : "memory");
-    if (!mbar_wait(smem_u32(done), 0, kWaitLimit)) failed = 1;
-  }
-  const bool ok = !__syncthreads_or(failed);
-  if (!ok && tid == 0) {
-    atomicOr(p.err_flag, 2u);
-    // let the copies still in flight land (bounded) before the CTA leaves
-    mbar_wait(smem_u32(abar), 0, kWaitLimit / 16);
-    for (int j = max(0, issued - NST); j < issued; ++j)
-      mbar_wait(smem_u32(&full[j % NST]), (uint32_t)((j / NST) & 1), kWaitLimit / 16);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  // ---- scores: each warp takes one lane quarter of the accumulator (32
-  // positions) and 16-column blocks of POIs; sums also go to shared memory,
-  // transposed (dsm[n][m]), for the exact winner
-  const int nacc = (S + rows_per_acc - 1) / rows_per_acc;
-  if (ok) {
-    const int quarter = warp & 3, m = quarter * 32 + lane, q = m / kTileR, r = m % kTileR;
-    const int rr = pdg[m] != 0 ? r : r + (1 << 21);  // Dg = 0: in no window
-    const float pinv_m = pinv[m];
-    const int sb = psb[m];
-    const float sbf = (float)sb;
-    for (int c0 = (warp >> 2) * 16; c0 < NP; c0 += (kThreads / 128) * 16) {
-      if (nacc > 1)
-        score_block<true>(p, tmem, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, dsm, red);
-      else
-        score_block<false>(p, tmem, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, dsm,
-                           red);
+      // the buffer's last TMEM read is done: release it to the MMA issuer
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      epi_sync();
+      if (et == 0) mbar_arrive(smem_u32(&acc_empty[b]));
+      for (int k = et; k < ntie; k += kEpiThreads) {
+        const int n = ties[k].x;
+        Cand best{0, 1, INT_MAX};
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const TieCand c = tcand[k * 4 + qq];
+          const Cand d{c.num, c.dg, c.l};
+          if (cand_better(d, best)) best = d;
+        }
+        write_slot(poi[n], n, best);
+      }
+      epi_sync();  // smem of this item is free for the next
+      ++i;
+      item = item_next;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
+    __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)p.tmem_cols)
                  : "memory");
-  }
-  if (!ok) return;
-
-  // ---- per-POI winner of the tile: merge the four quarters' best two.  The
-  // float winner is the exact winner if it is positive above 1e-8 and clears
-  // the second by 5e-4 (relative): float scores err by less than 1.5e-4 and
-  // num != 0 there.  Otherwise (a near tie) one warp compares exactly the
-  // POI's positions whose float score is within 5e-4 (+1e-8) of the best,
-  // lowest linear index on ties; no position outside that band can be the
-  // tile's maximum.
-  const int wide = nacc > 1;
-  const int ow = 2 * R + 1;
-  const float Nf = (float)N;
-  auto exact = [&](const PoiInfo& pi, int n, int m) {
-    const int raw = dsm[n * kDs + m];
-    const int sab = wide ? raw : __float2int_rn(__int_as_float(raw));
-    return Cand{N * (long long)sab - (long long)pi.sa * psb[m], pdg[m],
-                (m / kTileR - pi.cy) * ow + (m % kTileR - pi.cx)};
-  };
-  auto write_slot = [&](const PoiInfo& pi, int n, const Cand& best) {
-    int bi, bj;
-    block_poi(p, n, bi, bj);
-    const int64_t poi_k = (int64_t)(kr0 + bi) * p.nx + (kc0 + bj);
-    const int xl = pi.cx + X0 + R, yl = pi.cy + Y0 + R;
-    // slot of this tile among the POI's tiles
-    const int tx_first = (xl - R - p.xmin) / kTileR, ty_first = (yl - R - p.ymin) / kTileQ;
-    const int slot = ((Y0 - p.ymin) / kTileQ - ty_first) * p.slots_x +
-                     ((X0 - p.xmin) / kTileR - tx_first);
-    SlotCand* s = p.slots + (size_t)poi_k * p.nslots + slot;
-    s->num = best.num;
-    s->dg = best.dg;
-    s->l = best.l;
-  };
-  for (int n = tid; n < NP; n += kThreads) {
-    const PoiInfo pi = poi[n];
-    if (pi.cx == kNoPoi) continue;
-    int mx = red[n].x, sc = red[n].y;
-#pragma unroll
-    for (int qq = 1; qq < 4; ++qq) merge2(mx, sc, red[qq * NP + n].x, red[qq * NP + n].y);
-    if (mx == INT_MIN) {
-      write_slot(pi, n, Cand{0, 1, INT_MAX});
-      continue;
-    }
-    const float fm = key2f(mx);
-    if (fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 5e-4f * fm)) {
-      write_slot(pi, n, exact(pi, n, mx & 127));
-    } else {
-      const int k = atomicAdd(nties, 1);
-      ties[k] = make_int2(n, __float_as_int(fm - 5e-4f * fabsf(fm) - 1e-8f));
-    }
-  }
-  __syncthreads();
-  for (int k = warp; k < *nties; k += kThreads / 32) {
-    const int n = ties[k].x;
-    const float thr = __int_as_float(ties[k].y);
-    const PoiInfo pi = poi[n];
-    Cand best{0, 1, INT_MAX};
-    for (int m = lane; m < kPos; m += 32) {
-      const int q = m / kTileR, r = m % kTileR;
-      if ((unsigned)(r - pi.cx) > (unsigned)(2 * R) || (unsigned)(q - pi.cy) > (unsigned)(2 * R) ||
-          pdg[m] == 0)
-        continue;
-      const int raw = dsm[n * kDs + m];
-      float nf;
-      if (wide) {
-        nf = ll_to_float(N * (long long)raw - (long long)pi.sa * psb[m]);
-      } else {
-        const float sbf = (float)psb[m], hi = pi.saf * sbf, lo = fmaf(pi.saf, sbf, -hi);
-        nf = fmaf(Nf, __int_as_float(raw), -hi) - lo;
-      }
-      if (nf * fabsf(nf) * pinv[m] < thr) continue;
-      const Cand c = exact(pi, n, m);
-      if (cand_better(c, best)) best = c;
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      Cand d;
-      d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
-      d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
-      d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
-      if (cand_better(d, best)) best = d;
-    }
-    if (lane == 0) write_slot(pi, n, best);
   }
 }
 
 // ------------------------------------------------------------ final reduce
 // One warp per POI.  Each slot holds the exact winner of one tile (or no
 // candidate).  Lanes score their slots in float from the exact sums (error
-// below 1e-6 plus 2^-13 from the slot index packed into the key) and the
-// warp keeps the best two; if the best is positive above 1e-8 and clears the
-// second by 1e-3 it is the POI's winner, otherwise the slots within 2e-3
-// (+1e-8) of the best are compared exactly, lowest linear index on ties.
+// below 1e-6 plus 2^-13 from the slot index packed into the key, relative;
+// exactly 0 where num = 0) and the warp keeps the best two; if the best's
+// magnitude exceeds 1e-8 and it clears the second by 1e-3 of that magnitude
+// it is the POI's winner, otherwise the slots within 2e-3 (+1e-8) of the
+// best are compared exactly, lowest linear index on ties.
 __device__ __forceinline__ float cand_score(long long num, long long dg) {
   const float n = ll_to_float(num);
   return n * fabsf(n) / ll_to_float(dg);  // sign(C) C^2 Df
@@ -814,7 +1085,7 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   Cand best{0, 1, INT_MAX};
   if (mx != INT_MIN) {
     const float fm = key2f(mx);
-    if (fm > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fm)) {
+    if (fabsf(fm) > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fabsf(fm))) {
       const SlotCand w = sl[mx & (kMaxSlots - 1)];
       best = Cand{w.num, w.dg, w.l};
     } else {
@@ -864,7 +1135,9 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->nx = nx;
   g->ny = ny;
   if (S > 64) return false;
-  g->twk = S <= 16 ? 16 : S <= 32 ? 32 : 64;  // one swizzle width per operand row
+  g->twk = S <= 16 ? 16 : S <= 32 ? 32 : 64;  // one swizzle width per A operand row
+  g->sub = 64 / g->twk;
+  g->sj = (S + g->sub - 1) / g->sub;
   if (nx == 0 || ny == 0) return false;
   // exact FP32 sums: at most 1024 nonzero products of |ab| <= 2^14 per
   // accumulator (taps at or beyond S are zero in the bank)
@@ -884,20 +1157,23 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->nchunk = (nrows_all + rmax - 1) / rmax;
   g->nrows_max = (nrows_all + g->nchunk - 1) / g->nchunk;
   g->npad = npad_of(g->nrows_max);
+  // two TMEM accumulator buffers where they fit in 512 columns, else one
+  g->accbufs = 2 * nacc * g->npad <= 512 ? 2 : 1;
   int cols = 32;
-  while (cols < nacc * g->npad) cols *= 2;
+  while (cols < g->accbufs * nacc * g->npad) cols *= 2;
   if (cols > 512) return false;
   g->tmem_cols = cols;
-  // template-row stages: as many as fit beside the A buffer inside the
-  // region the transposed sums need anyway (at least 3, fewer only if the
-  // shared memory would not hold them)
+  // two A buffers where they fit beside at least two B stages, then as many
+  // B stages as fit (one CTA per SM)
   {
-    const int rows = kTileQ + S - 1;
-    const size_t abuf = (size_t)rows * 16 * g->twk, stage = (size_t)2 * g->twk * g->npad;
-    const size_t dd = (size_t)g->npad * kDs * 4;
-    int st = 3;
-    while (st < kMaxStages && abuf + (st + 1) * stage <= dd) ++st;
-    while (st > 2 && tile_layout(S, g->twk, g->npad, st).total > 227 * 1024) --st;
+    auto fits = [&](int st, int ab) {
+      return tile_layout(S, g->twk, g->npad, st, ab).total <= 227 * 1024;
+    };
+    if (fits(2, 2)) g->abufs = 2;
+    else if (fits(2, 1)) g->abufs = 1;
+    else return false;
+    int st = 2;
+    while (st < kMaxStages && fits(st + 1, g->abufs)) ++st;
     g->stages = st;
   }
   g->arows = kTileQ + S - 1;
@@ -911,8 +1187,14 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->slots_y = (2 * R + kTileQ - 1) / kTileQ + 1;
   g->nslots = g->slots_x * g->slots_y;
   if (g->nslots > kMaxSlots) return false;  // slot index packed in 10 bits by the reduce
-  // template bank offsets are 32-bit element counts
-  if ((double)nx * ny * S * g->twk >= 4294967296.0) return false;
+  // template bank: by image row where that is the smaller order (the
+  // caller switches to the stacked order if the tensor map encoder refuses
+  // the overlapping strides)
+  {
+    const long long over = (long long)(ny - 1) * step + (long long)g->sub * g->sj;
+    const long long stacked = (long long)ny * g->sj;
+    if (!search_tc_bank_order(g, over < stacked ? 1 : 0)) return false;
+  }
   // phase images cover every A row / column a tile touches and every
   // template row, with room for an 8-column chunk past the last tap
   const int wneed = std::max(W, g->xmin + g->ntx * kTileR + g->twk + 16);
@@ -920,20 +1202,29 @@ bool search_tc_geometry(int W, int H, int S, int step, int R, int nx, int ny, Se
   g->phw = (wneed + 7) / 8 * 8;
   g->phh = hneed;
   // grid rows of the bank launch, 32-bit chunk indices of the phase images
-  if (g->phh > 65535 || (long long)ny * S > 65535 ||
-      (long long)g->phh * g->phw >= (1ll << 31))
+  if (g->phh > 65535 || (long long)g->phh * g->phw >= (1ll << 31))
     return false;
   return true;
 }
 
 size_t search_tc_smem(const SearchTcParams& g) {
-  return tile_layout(g.S, g.twk, g.npad, g.stages).total;
+  return tile_layout(g.S, g.twk, g.npad, g.stages, g.abufs).total;
 }
 
 size_t search_tc_gph_elems(const SearchTcParams& g) { return (size_t)8 * g.phh * g.phw; }
 
 size_t search_tc_phase_elems(const SearchTcParams& g) {
-  return search_tc_gph_elems(g) + (size_t)g.nx * g.ny * g.S * g.twk;
+  return search_tc_gph_elems(g) + (size_t)g.bank_rows * g.nx * 64;
+}
+
+bool search_tc_bank_order(SearchTcParams* g, int overlap) {
+  const long long rows = overlap ? (long long)(g->ny - 1) * g->step + (long long)g->sub * g->sj
+                                 : (long long)g->ny * g->sj;
+  // grid rows of the bank launch; bank of at most 2^32 elements
+  if (rows > 65535 || (double)rows * g->nx * 64 >= 4294967296.0) return false;
+  g->bank_overlap = overlap;
+  g->bank_rows = (int)rows;
+  return true;
 }
 
 size_t search_tc_posbox_elems(const SearchTcParams& g) {
@@ -959,8 +1250,8 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   {
     const int chunks = 8 * p.phh * (p.phw / 8);  // 16-byte chunks of the phase images
     phase_kernel<<<(chunks + 255) / 256, 256, 0, st>>>(p);
-    const int per_row = p.nx * (p.twk / 8);
-    bank_kernel<<<dim3((per_row + 127) / 128, p.ny * p.S), 128, 0, st>>>(p);
+    const int per_row = p.nx * 8;  // 16-byte chunks of a bank row
+    bank_kernel<<<dim3((per_row + 127) / 128, p.bank_rows), 128, 0, st>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -984,8 +1275,12 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   // geometries, each checked against the attribute when the graph runs
   e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
-  tile_kernel<<<dim3((unsigned)(p.ntx * p.nty), (unsigned)p.nchunk), kThreads, smem, st>>>(
-      p, *tmA, *tmB);
+  int dev = 0, nsm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int nitems = p.ntx * p.nty * p.nchunk;
+  tile_kernel<<<(unsigned)std::max(1, std::min(nitems, nsm)), kThreads, smem, st>>>(p, *tmA, *tmB);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_kernel<<<wblocks, 256, 0, st>>>(p);
