@@ -325,6 +325,7 @@ constexpr unsigned kGaveUpAccFull = 1u << 9;   // epilogue: accumulator complete
 constexpr unsigned kGaveUpDone = 1u << 10;     // MMA: last MMAs complete
 
 constexpr int kRowB = 128;  // bytes of a B operand row (64 taps): its swizzle width
+constexpr int kTieRound = 32;  // near ties resolved per round (rare: well under 1 %)
 constexpr int kPos = kTileQ * kTileR;  // positions per tile (the MMA's M)
 
 struct TileLayout {
@@ -359,7 +360,7 @@ __host__ __device__ inline TileLayout tile_layout(int S, int TWK, int npad, int 
   L.off_poi = o;  o += (size_t)npad * 16;                    // per-POI window and sums
   L.off_red = o;  o += (size_t)4 * npad * 16;                // per-quarter best two + sum
   L.off_tie = o;  o += (size_t)npad * 8;                     // near-tie list
-  L.off_tc = o;   o += (size_t)4 * npad * sizeof(TieCand);   // per-quarter tie winners
+  L.off_tc = o;   o += (size_t)4 * kTieRound * sizeof(TieCand);  // per-quarter tie winners
   o = al(o, 1024);  // swizzle atoms of the operands start on 1024-byte boundaries
   L.off_a = o;    o += (size_t)abufs * L.abytes;
   L.off_b = o;    o += (size_t)stages * L.stageB;
@@ -963,62 +964,68 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       epi_sync();
-      // ---- near ties: the warps of lane group grp take every kEpiGroups-th
-      // tie, each warp its quarter's positions, reading the sums of the
-      // tie's column back from TMEM
+      // ---- near ties, kTieRound at a time: the warps of lane group grp
+      // take every kEpiGroups-th tie, each warp its quarter's positions,
+      // reading the sums of the tie's column back from TMEM; then one
+      // thread per tie merges the four quarters' candidates
       const int ntie = *nties;
-      __syncwarp();
-      for (int k = grp; k < ntie; k += kEpiGroups) {
-        const int n = ties[k].x;
-        const float thr = __int_as_float(ties[k].y);
-        const PoiInfo pi = poi[n];
-        int raw = 0;
-        for (int a = 0; a < nacc; ++a) {
-          uint32_t v;
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
-                       : "=r"(v)
-                       : "r"(tbuf + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * NP + n)));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          raw = wide ? raw + __float2int_rn(__uint_as_float(v)) : (int)v;
-        }
-        const int m = quarter * 32 + lane, q = m / kTileR, r = m % kTileR;
-        Cand best{0, 1, INT_MAX};
-        if ((unsigned)(r - pi.cx) <= (unsigned)(2 * R) && (unsigned)(q - pi.cy) <= (unsigned)(2 * R) &&
-            pdg[m] != 0) {
-          float nf;
-          if (wide) {
-            nf = ll_to_float(N * (long long)raw - (long long)pi.sa * psb[m]);
-          } else {
-            const float sbf = (float)psb[m], hi = pi.saf * sbf, lo = fmaf(pi.saf, sbf, -hi);
-            nf = fmaf(Nf, __int_as_float(raw), -hi) - lo;
+      for (int base = 0; base < ntie; base += kTieRound) {
+        const int nround = min(kTieRound, ntie - base);
+        __syncwarp();
+        for (int k = grp; k < nround; k += kEpiGroups) {
+          const int n = ties[base + k].x;
+          const float thr = __int_as_float(ties[base + k].y);
+          const PoiInfo pi = poi[n];
+          int raw = 0;
+          for (int a = 0; a < nacc; ++a) {
+            uint32_t v;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                         : "=r"(v)
+                         : "r"(tbuf + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * NP + n)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            raw = wide ? raw + __float2int_rn(__uint_as_float(v)) : (int)v;
           }
-          if (nf * fabsf(nf) * pinv[m] >= thr) best = cand_at(pi, raw, m);
-        }
+          const int m = quarter * 32 + lane, q = m / kTileR, r = m % kTileR;
+          Cand best{0, 1, INT_MAX};
+          if ((unsigned)(r - pi.cx) <= (unsigned)(2 * R) &&
+              (unsigned)(q - pi.cy) <= (unsigned)(2 * R) && pdg[m] != 0) {
+            float nf;
+            if (wide) {
+              nf = ll_to_float(N * (long long)raw - (long long)pi.sa * psb[m]);
+            } else {
+              const float sbf = (float)psb[m], hi = pi.saf * sbf, lo = fmaf(pi.saf, sbf, -hi);
+              nf = fmaf(Nf, __int_as_float(raw), -hi) - lo;
+            }
+            if (nf * fabsf(nf) * pinv[m] >= thr) best = cand_at(pi, raw, m);
+          }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          Cand d;
-          d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
-          d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
-          d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
-          if (cand_better(d, best)) best = d;
+          for (int o = 16; o; o >>= 1) {
+            Cand d;
+            d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
+            d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
+            d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
+            if (cand_better(d, best)) best = d;
+          }
+          if (lane == 0) tcand[k * 4 + quarter] = TieCand{best.num, best.dg, best.l, 0};
         }
-        if (lane == 0) tcand[k * 4 + quarter] = TieCand{best.num, best.dg, best.l, 0};
+        epi_sync();
+        for (int k = et; k < nround; k += kEpiThreads) {
+          const int n = ties[base + k].x;
+          Cand best{0, 1, INT_MAX};
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const TieCand c = tcand[k * 4 + qq];
+            const Cand d{c.num, c.dg, c.l};
+            if (cand_better(d, best)) best = d;
+          }
+          write_slot(poi[n], n, best);
+        }
+        epi_sync();  // tcand is free for the next round
       }
       // the buffer's last TMEM read is done: release it to the MMA issuer
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       epi_sync();
       if (et == 0) mbar_arrive(smem_u32(&acc_empty[b]));
-      for (int k = et; k < ntie; k += kEpiThreads) {
-        const int n = ties[k].x;
-        Cand best{0, 1, INT_MAX};
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          const TieCand c = tcand[k * 4 + qq];
-          const Cand d{c.num, c.dg, c.l};
-          if (cand_better(d, best)) best = d;
-        }
-        write_slot(poi[n], n, best);
-      }
       epi_sync();  // smem of this item is free for the next
       ++i;
       item = item_next;
