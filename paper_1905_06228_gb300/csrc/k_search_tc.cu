@@ -1075,10 +1075,18 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     return;
   }
   const SlotCand* sl = p.slots + (size_t)poi * p.nslots;
-  // an unwritten slot (all bits set) or a tile without a candidate
-  auto valid = [&](int l) { return l >= 0 && l < ow * ow; };
+  // The slots of the tiles that meet the POI's window, (tx, ty) from
+  // (xl - R, yl - R) to (xl + R, yl + R) in tile units: the tile kernel has
+  // written each of them (a winner, or no candidate); the other slots of
+  // the POI's slots_x x slots_y block are never written and never read.
+  const int xl = x0 - M, yl = y0 - M;
+  const int nsx = (xl + R - p.xmin) / kTileR - (xl - R - p.xmin) / kTileR + 1;
+  const int nsy = (yl + R - p.ymin) / kTileQ - (yl - R - p.ymin) / kTileQ + 1;
+  auto used = [&](int s) { return s % p.slots_x < nsx && s / p.slots_x < nsy; };
+  auto valid = [&](int l) { return l >= 0 && l < ow * ow; };  // not "no candidate"
   int mx = INT_MIN, sc = INT_MIN;
   for (int s = lane; s < p.nslots; s += 32) {
+    if (!used(s)) continue;
     const SlotCand c = sl[s];
     if (valid(c.l))
       merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~(kMaxSlots - 1)) | s, INT_MIN);
@@ -1098,6 +1106,7 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     } else {
       const float thr = fm - 2e-3f * fabsf(fm) - 1e-8f;
       for (int s = lane; s < p.nslots; s += 32) {
+        if (!used(s)) continue;
         const SlotCand c = sl[s];
         if (valid(c.l) && cand_score(c.num, c.dg) >= thr) {
           const Cand d{c.num, c.dg, c.l};
@@ -1262,9 +1271,6 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // slots of tiles that meet no position of a POI stay "empty"
-  e = cudaMemsetAsync(p.slots, 0xff, sizeof(SlotCand) * (size_t)p.n_pois * p.nslots, st);
-  if (e != cudaSuccess) return e;
   {
     const size_t bsm = boxmap_smem(p.S);
     if (bsm > 227 * 1024) return cudaErrorInvalidConfiguration;
