@@ -247,6 +247,16 @@ def run_gpu(args):
         if events:
             events[2].record(stream)
 
+    # bounded device waits that gave up in a timed loop (each kernel's wait
+    # records it in the handle's flag; a number taken then is not valid)
+    gave_up = []
+
+    def check_waits(dd, where):
+        try:
+            dic.dic_check(dd.h)
+        except dic.DICError as ex:
+            gave_up.append(f"{where}: {ex}")
+
     def timed_loop(dd, steps, warmup, sampler=None, method=dic.DIC_ICGN):
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -275,6 +285,7 @@ def run_gpu(args):
         search_ms = [a.elapsed_time(b) for a, b, _ in sev]
         sub_ms = [b.elapsed_time(c) for _, b, c in sev]
         conv = int((p_out["status"] == 0).sum().item())
+        check_waits(dd, "timed loop")
         return step_ms, (search_ms, sub_ms), conv, wall, clocks
 
     # clocks: sampled from just before the headline's timed loop to the end of
@@ -411,6 +422,7 @@ def run_gpu(args):
                 h_s[k].copy_(s_out[k], non_blocking=True)
             e_ends[i].record(stream)
     torch.cuda.synchronize(dev)
+    check_waits(d, "e2e loop")
     clocks = sampler.stop()
     clocks["window"] = "headline, forms and e2e timed loops"
     e_ms, e_conv = reduce_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends)) / ek,
@@ -556,6 +568,7 @@ def run_gpu(args):
                           "swarm_searches": pso,
                           "second_order_shape": second_order},
                 "converged_fraction": conv / n, "wall_s_timed": wall,
+                "device_waits_gave_up": gave_up,
                 "sub_records": sub_records}
         print(json.dumps(line))
     d.close()
