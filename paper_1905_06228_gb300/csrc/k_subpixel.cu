@@ -79,12 +79,6 @@ template <>
 __device__ __forceinline__ float rcp_refined<float>(float d) {
   return __frcp_rn(d);
 }
-template <>
-__device__ __forceinline__ double rcp_refined<double>(double d) {
-  double y = (double)__frcp_rn((float)d);
-  y = fma(y, fma(-d, y, 1.0), y);
-  return fma(y, fma(-d, y, 1.0), y);
-}
 
 __device__ __forceinline__ int packed_index(int r, int c) {  // entry (r, c) of a packed lower triangle
   return r >= c ? r * (r + 1) / 2 + c : c * (c + 1) / 2 + r;
@@ -99,6 +93,21 @@ __device__ __forceinline__ void packed_entry(int lane, int& i, int& j) {
   j = min(lane - i * (i + 1) / 2, i);
 }
 
+// Reciprocal of an FP64 pivot 2^-100 <= d < 2^100 with no FP64-pipe
+// conversion (each FP64 instruction is costly on this GPU): an FP32 view of
+// d made from its high word by integer moves (the exponent rebiased, the
+// top 20 mantissa bits), its FP32 reciprocal, widened back to a double
+// exactly by integer moves, then two Newton steps in FP64 (at least 20 ->
+// 40 -> 80 correct bits).
+__device__ __forceinline__ double rcp_pivot(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d);
+  const float df = __uint_as_float((hi << 3) + 0x40000000u);  // exponent - 896
+  const unsigned yb = __float_as_uint(__frcp_rn(df));
+  double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+  y = fma(y, fma(-d, y, 1.0), y);
+  return fma(y, fma(-d, y, 1.0), y);
+}
+
 // Inverse of a symmetric positive definite 6x6 by the symmetric sweep
 // operator, one lane per entry of the lower triangle (lane l < 21 passes
 // its entry h = A_ij, (i, j) from packed_entry).  Pivot k (k = 0..5)
@@ -108,8 +117,12 @@ __device__ __forceinline__ void packed_entry(int lane, int& i, int& j) {
 // symmetric form; the pivots are the successive Schur complements, positive
 // for a positive definite A, so no pivoting is needed).  Each step costs a
 // few instructions for the whole warp, instead of a full factorisation
-// repeated on every lane.  Returns false on every lane if a pivot is not
-// positive and finite; out = (A^-1)_ij on lanes < 21.
+// repeated on every lane.  A lane of row or column k holds a_ik (or a_kj)
+// itself, so its new value a / a_kk is the product of the other operand's
+// selection with 1/a_kk: one multiply per step for every lane.  Returns
+// false on every lane if a pivot is not positive and finite (FP64: not in
+// [2^-100, 2^100), tested on the high word with integer compares);
+// out = (A^-1)_ij on lanes < 21.
 template <typename T>
 __device__ __forceinline__ bool sweep_inverse6(float h, int i, int j, T& out) {
   T a = (T)h;
@@ -119,11 +132,20 @@ __device__ __forceinline__ bool sweep_inverse6(float h, int i, int j, T& out) {
     const T akk = __shfl_sync(0xffffffffu, a, k * (k + 1) / 2 + k);
     const T aik = __shfl_sync(0xffffffffu, a, packed_index(i, k));
     const T ajk = __shfl_sync(0xffffffffu, a, packed_index(j, k));
-    ok = ok && akk > T(0) && akk < T(3e38);
-    const T d = rcp_refined<T>(ok ? akk : T(1));
-    T r = fma(-(aik * d), ajk, a);
-    if (i == k || j == k) r = a * d;
-    if (i == k && j == k) r = -d;
+    T d;
+    if constexpr (sizeof(T) == 8) {
+      const int hk = __double2hiint(akk);
+      ok = ok && hk >= 0x39B00000 && hk < 0x46300000;  // 2^-100 <= akk < 2^100
+      d = rcp_pivot(ok ? akk : 1.0);
+    } else {
+      ok = ok && akk > T(0) && akk < T(3e38);
+      d = rcp_refined<T>(ok ? akk : T(1));
+    }
+    const bool ik = i == k, jk = j == k;
+    const T t = (ik ? ajk : aik) * d;  // a * d on the lanes of row / column k
+    T r = fma(-t, ik ? aik : ajk, a);
+    if (ik || jk) r = t;
+    if (ik && jk) r = -d;
     a = r;
   }
   out = -a;
