@@ -85,6 +85,28 @@ __device__ __forceinline__ float bicubic(const float* __restrict__ img, int W, s
 // Each packed operation rounds every half exactly like its scalar form, so
 // the helpers below give bitwise the results of keys_weights / bicubic /
 // locate.
+// Reciprocal of an FP64 pivot 2^-100 <= d < 2^100 with no FP64-pipe
+// conversion (each FP64 instruction is costly on this GPU): an FP32 view of
+// d made from its high word by integer moves (the exponent rebiased, the
+// top 20 mantissa bits), its FP32 reciprocal, widened back to a double
+// exactly by integer moves, then two Newton steps in FP64 (at least 20 ->
+// 40 -> 80 correct bits).
+__device__ __forceinline__ double rcp_pivot(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d);
+  const float df = __uint_as_float((hi << 3) + 0x40000000u);  // exponent - 896
+  const unsigned yb = __float_as_uint(__frcp_rn(df));
+  double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
+  y = fma(y, fma(-d, y, 1.0), y);
+  return fma(y, fma(-d, y, 1.0), y);
+}
+
+// Pivot test of the FP64 sweeps: 2^-100 <= d < 2^100 (positive, finite and
+// within rcp_pivot's range), from the high word with integer compares.
+__device__ __forceinline__ bool pivot_ok(double d) {
+  const int hk = __double2hiint(d);
+  return hk >= 0x39B00000 && hk < 0x46300000;
+}
+
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
 // Keys weights of both axes at once: w[k] = (weight of tap k-1 along x at

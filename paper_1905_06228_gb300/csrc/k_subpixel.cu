@@ -93,21 +93,6 @@ __device__ __forceinline__ void packed_entry(int lane, int& i, int& j) {
   j = min(lane - i * (i + 1) / 2, i);
 }
 
-// Reciprocal of an FP64 pivot 2^-100 <= d < 2^100 with no FP64-pipe
-// conversion (each FP64 instruction is costly on this GPU): an FP32 view of
-// d made from its high word by integer moves (the exponent rebiased, the
-// top 20 mantissa bits), its FP32 reciprocal, widened back to a double
-// exactly by integer moves, then two Newton steps in FP64 (at least 20 ->
-// 40 -> 80 correct bits).
-__device__ __forceinline__ double rcp_pivot(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d);
-  const float df = __uint_as_float((hi << 3) + 0x40000000u);  // exponent - 896
-  const unsigned yb = __float_as_uint(__frcp_rn(df));
-  double y = __hiloint2double((int)((yb >> 3) + (896u << 20)), (int)(yb << 29));
-  y = fma(y, fma(-d, y, 1.0), y);
-  return fma(y, fma(-d, y, 1.0), y);
-}
-
 // Inverse of a symmetric positive definite 6x6 by the symmetric sweep
 // operator, one lane per entry of the lower triangle (lane l < 21 passes
 // its entry h = A_ij, (i, j) from packed_entry).  Pivot k (k = 0..5)
@@ -134,8 +119,7 @@ __device__ __forceinline__ bool sweep_inverse6(float h, int i, int j, T& out) {
     const T ajk = __shfl_sync(0xffffffffu, a, packed_index(j, k));
     T d;
     if constexpr (sizeof(T) == 8) {
-      const int hk = __double2hiint(akk);
-      ok = ok && hk >= 0x39B00000 && hk < 0x46300000;  // 2^-100 <= akk < 2^100
+      ok = ok && pivot_ok(akk);
       d = rcp_pivot(ok ? akk : 1.0);
     } else {
       ok = ok && akk > T(0) && akk < T(3e38);

@@ -36,12 +36,6 @@ template <>
 __device__ __forceinline__ float rcp2<float>(float d) {
   return __frcp_rn(d);
 }
-template <>
-__device__ __forceinline__ double rcp2<double>(double d) {
-  double y = (double)__frcp_rn((float)d);  // FP32 estimate, two Newton steps
-  y = fma(y, fma(-d, y, 1.0), y);
-  return fma(y, fma(-d, y, 1.0), y);
-}
 
 // (i, j) of packed lower-triangle entry e of a 12 x 12 matrix.
 __device__ __forceinline__ void tri_ij(int e, int& i, int& j) {
@@ -389,16 +383,26 @@ __global__ void __launch_bounds__(32 * kWarps2) subpixel2_kernel(const SubpixelP
 #pragma unroll 1
   for (int k = 0; k < 12; ++k) {
     const TS akk = swp[tri(k, k)];
-    ok = ok && akk > TS(0) && akk < TS(3e38);
-    const TS d = rcp2<TS>(ok ? akk : TS(1));
+    TS d;
+    if constexpr (sizeof(TS) == 8) {  // no FP64 compares or conversions (see rcp_pivot)
+      ok = ok && pivot_ok(akk);
+      d = rcp_pivot(ok ? akk : 1.0);
+    } else {
+      ok = ok && akk > TS(0) && akk < TS(3e38);
+      d = rcp2<TS>(ok ? akk : TS(1));
+    }
     TS nv[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+      // an entry of row or column k is a_ik (a_kj) itself: its new value
+      // a / a_kk is the other operand times 1/a_kk, one multiply
       const int i = ei[c], j = ej[c];
+      const bool ik = i == k, jk = j == k;
       const TS aik = swp[tri(i, k)], ajk = swp[tri(j, k)];
-      TS r = fma(-(aik * d), ajk, av[c]);
-      if (i == k || j == k) r = av[c] * d;
-      if (i == k && j == k) r = -d;
+      const TS t = (ik ? ajk : aik) * d;
+      TS r = fma(-t, ik ? aik : ajk, av[c]);
+      if (ik || jk) r = t;
+      if (ik && jk) r = -d;
       nv[c] = r;
     }
     __syncwarp();
