@@ -14,6 +14,42 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sums over the warp of 8 values per lane, returned to every lane in v.
+// Halving exchanges (xor 16, 8, 4) leave each lane one value's partial sum,
+// two more exchanges complete it, and eight shuffles gather the eight sums:
+// 17 shuffles instead of 40 for eight warp_sum calls.  The additions pair
+// the lanes exactly as warp_sum does (xor 16, 8, 4, 2, 1), so every result
+// equals warp_sum's bit for bit.
+__device__ __forceinline__ void warp_sum8(float (&v)[8], int lane) {
+  float w[4], x[2];
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float send = up ? v[k] : v[k + 4];
+      const float keep = up ? v[k + 4] : v[k];
+      w[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float send = up ? w[k] : w[k + 2];
+      const float keep = up ? w[k + 2] : w[k];
+      x[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  const bool up = lane & 4;
+  float y = (up ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, up ? x[0] : x[1], 4);
+  y += __shfl_xor_sync(0xffffffffu, y, 2);
+  y += __shfl_xor_sync(0xffffffffu, y, 1);
+  // lane l holds the sum of value 4 b16 + 2 b8 + b4 (its bits 16, 8, 4)
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    v[j] = __shfl_sync(0xffffffffu, y, ((j >> 2) & 1) * 16 + ((j >> 1) & 1) * 8 + (j & 1) * 4);
+}
+
 // Sum over the warp of 32 values per lane, scattered: lane l returns the
 // sum of every lane's v[l] (five halving exchanges, 31 shuffles in all).
 __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {

@@ -458,11 +458,15 @@ __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t po
       }
     }
     const float2 a14 = __fmul2_rn(a03, dup2(act ? fdx : 0.f));
-    float acc[6] = {a03.x, a14.x, a25.x, a03.y, a14.y, a25.y};
-    s0s = warp_sum(s0s);
-    s1s = warp_sum(s1s);
+    float acc[6];
+    {
+      float sums[8] = {s0s, s1s, a03.x, a14.x, a25.x, a03.y, a14.y, a25.y};
+      warp_sum8(sums, lane);
+      s0s = sums[0];
+      s1s = sums[1];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
+      for (int k = 0; k < 6; ++k) acc[k] = sums[k + 2];
+    }
     const float gm = s0s * invN;  // gbar - c
     const float var = s1s - s0s * gm;
     const float dg = sqrtf(fmaxf(var, 0.f));
@@ -799,22 +803,27 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
       acc[4] = a14.y;
       acc[5] = a25.y;
     }
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    // FA-NR: the first 32 of its 39 sums by a reduce-scatter (sum k on lane
-    // k: J^T J on lanes 0..20, sum J (g - c) on 21..26, sum J (f - fbar) of
-    // J_0..J_4 on 27..31), the other 7 whole
+    // IC-GN: s0, s1 and the six sums together (warp_sum8).  FA-NR: the
+    // first 32 of its 39 sums by a reduce-scatter (sum k on lane k: J^T J
+    // on lanes 0..20, sum J (g - c) on 21..26, sum J (f - fbar) of J_0..J_4
+    // on 27..31), s0, s1 and six of the other 7 together, the last whole
     float fa_mine = 0.f;
-    if (!FANR) {
+    {
+      const int k0 = FANR ? 32 : 0;
+      float sums[8] = {s0, s1, acc[k0], acc[k0 + 1], acc[k0 + 2], acc[k0 + 3], acc[k0 + 4],
+                       acc[k0 + 5]};
+      if constexpr (FANR) {
+        float v[32];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) acc[k] = warp_sum(acc[k]);
-    } else {
-      float v[32];
+        for (int k = 0; k < 32; ++k) v[k] = acc[k];
+        fa_mine = reduce_scatter32(v, lane);
+        acc[38] = warp_sum(acc[38]);
+      }
+      warp_sum8(sums, lane);
+      s0 = sums[0];
+      s1 = sums[1];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = acc[k];
-      fa_mine = reduce_scatter32(v, lane);
-#pragma unroll
-      for (int k = 32; k < (FANR ? 39 : 6); ++k) acc[k] = warp_sum(acc[k]);
+      for (int k = 0; k < 6; ++k) acc[k0 + k] = sums[k + 2];
     }
     const float gm = s0 * invN;  // gbar - c
     const float var = s1 - s0 * gm;
