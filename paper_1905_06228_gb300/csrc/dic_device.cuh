@@ -347,6 +347,19 @@ __device__ __forceinline__ bool corners_in(const float p[6], int x0, int y0, int
   return ok;
 }
 
+// corners_in for a converged warp: lane l tests corner l & 3 with the same
+// arithmetic, and the warp votes (one corner's instructions per lane
+// instead of four).
+__device__ __forceinline__ bool corners_in_warp(const float p[6], int x0, int y0, int M, int W,
+                                                int H, int lane) {
+  const int c = lane & 3;
+  const float cx = (c & 1) ? (float)M : -(float)M, cy = (c & 2) ? (float)M : -(float)M;
+  const float lx = fmaf(p[2], cy, fmaf(1.f + p[1], cx, p[0]));
+  const float ly = fmaf(1.f + p[5], cy, fmaf(p[4], cx, p[3]));
+  const float x = (float)x0 + lx, y = (float)y0 + ly;
+  const bool ok = (x >= 1.f) && (x < (float)(W - 2)) && (y >= 1.f) && (y < (float)(H - 2));
+  return __all_sync(0xffffffffu, ok);
+}
 
 // float of an exact 64-bit integer without the 64-bit conversion (which runs
 // on the FP64 pipe): sign * (hi * 2^32 + lo) of the magnitude, relative

@@ -410,7 +410,7 @@ __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t po
     write_out(0.f, 0, kSingular);
     return;
   }
-  if (!corners_in(prm, x0, y0, M, W, H)) {
+  if (!corners_in_warp(prm, x0, y0, M, W, H, lane)) {
     write_out(0.f, 0, kOutOfBounds);
     return;
   }
@@ -493,7 +493,7 @@ __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t po
 #pragma unroll
     for (int a = 0; a < 6; ++a) pn[a] = prm[a];
     compose_inverse(pn, dp);
-    if (!corners_in(pn, x0, y0, M, W, H)) {
+    if (!corners_in_warp(pn, x0, y0, M, W, H, lane)) {
       st = kOutOfBounds;
       break;
     }
@@ -684,7 +684,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
     write_out(0.f, 0, kZeroVarRef);
     return;
   }
-  if (!corners_in(prm, x0, y0, M, W, H)) {
+  if (!corners_in_warp(prm, x0, y0, M, W, H, lane)) {
     write_out(0.f, 0, kOutOfBounds);
     return;
   }
@@ -884,7 +884,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
 #pragma unroll
       for (int a = 0; a < 6; ++a) pn[a] += dp[a];
     }
-    if (!corners_in(pn, x0, y0, M, W, H)) {
+    if (!corners_in_warp(pn, x0, y0, M, W, H, lane)) {
       st = kOutOfBounds;
       break;
     }
