@@ -1052,7 +1052,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // best are compared exactly, lowest linear index on ties.
 __device__ __forceinline__ float cand_score(long long num, long long dg) {
   const float n = ll_to_float(num);
-  return n * fabsf(n) / ll_to_float(dg);  // sign(C) C^2 Df
+  return n * fabsf(n) * __frcp_rn(ll_to_float(dg));  // sign(C) C^2 Df
 }
 
 __global__ void reduce_kernel(const SearchTcParams p) {
@@ -1062,6 +1062,19 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   const int S = p.S, M = p.M, R = p.R, ow = 2 * R + 1;
   const int x0 = M + R + 2 + (int)(poi % p.nx) * p.step;
   const int y0 = M + R + 2 + (int)(poi / p.nx) * p.step;
+  const SlotCand* sl = p.slots + (size_t)poi * p.nslots;
+  // The slots of the tiles that meet the POI's window, (tx, ty) from
+  // (xl - R, yl - R) to (xl + R, yl + R) in tile units: the tile kernel has
+  // written each of them (a winner, or no candidate); the other slots of
+  // the POI's slots_x x slots_y block are never written and never read.
+  const int xl = x0 - M, yl = y0 - M;
+  const int nsx = (xl + R - p.xmin) / kTileR - (xl - R - p.xmin) / kTileR + 1;
+  const int nsy = (yl + R - p.ymin) / kTileQ - (yl - R - p.ymin) / kTileQ + 1;
+  auto used = [&](int s) { return s % p.slots_x < nsx && s / p.slots_x < nsy; };
+  auto valid = [&](int l) { return l >= 0 && l < ow * ow; };  // not "no candidate"
+  // the first round of slots is loaded together with the POI's own sums
+  SlotCand c0{0, 1, -1, 0};
+  if (lane < p.nslots && used(lane)) c0 = sl[lane];
   const int2 fb = p.fbox[(size_t)(y0 - M - p.ymin) * (p.ntx * 8) + (x0 - M - p.xmin)];
   const long long N = (long long)S * S;
   const long long Df = N * (long long)fb.y - (long long)fb.x * fb.x;
@@ -1074,18 +1087,10 @@ __global__ void reduce_kernel(const SearchTcParams p) {
     }
     return;
   }
-  const SlotCand* sl = p.slots + (size_t)poi * p.nslots;
-  // The slots of the tiles that meet the POI's window, (tx, ty) from
-  // (xl - R, yl - R) to (xl + R, yl + R) in tile units: the tile kernel has
-  // written each of them (a winner, or no candidate); the other slots of
-  // the POI's slots_x x slots_y block are never written and never read.
-  const int xl = x0 - M, yl = y0 - M;
-  const int nsx = (xl + R - p.xmin) / kTileR - (xl - R - p.xmin) / kTileR + 1;
-  const int nsy = (yl + R - p.ymin) / kTileQ - (yl - R - p.ymin) / kTileQ + 1;
-  auto used = [&](int s) { return s % p.slots_x < nsx && s / p.slots_x < nsy; };
-  auto valid = [&](int l) { return l >= 0 && l < ow * ow; };  // not "no candidate"
   int mx = INT_MIN, sc = INT_MIN;
-  for (int s = lane; s < p.nslots; s += 32) {
+  if (valid(c0.l))
+    merge2(mx, sc, (f2key(cand_score(c0.num, c0.dg)) & ~(kMaxSlots - 1)) | lane, INT_MIN);
+  for (int s = lane + 32; s < p.nslots; s += 32) {
     if (!used(s)) continue;
     const SlotCand c = sl[s];
     if (valid(c.l))
