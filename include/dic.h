@@ -115,9 +115,11 @@ const char *dic_last_error(dic_t h);
  * wait gives up records it in the handle's error flag, waits (bounded) for
  * its own copies in flight and returns, leaving its results incomplete.
  * dic_check synchronises the handle's stream, reads the flag and returns
- * DIC_ERR_TIMEOUT (clearing the flag; which kernel in dic_last_error) if it
- * is set, DIC_OK otherwise (also before any launch); DIC_ERR_CUDA if the
- * stream itself failed.  No counterpart in the paper. */
+ * DIC_ERR_TIMEOUT (clearing the flag; dic_last_error names the kernel and,
+ * for the tensor-core tile kernel, which wait gave up: A buffer free, B
+ * stage free, accumulator read, A landed, B landed, accumulator complete,
+ * last MMAs) if it is set, DIC_OK otherwise (also before any launch);
+ * DIC_ERR_CUDA if the stream itself failed.  No counterpart in the paper. */
 dic_status dic_check(dic_t h);
 
 /* Stream for all later work (a cudaStream_t passed as void*; NULL = default). */
