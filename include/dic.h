@@ -159,7 +159,15 @@ dic_status dic_set_interpolation(dic_t h, dic_interp interp);
  *   pitch_bytes    >= width; both pointers 16-byte aligned and pitch a
  *                  multiple of 16 enable TMA staging, otherwise plain loads
  * Allocates scratch of 20 bytes per pixel on first use or growth
- * (DIC_ERR_OOM on failure). */
+ * (DIC_ERR_OOM on failure).  The precompute runs on a stream of the
+ * handle's own that first waits for everything already queued on the
+ * handle's stream, so that it overlaps the next integer search; it is joined
+ * back into the handle's stream by the first of dic_integer_search,
+ * dic_pso_search, dic_subpixel, dic_subpixel2, dic_znssd, dic_backward and
+ * dic_check, so work queued on the handle's stream after any of them comes
+ * after it.  The images must not be rewritten before such a call.  While
+ * the handle's stream is being captured into a graph the precompute stays on
+ * that stream. */
 dic_status dic_set_pair(dic_t h, const uint8_t *ref_dev, const uint8_t *def_dev,
                         int width, int height, int pitch_bytes);
 

@@ -226,6 +226,9 @@ void dic_destroy(dic_t h) {
   if (h->tc_fbox) cudaFree(h->tc_fbox);
   if (h->tc_slots) cudaFree(h->tc_slots);
   if (h->tc_posbox) cudaFree(h->tc_posbox);
+  if (h->pre_side) cudaStreamDestroy(h->pre_side);
+  if (h->pre_fork) cudaEventDestroy(h->pre_fork);
+  if (h->pre_done) cudaEventDestroy(h->pre_done);
   delete h;
 }
 
@@ -235,8 +238,9 @@ dic_status dic_check(dic_t h) {
   if (!h) return DIC_ERR_ARG;
   if (!h->err_flag) return DIC_OK;  // nothing launched yet
   unsigned int flag = 0;
-  cudaError_t e = cudaMemcpyAsync(&flag, h->err_flag, sizeof flag, cudaMemcpyDeviceToHost,
-                                  h->stream);
+  cudaError_t e = h->pre_pending ? cudaStreamWaitEvent(h->stream, h->pre_done, 0) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&flag, h->err_flag, sizeof flag, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "error-flag read");
   if (flag == 0) return DIC_OK;
@@ -291,6 +295,43 @@ namespace {
 
 // Common part of dic_set_pair / dic_set_pair_f32: geometry, scratch, and the
 // precompute launch.
+// Stream for the pair's precompute: a side stream that first waits for all
+// earlier work on the handle's stream (which may still read the previous
+// pair's gradient and float image), so that the precompute overlaps the
+// integer search.  While the handle's stream is being captured into a graph
+// (or if the side stream cannot be made) it is the handle's stream itself.
+cudaStream_t pre_stream(dic_t h) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return h->stream;
+  }
+  if (!h->pre_side) {
+    if (cudaStreamCreateWithFlags(&h->pre_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->pre_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->pre_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->pre_side) cudaStreamDestroy(h->pre_side);
+      if (h->pre_fork) cudaEventDestroy(h->pre_fork);
+      if (h->pre_done) cudaEventDestroy(h->pre_done);
+      h->pre_side = nullptr;
+      h->pre_fork = h->pre_done = nullptr;
+      return h->stream;
+    }
+  }
+  if (cudaEventRecord(h->pre_fork, h->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(h->pre_side, h->pre_fork, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return h->stream;
+  }
+  return h->pre_side;
+}
+
+// The handle's stream waits for the current pair's precompute.
+cudaError_t pre_join(dic_t h) {
+  return h->pre_pending ? cudaStreamWaitEvent(h->stream, h->pre_done, 0) : cudaSuccess;
+}
+
 dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int width, int height,
                      int pitch) {
   if (!h) return DIC_ERR_ARG;
@@ -335,13 +376,15 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
   h->g.ny = ny;
   h->g.n_pois = (int64_t)nx * ny;
   cudaError_t e;
+  h->pre_pending = false;
+  const cudaStream_t pst = pre_stream(h);
   if (f32) {
     h->ref = h->def = nullptr;
     h->ref_f32 = static_cast<const float*>(ref);
     h->def_f32 = static_cast<const float*>(def);
     h->tma_ok = false;
     e = dic::launch_precompute_f32(h->ref_f32, h->def_f32, width, height, pitch, h->grad, h->gimg,
-                                   h->stream);
+                                   pst);
   } else {
     h->ref_f32 = h->def_f32 = nullptr;
     h->ref = static_cast<const uint8_t*>(ref);
@@ -354,9 +397,14 @@ dic_status bind_pair(dic_t h, const void* ref, const void* def, bool f32, int wi
                 encode_u8(&h->tm_def, h->def, width, height, pitch, bwg, span) &&
                 encode_u8(&h->tm_ref, h->ref, width, height, pitch, bwf, h->subset);
     e = dic::launch_precompute(h->ref, h->def, width, height, pitch, h->grad, h->gimg, h->gq,
-                               h->stream);
+                               pst);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "precompute launch");
+  if (pst != h->stream) {
+    e = cudaEventRecord(h->pre_done, pst);
+    if (e != cudaSuccess) return cuda_fail(h, e, "precompute event");
+    h->pre_pending = true;
+  }
   h->have_pair = true;
   return DIC_OK;
 }
@@ -371,6 +419,7 @@ dic_status run_adjoint(dic_t h, const float* p6, float* loss_poi, float* loss_to
   if (backward)
     cudaMemsetAsync(dL_ddef, 0, sizeof(float) * (size_t)h->g.W * h->g.H, h->stream);
   if (h->g.n_pois == 0) return DIC_OK;
+  if (cudaError_t je = pre_join(h); je != cudaSuccess) return cuda_fail(h, je, "precompute join");
   dic::AdjointParams p;
   p.ref = h->ref;
   p.ref_f32 = h->ref_f32;
@@ -524,7 +573,8 @@ dic_status dic_pso_search(dic_t h, int modified, int particles, int generations,
   p.evals = evals;
   e = dic::launch_pso(p, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "swarm search launch");
-  return DIC_OK;
+  e = pre_join(h);  // the pair's precompute ran beside the search
+  return e == cudaSuccess ? DIC_OK : cuda_fail(h, e, "precompute join");
 }
 
 }  // extern "C"
@@ -679,8 +729,13 @@ dic_status dic_integer_search(dic_t h, int32_t* u0, int32_t* v0, float* zncc0,
     return fail(h, DIC_ERR_UNSUPPORTED, "integer search needs an 8-bit pair (exact sums)");
   if (h->g.n_pois == 0) return DIC_OK;
   if (!u0 || !v0 || !zncc0 || !status) return fail(h, DIC_ERR_ARG, "null output pointer");
-  return search_images(h, h->ref, h->def, h->tma_ok, &h->tm_ref, &h->tm_def, u0, v0, zncc0,
-                       status, h->stream);
+  const dic_status st = search_images(h, h->ref, h->def, h->tma_ok, &h->tm_ref, &h->tm_def, u0,
+                                      v0, zncc0, status, h->stream);
+  if (st != DIC_OK) return st;
+  // the pair's precompute ran beside the search; later work on the stream
+  // comes after both
+  const cudaError_t e = pre_join(h);
+  return e == cudaSuccess ? DIC_OK : cuda_fail(h, e, "precompute join");
 }
 
 
@@ -723,7 +778,9 @@ dic_status dic_subpixel2(dic_t h, dic_method method, const int32_t* u0, const in
   p.zncc = zncc;
   p.iters = iters;
   p.status = status;
-  cudaError_t e = dic::launch_subpixel2(p, h->solve_bits == 64, p12, h->stream);
+  cudaError_t e = pre_join(h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "precompute join");
+  e = dic::launch_subpixel2(p, h->solve_bits == 64, p12, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "second-order subpixel launch");
   return DIC_OK;
 }
@@ -769,8 +826,10 @@ dic_status dic_subpixel(dic_t h, dic_method method, const int32_t* u0, const int
   p.zncc = zncc;
   p.iters = iters;
   p.status = status;
-  cudaError_t e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, h->stream,
-                                       h->interp == DIC_INTERP_BILINEAR);
+  cudaError_t e = pre_join(h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "precompute join");
+  e = dic::launch_subpixel(p, (int)method, h->solve_bits == 64, h->stream,
+                           h->interp == DIC_INTERP_BILINEAR);
   if (e != cudaSuccess) return cuda_fail(h, e, "subpixel launch");
   return DIC_OK;
 }

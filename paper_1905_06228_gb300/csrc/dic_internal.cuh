@@ -287,6 +287,12 @@ struct dic_s {
   int solve_bits = 32;
   int interp = DIC_INTERP_BICUBIC;
   cudaStream_t stream = nullptr;
+  // The pair's precompute runs on pre_side, forked from stream, so that it
+  // overlaps the integer search; the kernels that read its output wait on
+  // pre_done (pre_pending: recorded for the current pair)
+  cudaStream_t pre_side = nullptr;
+  cudaEvent_t pre_fork = nullptr, pre_done = nullptr;
+  bool pre_pending = false;
 
   bool have_pair = false;
   const uint8_t* ref = nullptr;
