@@ -229,6 +229,9 @@ void dic_destroy(dic_t h) {
   if (h->pre_side) cudaStreamDestroy(h->pre_side);
   if (h->pre_fork) cudaEventDestroy(h->pre_fork);
   if (h->pre_done) cudaEventDestroy(h->pre_done);
+  if (h->search_side) cudaStreamDestroy(h->search_side);
+  if (h->search_fork) cudaEventDestroy(h->search_fork);
+  if (h->search_join) cudaEventDestroy(h->search_join);
   delete h;
 }
 
@@ -325,6 +328,29 @@ cudaStream_t pre_stream(dic_t h) {
     return h->stream;
   }
   return h->pre_side;
+}
+
+// Side stream of the tensor-core search's set-up kernels (nullptr while st
+// is being captured into a graph, or if it cannot be made).
+cudaStream_t search_side(dic_t h, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (!h->search_side) {
+    if (cudaStreamCreateWithFlags(&h->search_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->search_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->search_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (h->search_side) cudaStreamDestroy(h->search_side);
+      if (h->search_fork) cudaEventDestroy(h->search_fork);
+      if (h->search_join) cudaEventDestroy(h->search_join);
+      h->search_side = nullptr;
+      h->search_fork = h->search_join = nullptr;
+    }
+  }
+  return h->search_side;
 }
 
 // The handle's stream waits for the current pair's precompute.
@@ -646,7 +672,8 @@ dic_status search_images(dic_t h, const uint8_t* ref, const uint8_t* def, bool t
     CUtensorMap tma, tmb;
     if (!encode_tc(&tma, &tmb, t))
       return fail(h, DIC_ERR_UNSUPPORTED, "tensor-core search: tensor map encoding failed");
-    cudaError_t e = dic::launch_search_tc(t, &tma, &tmb, st);
+    const cudaStream_t side = search_side(h, st);
+    cudaError_t e = dic::launch_search_tc(t, &tma, &tmb, st, side, h->search_fork, h->search_join);
     if (e != cudaSuccess) return cuda_fail(h, e, "tensor-core search launch");
     return DIC_OK;
   }

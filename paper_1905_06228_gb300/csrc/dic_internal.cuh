@@ -175,8 +175,12 @@ size_t search_tc_gph_elems(const SearchTcParams& g);
 // Sets the bank's row order (1: by image row, 0: stacked) and its row
 // count; false if that order exceeds the bank's limits.
 bool search_tc_bank_order(SearchTcParams* g, int overlap);
+// With side (and its two events) the phase images and template bank run on
+// side, forked from st, beside the box-sum maps, and st joins it before the
+// tile kernel.
 cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
-                             const CUtensorMap* tmB, cudaStream_t st);
+                             const CUtensorMap* tmB, cudaStream_t st, cudaStream_t side = nullptr,
+                             cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 // Box-sum maps of f (fbox) and g (posbox) over p.xmin, p.ymin, p.ntx * 8 by
 // p.nty * 16 subset top-left positions (reads p.ref, p.def, W, H, pitch, S).
 cudaError_t launch_boxmaps(const SearchTcParams& p, cudaStream_t st);
@@ -293,6 +297,10 @@ struct dic_s {
   cudaStream_t pre_side = nullptr;
   cudaEvent_t pre_fork = nullptr, pre_done = nullptr;
   bool pre_pending = false;
+  // the tensor-core search's phase images and bank run on search_side
+  // beside its box-sum maps
+  cudaStream_t search_side = nullptr;
+  cudaEvent_t search_fork = nullptr, search_join = nullptr;
 
   bool have_pair = false;
   const uint8_t* ref = nullptr;

@@ -1264,15 +1264,24 @@ cudaError_t launch_boxmaps(const SearchTcParams& p, cudaStream_t st) {
 }
 
 cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
-                             const CUtensorMap* tmB, cudaStream_t st) {
+                             const CUtensorMap* tmB, cudaStream_t st, cudaStream_t side,
+                             cudaEvent_t fork, cudaEvent_t join) {
   if (p.n_pois == 0) return cudaSuccess;
   const unsigned wblocks = (unsigned)((p.n_pois + 7) / 8);
   cudaError_t e;
+  // phase images and template bank (on side, beside the box-sum maps, when
+  // given), then the box-sum maps
+  const cudaStream_t pst = side ? side : st;
+  if (side) {
+    e = cudaEventRecord(fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+    if (e != cudaSuccess) return e;
+  }
   {
     const int chunks = 8 * p.phh * (p.phw / 8);  // 16-byte chunks of the phase images
-    phase_kernel<<<(chunks + 255) / 256, 256, 0, st>>>(p);
+    phase_kernel<<<(chunks + 255) / 256, 256, 0, pst>>>(p);
     const int per_row = p.nx * 8;  // 16-byte chunks of a bank row
-    bank_kernel<<<dim3((per_row + 127) / 128, p.bank_rows), 128, 0, st>>>(p);
+    bank_kernel<<<dim3((per_row + 127) / 128, p.bank_rows), 128, 0, pst>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1285,6 +1294,11 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
     dim3 grid((p.ntx * 8 + kBoxX - 1) / kBoxX, (p.nty * 16 + kBoxY - 1) / kBoxY, 2);
     boxmap_kernel<<<grid, 256, bsm, st>>>(p);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (side) {
+    e = cudaEventRecord(join, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
     if (e != cudaSuccess) return e;
   }
   const size_t smem = search_tc_smem(p);
