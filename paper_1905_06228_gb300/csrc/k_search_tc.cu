@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------ final reduce
-// One warp per POI.  Each slot holds the exact winner of one tile (or no
+// kRedLanes lanes per POI.  Each slot holds the exact winner of one tile (or no
 // candidate).  Lanes score their slots in float from the exact sums (error
 // below 1e-6 plus 2^-13 from the slot index packed into the key, relative;
 // exactly 0 where num = 0) and the warp keeps the best two; if the best's
@@ -1055,14 +1055,20 @@ __device__ __forceinline__ float cand_score(long long num, long long dg) {
   return n * fabsf(n) * __frcp_rn(ll_to_float(dg));  // sign(C) C^2 Df
 }
 
+constexpr int kRedLanes = 8;  // lanes per POI of the reduce kernel (4 POIs per warp)
+
 __global__ void reduce_kernel(const SearchTcParams p) {
-  const int lane = threadIdx.x & 31;
-  const int64_t poi = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (poi >= p.n_pois) return;
+  const int lane = threadIdx.x & 31, sub = lane & (kRedLanes - 1);
+  const int64_t poi =
+      ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 / kRedLanes) +
+      lane / kRedLanes;
+  // no early exit: every lane takes part in the warp's shuffles
+  const bool live = poi < p.n_pois;
+  const int64_t pq = live ? poi : 0;
   const int S = p.S, M = p.M, R = p.R, ow = 2 * R + 1;
-  const int x0 = M + R + 2 + (int)(poi % p.nx) * p.step;
-  const int y0 = M + R + 2 + (int)(poi / p.nx) * p.step;
-  const SlotCand* sl = p.slots + (size_t)poi * p.nslots;
+  const int x0 = M + R + 2 + (int)(pq % p.nx) * p.step;
+  const int y0 = M + R + 2 + (int)(pq / p.nx) * p.step;
+  const SlotCand* sl = p.slots + (size_t)pq * p.nslots;
   // The slots of the tiles that meet the POI's window, (tx, ty) from
   // (xl - R, yl - R) to (xl + R, yl + R) in tile units: the tile kernel has
   // written each of them (a winner, or no candidate); the other slots of
@@ -1072,64 +1078,72 @@ __global__ void reduce_kernel(const SearchTcParams p) {
   const int nsy = (yl + R - p.ymin) / kTileQ - (yl - R - p.ymin) / kTileQ + 1;
   auto used = [&](int s) { return s % p.slots_x < nsx && s / p.slots_x < nsy; };
   auto valid = [&](int l) { return l >= 0 && l < ow * ow; };  // not "no candidate"
-  // the first round of slots is loaded together with the POI's own sums
+  // the first slot of each lane is loaded together with the POI's own sums
   SlotCand c0{0, 1, -1, 0};
-  if (lane < p.nslots && used(lane)) c0 = sl[lane];
+  if (live && sub < p.nslots && used(sub)) c0 = sl[sub];
   const int2 fb = p.fbox[(size_t)(y0 - M - p.ymin) * (p.ntx * 8) + (x0 - M - p.xmin)];
   const long long N = (long long)S * S;
   const long long Df = N * (long long)fb.y - (long long)fb.x * fb.x;
-  if (Df == 0) {
-    if (lane == 0) {
-      p.u0[poi] = 0;
-      p.v0[poi] = 0;
-      p.zncc0[poi] = 0.f;
-      p.status[poi] = kZeroVarRef;
-    }
-    return;
-  }
+  const bool act = live && Df != 0;
   int mx = INT_MIN, sc = INT_MIN;
-  if (valid(c0.l))
-    merge2(mx, sc, (f2key(cand_score(c0.num, c0.dg)) & ~(kMaxSlots - 1)) | lane, INT_MIN);
-  for (int s = lane + 32; s < p.nslots; s += 32) {
-    if (!used(s)) continue;
-    const SlotCand c = sl[s];
-    if (valid(c.l))
-      merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~(kMaxSlots - 1)) | s, INT_MIN);
+  if (act) {
+    if (valid(c0.l))
+      merge2(mx, sc, (f2key(cand_score(c0.num, c0.dg)) & ~(kMaxSlots - 1)) | sub, INT_MIN);
+    for (int s = sub + kRedLanes; s < p.nslots; s += kRedLanes) {
+      if (!used(s)) continue;
+      const SlotCand c = sl[s];
+      if (valid(c.l))
+        merge2(mx, sc, (f2key(cand_score(c.num, c.dg)) & ~(kMaxSlots - 1)) | s, INT_MIN);
+    }
   }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) {
+  for (int o = kRedLanes / 2; o; o >>= 1) {  // within the POI's lanes
     const int omx = __shfl_xor_sync(0xffffffffu, mx, o);
     const int osc = __shfl_xor_sync(0xffffffffu, sc, o);
     merge2(mx, sc, omx, osc);
   }
   Cand best{0, 1, INT_MAX};
-  if (mx != INT_MIN) {
+  bool tie = false;
+  float thr = 0.f;
+  if (act && mx != INT_MIN) {
     const float fm = key2f(mx);
     if (fabsf(fm) > 1e-8f && (sc == INT_MIN || key2f(sc) < fm - 1e-3f * fabsf(fm))) {
       const SlotCand w = sl[mx & (kMaxSlots - 1)];
       best = Cand{w.num, w.dg, w.l};
     } else {
-      const float thr = fm - 2e-3f * fabsf(fm) - 1e-8f;
-      for (int s = lane; s < p.nslots; s += 32) {
+      tie = true;
+      thr = fm - 2e-3f * fabsf(fm) - 1e-8f;
+    }
+  }
+  if (__any_sync(0xffffffffu, tie)) {
+    Cand tb{0, 1, INT_MAX};
+    if (tie) {
+      for (int s = sub; s < p.nslots; s += kRedLanes) {
         if (!used(s)) continue;
         const SlotCand c = sl[s];
         if (valid(c.l) && cand_score(c.num, c.dg) >= thr) {
           const Cand d{c.num, c.dg, c.l};
-          if (cand_better(d, best)) best = d;
+          if (cand_better(d, tb)) tb = d;
         }
       }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        Cand d;
-        d.num = __shfl_xor_sync(0xffffffffu, best.num, o);
-        d.dg = __shfl_xor_sync(0xffffffffu, best.dg, o);
-        d.l = __shfl_xor_sync(0xffffffffu, best.l, o);
-        if (cand_better(d, best)) best = d;
-      }
     }
+#pragma unroll
+    for (int o = kRedLanes / 2; o; o >>= 1) {
+      Cand d;
+      d.num = __shfl_xor_sync(0xffffffffu, tb.num, o);
+      d.dg = __shfl_xor_sync(0xffffffffu, tb.dg, o);
+      d.l = __shfl_xor_sync(0xffffffffu, tb.l, o);
+      if (cand_better(d, tb)) tb = d;
+    }
+    if (tie) best = tb;
   }
-  if (lane == 0) {
-    if (best.l == INT_MAX) {
+  if (live && sub == 0) {
+    if (Df == 0) {
+      p.u0[poi] = 0;
+      p.v0[poi] = 0;
+      p.zncc0[poi] = 0.f;
+      p.status[poi] = kZeroVarRef;
+    } else if (best.l == INT_MAX) {
       p.u0[poi] = -R;
       p.v0[poi] = -R;
       p.zncc0[poi] = 0.f;
@@ -1267,7 +1281,8 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
                              const CUtensorMap* tmB, cudaStream_t st, cudaStream_t side,
                              cudaEvent_t fork, cudaEvent_t join) {
   if (p.n_pois == 0) return cudaSuccess;
-  const unsigned wblocks = (unsigned)((p.n_pois + 7) / 8);
+  const int pois_per_block = (256 / 32) * (32 / kRedLanes);
+  const unsigned rblocks = (unsigned)((p.n_pois + pois_per_block - 1) / pois_per_block);
   cudaError_t e;
   // phase images and template bank (on side, beside the box-sum maps, when
   // given), then the box-sum maps
@@ -1315,7 +1330,7 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
   tile_kernel<<<(unsigned)std::max(1, std::min(nitems, nsm)), kThreads, smem, st>>>(p, *tmA, *tmB);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  reduce_kernel<<<wblocks, 256, 0, st>>>(p);
+  reduce_kernel<<<rblocks, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
