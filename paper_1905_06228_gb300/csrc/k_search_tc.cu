@@ -143,28 +143,31 @@ __device__ __forceinline__ uint32_t centred_bf16(uint32_t byte) {
 // BF16:  ph[s][y][c] = g[y][c + s] - 128  (0 outside the image),
 // so that any run of 8 consecutive pixels starting at column x is one
 // aligned 16-byte chunk: copy s = x mod 8 at column x - s.  One thread per
-// 16-byte chunk.
+// 8-column chunk (y, c): it reads g[y][c .. c+14] once and writes that
+// chunk of all eight copies.
 __global__ void phase_kernel(const SearchTcParams p) {
   const int cpr = p.phw / 8;  // chunks per row
   const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
-  if (chunk >= 8 * p.phh * cpr) return;
-  const int row = chunk / cpr;  // sft * phh + y
-  const int c = (chunk - row * cpr) * 8;
-  const int sft = row / p.phh, y = row - sft * p.phh;
-  uint32_t w[4];
+  if (chunk >= p.phh * cpr) return;
+  const int y = chunk / cpr;
+  const int c = (chunk - y * cpr) * 8;
+  const bool yin = y < p.H;
+  const uint8_t* row = p.def + (size_t)(yin ? y : 0) * p.pitch;
+  uint32_t h[16];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    uint32_t h2[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int x = c + sft + 2 * e + k;
-      // small integers are exact in BF16; 0 outside the image
-      h2[k] = (x < p.W && y < p.H) ? centred_bf16(p.def[(size_t)y * p.pitch + x]) : 0u;
-    }
-    w[e] = h2[0] | (h2[1] << 16);
+  for (int k = 0; k < 15; ++k) {
+    const int x = c + k;
+    // small integers are exact in BF16; 0 outside the image
+    h[k] = (yin && x < p.W) ? centred_bf16(row[x]) : 0u;
   }
-  uint16_t* dst = p.gph + (size_t)row * p.phw + c;
-  *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  h[15] = 0u;
+#pragma unroll
+  for (int sft = 0; sft < 8; ++sft) {
+    uint16_t* dst = p.gph + ((size_t)sft * p.phh + y) * p.phw + c;
+    *reinterpret_cast<uint4*>(dst) =
+        make_uint4(h[sft] | (h[sft + 1] << 16), h[sft + 2] | (h[sft + 3] << 16),
+                   h[sft + 4] | (h[sft + 5] << 16), h[sft + 6] | (h[sft + 7] << 16));
+  }
 }
 
 // ------------------------------------------------------------ template bank
@@ -215,9 +218,10 @@ __global__ void bank_kernel(const SearchTcParams p) {
 // blockIdx.z = 0 for f (POI sums, fbox), 1 for g (position sums, posbox).
 // A CTA covers kBoxX x kBoxY outputs: the centred pixels go to shared
 // memory, then separable sums, each thread sliding an S-wide window over
-// kBoxSeg consecutive outputs (one add and one subtract per output after the
-// first).  All sums are exact integers.
-constexpr int kBoxX = 64, kBoxY = 32, kBoxSeg = 8;
+// kBoxSegR consecutive outputs of a row, then kBoxSegC of a column (one add
+// and one subtract per output after the first).  All sums are exact
+// integers.
+constexpr int kBoxX = 64, kBoxY = 32, kBoxSegR = 16, kBoxSegC = 8;
 
 // Row strides in shared memory: pixels padded to an odd number of words and
 // row sums to kBoxX + 1 int2, so that lanes walking consecutive rows hit
@@ -239,20 +243,33 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
   int2* hs = reinterpret_cast<int2*>(v + (size_t)sh * vs);  // [sh][kBoxHs]
   const int px0 = blockIdx.x * kBoxX, py0 = blockIdx.y * kBoxY;
   const int X0 = p.xmin + px0, Y0 = p.ymin + py0;
-  for (int r = threadIdx.x >> 5; r < sh; r += blockDim.x >> 5) {
-    const int y = Y0 + r;
-    const bool yin = y >= 0 && y < p.H;
-    for (int c = threadIdx.x & 31; c < sw; c += 32) {
-      const int x = X0 + c;
-      v[r * vs + c] = (yin && x >= 0 && x < p.W) ? (int)img[(size_t)y * p.pitch + x] - 128 : 0;
+  // pixels: warp w takes rows w, w + 8, ...; each lane up to four columns
+  // (sw <= kBoxX + 63 for S <= 64), all loads of two rows in flight
+  {
+    const int lane = threadIdx.x & 31;
+#pragma unroll 2
+    for (int r = threadIdx.x >> 5; r < sh; r += blockDim.x >> 5) {
+      const int y = Y0 + r;
+      const bool yin = y >= 0 && y < p.H;
+      const uint8_t* row = img + (size_t)(yin ? y : 0) * p.pitch;
+      int px[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = lane + 32 * k, x = X0 + c;
+        px[k] = (c < sw && yin && x >= 0 && x < p.W) ? (int)row[x] - 128 : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (lane + 32 * k < sw) v[r * vs + lane + 32 * k] = px[k];
     }
   }
   __syncthreads();
   // rows: thread t -> row t % sh, segment t / sh
-  for (int t = threadIdx.x; t < sh * (kBoxX / kBoxSeg); t += blockDim.x) {
-    const int r = t % sh, c0 = (t / sh) * kBoxSeg;
+  for (int t = threadIdx.x; t < sh * (kBoxX / kBoxSegR); t += blockDim.x) {
+    const int r = t % sh, c0 = (t / sh) * kBoxSegR;
     const int* row = v + (size_t)r * vs + c0;
     int a = 0, b = 0;
+#pragma unroll 8
     for (int k = 0; k < S; ++k) {
       const int x = row[k];
       a += x;
@@ -261,7 +278,7 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
     int2* o = hs + (size_t)r * kBoxHs + c0;
     o[0] = make_int2(a, b);
 #pragma unroll
-    for (int j = 1; j < kBoxSeg; ++j) {
+    for (int j = 1; j < kBoxSegR; ++j) {
       const int xo = row[j - 1], xi = row[j + S - 1];
       a += xi - xo;
       b += xi * xi - xo * xo;
@@ -271,10 +288,11 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
   __syncthreads();
   // columns: thread t -> column t % kBoxX, segment t / kBoxX
   const int pw = p.ntx * 8, ph = p.nty * 16;
-  for (int t = threadIdx.x; t < kBoxX * (kBoxY / kBoxSeg); t += blockDim.x) {
-    const int c = t % kBoxX, r0 = (t / kBoxX) * kBoxSeg;
+  for (int t = threadIdx.x; t < kBoxX * (kBoxY / kBoxSegC); t += blockDim.x) {
+    const int c = t % kBoxX, r0 = (t / kBoxX) * kBoxSegC;
     const int2* col = hs + (size_t)r0 * kBoxHs + c;
     int a = 0, b = 0;
+#pragma unroll 8
     for (int k = 0; k < S; ++k) {
       const int2 x = col[(size_t)k * kBoxHs];
       a += x.x;
@@ -282,7 +300,7 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
     }
     const int px = px0 + c;
 #pragma unroll
-    for (int j = 0; j < kBoxSeg; ++j) {
+    for (int j = 0; j < kBoxSegC; ++j) {
       if (j > 0) {
         const int2 xo = col[(size_t)(j - 1) * kBoxHs], xi = col[(size_t)(j + S - 1) * kBoxHs];
         a += xi.x - xo.x;
@@ -1293,7 +1311,7 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
     if (e != cudaSuccess) return e;
   }
   {
-    const int chunks = 8 * p.phh * (p.phw / 8);  // 16-byte chunks of the phase images
+    const int chunks = p.phh * (p.phw / 8);  // 8-column chunks of a phase image
     phase_kernel<<<(chunks + 255) / 256, 256, 0, pst>>>(p);
     const int per_row = p.nx * 8;  // 16-byte chunks of a bank row
     bank_kernel<<<dim3((per_row + 127) / 128, p.bank_rows), 128, 0, pst>>>(p);
