@@ -181,35 +181,48 @@ __global__ void phase_kernel(const SearchTcParams p) {
 //    bank rows); an image row is stored SUB times instead of S/step times;
 //  - stacked (bank_overlap = 0): b = kr*sj + j, y(b) = top row of POI row kr
 //    + SUB*j, template rows at or beyond S stored as zeros.
-// One thread per 16-byte chunk (8 taps, never across two template rows).
+// One thread per 16-byte chunk (8 taps, never across two template rows) of
+// kBankRows consecutive bank rows, their loads in flight together.
+constexpr int kBankRows = 4;
+
 __global__ void bank_kernel(const SearchTcParams p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.nx * 8) return;
   const int kc = t >> 3, kb = t & 7;
-  const int b = blockIdx.y, B = p.M + p.R + 2;
-  int ytop = B - p.M + b, ty_lim = INT_MAX;  // image row of sub-row 0, template rows left
-  if (!p.bank_overlap) {
-    const int kr = b / p.sj, j = b - kr * p.sj;
-    ytop = B - p.M + kr * p.step + p.sub * j;
-    ty_lim = p.S - p.sub * j;
-  }
+  const int B = p.M + p.R + 2;
   const int s = (8 * kb) / p.twk, tx0 = 8 * kb - s * p.twk;
-  const int y = ytop + s;
-  const bool row_ok = s < ty_lim && y < p.H;
-  const uint8_t* src = p.ref + (size_t)(row_ok ? y : 0) * p.pitch + (B + kc * p.step - p.M);
-  uint32_t w[4];
+  const uint8_t* col = p.ref + (B + kc * p.step - p.M);
+  uint32_t w[kBankRows][4];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    uint32_t h2[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int tx = tx0 + 2 * e + k;
-      h2[k] = (row_ok && tx < p.S) ? centred_bf16(src[tx]) : 0u;
+  for (int i = 0; i < kBankRows; ++i) {
+    const int b = blockIdx.y * kBankRows + i;
+    int ytop = B - p.M + b, ty_lim = INT_MAX;  // image row of sub-row 0, template rows left
+    if (!p.bank_overlap) {
+      const int kr = b / p.sj, j = b - kr * p.sj;
+      ytop = B - p.M + kr * p.step + p.sub * j;
+      ty_lim = p.S - p.sub * j;
     }
-    w[e] = h2[0] | (h2[1] << 16);
+    const int y = ytop + s;
+    const bool row_ok = b < p.bank_rows && s < ty_lim && y < p.H;
+    const uint8_t* src = col + (size_t)(row_ok ? y : 0) * p.pitch;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t h2[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int tx = tx0 + 2 * e + k;
+        h2[k] = (row_ok && tx < p.S) ? centred_bf16(src[tx]) : 0u;
+      }
+      w[i][e] = h2[0] | (h2[1] << 16);
+    }
   }
-  *reinterpret_cast<uint4*>(p.bank + ((size_t)b * p.nx + kc) * 64 + 8 * kb) =
-      make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+  for (int i = 0; i < kBankRows; ++i) {
+    const int b = blockIdx.y * kBankRows + i;
+    if (b < p.bank_rows)
+      *reinterpret_cast<uint4*>(p.bank + ((size_t)b * p.nx + kc) * 64 + 8 * kb) =
+          make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+  }
 }
 
 // ------------------------------------------------------------ box-sum maps
@@ -244,10 +257,10 @@ __global__ void __launch_bounds__(256) boxmap_kernel(const SearchTcParams p) {
   const int px0 = blockIdx.x * kBoxX, py0 = blockIdx.y * kBoxY;
   const int X0 = p.xmin + px0, Y0 = p.ymin + py0;
   // pixels: warp w takes rows w, w + 8, ...; each lane up to four columns
-  // (sw <= kBoxX + 63 for S <= 64), all loads of two rows in flight
+  // (sw <= kBoxX + 63 for S <= 64), the loads of up to eight rows in flight
   {
     const int lane = threadIdx.x & 31;
-#pragma unroll 2
+#pragma unroll 8
     for (int r = threadIdx.x >> 5; r < sh; r += blockDim.x >> 5) {
       const int y = Y0 + r;
       const bool yin = y >= 0 && y < p.H;
@@ -1314,7 +1327,8 @@ cudaError_t launch_search_tc(const SearchTcParams& p, const CUtensorMap* tmA,
     const int chunks = p.phh * (p.phw / 8);  // 8-column chunks of a phase image
     phase_kernel<<<(chunks + 255) / 256, 256, 0, pst>>>(p);
     const int per_row = p.nx * 8;  // 16-byte chunks of a bank row
-    bank_kernel<<<dim3((per_row + 127) / 128, p.bank_rows), 128, 0, pst>>>(p);
+    bank_kernel<<<dim3((per_row + 127) / 128, (p.bank_rows + kBankRows - 1) / kBankRows), 128,
+                  0, pst>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
