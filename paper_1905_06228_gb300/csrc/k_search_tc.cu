@@ -42,7 +42,7 @@
 // Epilogue: each warp reads one lane quarter of TMEM (32 positions) x 16
 // POIs, scores sign(num) num^2 / Dg in FP32 (errors bounded, see
 // score_block) and keeps each POI's best two, and the exact sum at the best,
-// through a warp reduce-scatter; a POI's float winner is its exact tile
+// by warp max reductions; a POI's float winner is its exact tile
 // winner when it clears the second by 5e-4, otherwise the warps of the four
 // lane quarters compare the near-tied positions exactly from the sums in
 // TMEM.  Each (tile, POI) winner goes to a slot; a final kernel reduces a
@@ -425,22 +425,6 @@ __device__ __forceinline__ void merge2(int& mx, int& sc, int omx, int osc) {
   mx = max(mx, omx);
 }
 
-// One halving step of the warp reduce-scatter: 2H (largest, second) pairs
-// per lane become H, each merged with the partner lane's matching pair.
-template <int H>
-__device__ __forceinline__ void bfly(int (&mx)[8], int (&sc)[8], bool up, int o) {
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    const int smx = up ? mx[i] : mx[i + H], ssc = up ? sc[i] : sc[i + H];
-    int kmx = up ? mx[i + H] : mx[i], ksc = up ? sc[i + H] : sc[i];
-    const int rmx = __shfl_xor_sync(0xffffffffu, smx, o);
-    const int rsc = __shfl_xor_sync(0xffffffffu, ssc, o);
-    merge2(kmx, ksc, rmx, rsc);
-    mx[i] = kmx;
-    sc[i] = ksc;
-  }
-}
-
 // Sums of the accumulator for lane quarter `quarter`, columns c .. c+15 of
 // every accumulator of a buffer (one accumulator: the exact FP32 sums as
 // bits; several: their int32 total).
@@ -490,7 +474,6 @@ __device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tm
   const float Nf = (float)N;
   uint32_t val[16];
   load_sums<kWide>(tmem, nacc, NP, quarter, c0, val);
-  int mx[8], sc[8];
   int key[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -507,38 +490,18 @@ __device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tm
     const float s = nf * fabsf(nf) * pinv_m;
     key[k] = in ? ((f2key(s) & ~127) | m) : INT_MIN;
   }
-  // reduce-scatter over the 32 lanes: 16 -> 8 -> 4 -> 2 -> 1 pairs
-  {
-    const bool up = lane & 16;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int s_ = up ? key[i] : key[i + 8];
-      const int k_ = up ? key[i + 8] : key[i];
-      const int r_ = __shfl_xor_sync(0xffffffffu, s_, 16);
-      mx[i] = max(k_, r_);
-      sc[i] = min(k_, r_);
-    }
-  }
-  bfly<4>(mx, sc, lane & 8, 8);
-  bfly<2>(mx, sc, lane & 4, 4);
-  bfly<1>(mx, sc, lane & 2, 2);
-  {
-    const int rmx = __shfl_xor_sync(0xffffffffu, mx[0], 1);
-    const int rsc = __shfl_xor_sync(0xffffffffu, sc[0], 1);
-    merge2(mx[0], sc[0], rmx, rsc);
-  }
-  // lanes l and l^1 now hold the best two of POI c0 + j; the sum at the
-  // best position sits in register val[j] of lane (best & 31)
-  const int j = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 +
-                ((lane >> 1) & 1);
-  const int src = mx[0] == INT_MIN ? lane : (mx[0] & 31);
-  int vbest = 0;
+  // per POI, the best and second-best keys over the warp's 32 positions by
+  // warp max reductions (a valid key is unique: its low 7 bits hold the
+  // position); the lane holding the best stores the POI's entry with the
+  // sum at the best, lane 0 stores it where the POI has no candidate here
+  int4* out = red + quarter * NP + c0;
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    const int v = __shfl_sync(0xffffffffu, (int)val[k], src);
-    if (j == k) vbest = v;
+    const int mx = __reduce_max_sync(0xffffffffu, key[k]);
+    const int sc = __reduce_max_sync(0xffffffffu, key[k] == mx ? INT_MIN : key[k]);
+    if (mx != INT_MIN ? (mx & 31) == lane : lane == 0)
+      out[k] = make_int4(mx, sc, (int)val[k], 0);
   }
-  if ((lane & 1) == 0) red[quarter * NP + c0 + j] = make_int4(mx[0], sc[0], vbest, 0);
 }
 
 // POI n of a tile's block (row-major over ncols_max x nrows_max): operand
