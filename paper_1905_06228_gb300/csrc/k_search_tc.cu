@@ -450,6 +450,20 @@ __device__ __forceinline__ void load_sums(uint32_t tmem, int nacc, int np, int q
   }
 }
 
+// Columns c .. c+15 of lane quarter `quarter` of a one-accumulator buffer:
+// the load only (tcgen05.wait::ld makes them valid).
+__device__ __forceinline__ void tmem_ld16(uint32_t tmem, int quarter, int c,
+                                          uint32_t (&v)[16]) {
+  const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+        "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(addr));
+}
+
 // Scores of one (quarter, 16-column) block of an accumulator buffer and
 // their per-POI best two over the quarter's 32 positions, with the sum at
 // the best.
@@ -465,15 +479,13 @@ __device__ __forceinline__ void load_sums(uint32_t tmem, int nacc, int np, int q
 // low 7 bits of its key, stays below 1.5e-4 for num != 0, and |score| <
 // 4e-9 when num = 0; the winner test relies on this.
 template <bool kWide>
-__device__ __forceinline__ void score_block(const SearchTcParams& p, uint32_t tmem, int nacc,
+__device__ __forceinline__ void score_block(const SearchTcParams& p, const uint32_t (&val)[16],
                                             int quarter, int lane, int c0, int rr, int q,
                                             float sbf, int sb, float pinv_m, const PoiInfo* poi,
                                             int4* red) {
   const int NP = p.npad, R2 = 2 * p.R, m = quarter * 32 + lane;
   const long long N = (long long)p.S * p.S;
   const float Nf = (float)N;
-  uint32_t val[16];
-  load_sums<kWide>(tmem, nacc, NP, quarter, c0, val);
   int key[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -895,11 +907,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float pinv_m = pinv[m];
         const int sb = psb[m];
         const float sbf = (float)sb;
-        for (int c0 = grp * 16; c0 < NP; c0 += kEpiGroups * 16) {
-          if (wide)
-            score_block<true>(p, tbuf, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, red);
-          else
-            score_block<false>(p, tbuf, nacc, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, red);
+        constexpr int kStep = kEpiGroups * 16;
+        if (wide) {
+          for (int c0 = grp * 16; c0 < NP; c0 += kStep) {
+            uint32_t val[16];
+            load_sums<true>(tbuf, nacc, NP, quarter, c0, val);
+            score_block<true>(p, val, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, red);
+          }
+        } else {
+          // two blocks' sums loaded under one wait
+          for (int c0 = grp * 16; c0 < NP; c0 += 2 * kStep) {
+            const bool two = c0 + kStep < NP;
+            uint32_t va[16], vb[16];
+            tmem_ld16(tbuf, quarter, c0, va);
+            if (two) tmem_ld16(tbuf, quarter, c0 + kStep, vb);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            score_block<false>(p, va, quarter, lane, c0, rr, q, sbf, sb, pinv_m, poi, red);
+            if (two)
+              score_block<false>(p, vb, quarter, lane, c0 + kStep, rr, q, sbf, sb, pinv_m, poi,
+                                 red);
+          }
         }
       }
       epi_sync();
