@@ -773,6 +773,76 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
           off += dwrap;
         }
       }
+    } else if (FANR && !BIL && (S == 31 || S == 15)) {
+      // FA-NR in the column walk of the IC-GN column layout: lane c of each
+      // group of LPR = S + 1 lanes owns column dx = c - M of every
+      // (32 / LPR)-th row (the last lane of a group idles).  With dx
+      // constant per lane, the 39 sums come from 21 per-lane moments in dy,
+      // multiplied by the lane's dx once after the pass; the samples and
+      // their positions are the generic walk's.
+      const int LPR = S + 1, col = lane % LPR, RPP = 32 / LPR;
+      if (col < S) {
+        const float fdx = (float)(col - M), dxx = fdx * fdx;
+        const WarpAffine wa(prm, x0, y0);
+        const float2 la = __ffma2_rn(wa.a, dup2(fdx), wa.o);
+        float2 q0 = dup2(0.f), q1 = dup2(0.f), q2 = dup2(0.f);  // (gx^2, gy^2) dy^0,1,2
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f;                      // gx gy dy^0,1,2
+        float2 e0 = dup2(0.f), e1 = dup2(0.f);                   // (gx, gy) (g - c) dy^0,1
+        float2 h0 = dup2(0.f), h1 = dup2(0.f);                   // (gx, gy) (f - fbar) dy^0,1
+        float2 j0 = dup2(0.f), j1 = dup2(0.f);                   // (gx, gy) dy^0,1
+#pragma unroll 2
+        for (int r = lane / LPR; r < S; r += RPP) {
+          const float dy = (float)(r - M);
+          const float2 dy2 = dup2(dy);
+          float2 t;
+          const size_t cell = wa.locate_l(__ffma2_rn(wa.b, dy2, la), W, H, t);
+          float gx, gy, g;
+          if (kQuads)
+            g = bicubic_q_grad(p.gq, W, cell, t.x, t.y, gx, gy);
+          else
+            g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
+          const float d = g - c;
+          s0 += d;
+          s1 = fmaf(d, d, s1);
+          float2 gr;
+          float f;
+          PS::unpack(spt[r * S + col], gr, f);
+          const float fc = f - fbar;
+          sfd = fmaf(fc, d, sfd);
+          const float2 gg = make_float2(gx, gy);
+          const float2 sq = __fmul2_rn(gg, gg), sqdy = __fmul2_rn(sq, dy2);
+          q0 = __fadd2_rn(q0, sq);
+          q1 = __fadd2_rn(q1, sqdy);
+          q2 = __ffma2_rn(sqdy, dy2, q2);
+          const float cx = gx * gy, cxdy = cx * dy;
+          c0 += cx;
+          c1 += cxdy;
+          c2 = fmaf(cxdy, dy, c2);
+          const float2 gd = __fmul2_rn(gg, dup2(d));
+          e0 = __fadd2_rn(e0, gd);
+          e1 = __ffma2_rn(gd, dy2, e1);
+          const float2 gf = __fmul2_rn(gg, dup2(fc));
+          h0 = __fadd2_rn(h0, gf);
+          h1 = __ffma2_rn(gf, dy2, h1);
+          j0 = __fadd2_rn(j0, gg);
+          j1 = __ffma2_rn(gg, dy2, j1);
+        }
+        // J = (gx, gx dx, gx dy, gy, gy dx, gy dy): J^T J (lower triangle,
+        // row by row), then sum J (g - c), sum J (f - fbar), sum J
+        acc[0] = q0.x; acc[1] = fdx * q0.x; acc[2] = dxx * q0.x;
+        acc[3] = q1.x; acc[4] = fdx * q1.x; acc[5] = q2.x;
+        acc[6] = c0; acc[7] = fdx * c0; acc[8] = c1; acc[9] = q0.y;
+        acc[10] = fdx * c0; acc[11] = dxx * c0; acc[12] = fdx * c1; acc[13] = fdx * q0.y;
+        acc[14] = dxx * q0.y;
+        acc[15] = c1; acc[16] = fdx * c1; acc[17] = c2; acc[18] = q1.y; acc[19] = fdx * q1.y;
+        acc[20] = q2.y;
+        acc[21] = e0.x; acc[22] = fdx * e0.x; acc[23] = e1.x;
+        acc[24] = e0.y; acc[25] = fdx * e0.y; acc[26] = e1.y;
+        acc[27] = h0.x; acc[28] = fdx * h0.x; acc[29] = h1.x;
+        acc[30] = h0.y; acc[31] = fdx * h0.y; acc[32] = h1.y;
+        acc[33] = j0.x; acc[34] = fdx * j0.x; acc[35] = j1.x;
+        acc[36] = j0.y; acc[37] = fdx * j0.y; acc[38] = j1.y;
+      }
     } else {
       const WarpAffine wa(prm, x0, y0);
       PtWalk2 w(lane, S, M);
