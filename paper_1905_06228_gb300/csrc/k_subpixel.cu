@@ -278,8 +278,8 @@ __host__ __device__ inline size_t warp_smem_bytes(int N, size_t point_bytes) {
   return ((size_t)N * point_bytes + 15) / 16 * 16 + 36 * sizeof(double) + 12 * sizeof(float);
 }
 
-// IC-GN of one POI of an 8-bit pair with bicubic interpolation when the
-// subset width is 31 or 15 (LPR = 32 or 16 lanes per subset row): lane c of
+// IC-GN of one POI of an 8-bit pair (bicubic interpolation, or bilinear with
+// BIL) when the subset width is 31 or 15 (LPR = 32 or 16 lanes per subset row): lane c of
 // each group of LPR lanes owns column dx = c - M of every (32 / LPR)-th row
 // (the last lane of a group idles), so dx is constant per lane.  The
 // arithmetic is the generic path's; what changes is where the work lands:
@@ -294,7 +294,7 @@ __host__ __device__ inline size_t warp_smem_bytes(int N, size_t point_bytes) {
 //  - sum SD_1 (g - c) and sum SD_4 (g - c) are dx times the lane's
 //    sum SD_0 (g - c) and sum SD_3 (g - c), formed once per pass;
 //  - the point records hold f - fbar instead of f.
-template <typename TS, int LPR>
+template <typename TS, int LPR, bool BIL>
 __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t poi, int lane,
                                              unsigned char* wsm) {
   using PS = PointStore<uint8_t>;
@@ -453,7 +453,14 @@ __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t po
           const float dy = (float)(r - M);
           float2 t;
           const size_t cell = wa.locate_l(__ffma2_rn(wa.b, dup2(dy), la), W, H, t);
-          absorb(r * S + col, bicubic_q(p.gq, W, cell, t), dy);
+          float g;
+          if (BIL) {
+            float gx, gy;
+            g = bilinear<false>(p.gimg, W, cell, t.x, t.y, gx, gy);
+          } else {
+            g = bicubic_q(p.gq, W, cell, t);
+          }
+          absorb(r * S + col, g, dy);
         }
       }
     }
@@ -515,7 +522,8 @@ __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t po
       for (int r = row0; r < S; r += RPP) {
         float tx, ty, gx, gy;
         const size_t cell = locate(prm, col - M, r - M, x0, y0, W, H, tx, ty);
-        const float d = bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy) - c;
+        const float d = (BIL ? bilinear<false>(p.gimg, W, cell, tx, ty, gx, gy)
+                             : bicubic<false>(p.gimg, W, cell, tx, ty, gx, gy)) - c;
         float2 gr;
         float fc;
         PS::unpack(spt[r * S + col], gr, fc);
@@ -539,10 +547,10 @@ __device__ __forceinline__ void icgn_col_poi(const SubpixelParams& p, int64_t po
 template <bool FANR, typename TS, typename TP, bool BIL = false>
 __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t poi, int lane,
                                              unsigned char* wsm) {
-  if constexpr (!FANR && !BIL && sizeof(TP) == 1) {
+  if constexpr (!FANR && sizeof(TP) == 1) {
     // subset widths whose rows fill a warp (or half of one): column layout
-    if (p.S == 31) return icgn_col_poi<TS, 32>(p, poi, lane, wsm);
-    if (p.S == 15) return icgn_col_poi<TS, 16>(p, poi, lane, wsm);
+    if (p.S == 31) return icgn_col_poi<TS, 32, BIL>(p, poi, lane, wsm);
+    if (p.S == 15) return icgn_col_poi<TS, 16, BIL>(p, poi, lane, wsm);
   }
   using PS = PointStore<TP>;
   using G = typename PS::T;
