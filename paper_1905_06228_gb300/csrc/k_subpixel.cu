@@ -781,7 +781,7 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
           off += dwrap;
         }
       }
-    } else if (FANR && !BIL && (S == 31 || S == 15)) {
+    } else if (FANR && (S == 31 || S == 15)) {
       // FA-NR in the column walk of the IC-GN column layout: lane c of each
       // group of LPR = S + 1 lanes owns column dx = c - M of every
       // (32 / LPR)-th row (the last lane of a group idles).  With dx
@@ -805,7 +805,9 @@ __device__ __forceinline__ void subpixel_poi(const SubpixelParams& p, int64_t po
           float2 t;
           const size_t cell = wa.locate_l(__ffma2_rn(wa.b, dy2, la), W, H, t);
           float gx, gy, g;
-          if (kQuads)
+          if (BIL)
+            g = bilinear<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
+          else if (kQuads)
             g = bicubic_q_grad(p.gq, W, cell, t.x, t.y, gx, gy);
           else
             g = bicubic<true>(p.gimg, W, cell, t.x, t.y, gx, gy);
