@@ -446,11 +446,24 @@ __global__ void __launch_bounds__(32 * kWarps2) subpixel2_kernel(const SubpixelP
   int it_done = 0;
   float zn = 0.f;
   bool have_zn = false;
+  // The bounds test of an accepted update is taken in the next pass, from
+  // the positions that pass computes anyway (the same arithmetic as
+  // all_in); a shape that fails it is undone as if it had been refused, so
+  // statuses, shapes and iteration counts are those of testing it at once.
+  // Only the shape a POI returns is tested by all_in.
+  // the shape before the last accepted update, entry a on lane a
+  float pprev = 0.f;
+  auto undo = [&]() {
+#pragma unroll
+    for (int a = 0; a < 12; ++a) prm[a] = __shfl_sync(0xffffffffu, pprev, a);
+  };
+  bool pending = false;  // prm is an update not yet tested against the bounds
   for (int it = 1; it <= p.max_iter; ++it) {
     float s0 = 0.f, s1 = 0.f, sfd = 0.f;
     float2 acc[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k] = dup2(0.f);
+    bool inb = true;
     PtWalk w(lane, S, M);
     for (int i = lane; i < N; i += 32, w.next()) {
       float e[6];
@@ -461,6 +474,10 @@ __global__ void __launch_bounds__(32 * kWarps2) subpixel2_kernel(const SubpixelP
         g = p.gimg[(size_t)(y0 + w.dy + (int)prm[6]) * W + (x0 + w.dx + (int)prm[0])];
       } else {
         const float2 l = warp2(prm, e);
+        if (pending) {
+          const float x = (float)x0 + l.x, y = (float)y0 + l.y;
+          inb = inb && x >= 1.f && x < (float)(W - 2) && y >= 1.f && y < (float)(H - 2);
+        }
         const float fx = floorf(l.x), fy = floorf(l.y);
         float2 t = make_float2(l.x - fx, l.y - fy);
         int ix = x0 + (int)fx, iy = y0 + (int)fy;
@@ -480,6 +497,14 @@ __global__ void __launch_bounds__(32 * kWarps2) subpixel2_kernel(const SubpixelP
       const float2 ab = make_float2(r.gx * d, r.gy * d);
 #pragma unroll
       for (int k = 0; k < 6; ++k) acc[k] = __ffma2_rn(ab, dup2(e[k]), acc[k]);
+    }
+    if (pending) {
+      if (!__all_sync(0xffffffffu, inb)) {
+        undo();
+        st = kOutOfBounds;
+        break;
+      }
+      pending = false;
     }
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
@@ -531,22 +556,32 @@ __global__ void __launch_bounds__(32 * kWarps2) subpixel2_kernel(const SubpixelP
       st = kNonFinite;
       break;
     }
-    if (!all_in(pn, x0, y0, S, M, W, H, lane)) {
-      st = kOutOfBounds;
-      break;
-    }
 #pragma unroll
-    for (int a = 0; a < 12; ++a) prm[a] = pn[a];
+    for (int a = 0; a < 12; ++a) {
+      pprev = lane == a ? prm[a] : pprev;
+      prm[a] = pn[a];
+    }
+    pending = true;
     const float nrm = sqrtf(dp[0] * dp[0] + dp[6] * dp[6] +
                             m2 * (dp[1] * dp[1] + dp[2] * dp[2] + dp[7] * dp[7] + dp[8] * dp[8]) +
                             q2 * (dp[3] * dp[3] + dp[5] * dp[5] + dp[9] * dp[9] + dp[11] * dp[11]) +
                             m4 * (dp[4] * dp[4] + dp[10] * dp[10]));
     if (nrm < p.tol) {
+      if (!all_in(prm, x0, y0, S, M, W, H, lane)) {
+        undo();
+        st = kOutOfBounds;
+        break;
+      }
       zn = warp_sum(sfd) / (df * dg);  // at the last sampled shape, as the first-order path
       have_zn = true;
       st = kOk;
       break;
     }
+  }
+  // iteration cap: the last update was accepted but never sampled
+  if (pending && st == kMaxIter && !all_in(prm, x0, y0, S, M, W, H, lane)) {
+    undo();
+    st = kOutOfBounds;
   }
   if (!have_zn) {
     float s0 = 0.f, s1 = 0.f, sfg = 0.f;
